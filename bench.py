@@ -1,0 +1,681 @@
+#!/usr/bin/env python3
+"""Benchmark of the state-vector gate engine on GB300.
+
+One step = one pass of the hot path over the 30-qubit complex128 workload:
+  HALL|0..0> (uniform fill), 100 Grover iterations with 8 seeded marked
+  items (oracle + diffusion, one fused pass each), the QFT, the Born-rule
+  probabilities and 1000 seeded samples, then the per-gate sweep H(t),
+  CNOT((t+1) mod n, t), CPHASE((t+1) mod n, t, k=1) for t = 0..n-1.
+Metric: amplitude-updates/s = 2^n x (operators applied per step) / step
+time, where HALL, each Grover operator G, the QFT and each swept gate count
+as one operator acting on all 2^n amplitudes (192 operators per step at
+n = 30).  The state (16 GiB) is larger than L2, so no flush is needed.
+
+Extra keys report the per-kernel bandwidth table, the 32-qubit complex64
+workload, the 10-qubit Grover run, the 24-qubit random circuit, the
+batched noisy trajectories and the adjoint gradient (each measured outside
+the timed region).
+
+Under torchrun with N > 1 every rank runs an independent replica (the path
+does not shard in this build); value = the work of all ranks / the slowest
+rank's time.  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "amplitude-updates/s & HBM GB/s per gate (30q); adjoint grad time/forward"
+UNIT = "amp-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=30, help="qubits of the main workload")
+    ap.add_argument("--iters", type=int, default=100, help="Grover iterations per step")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only", default="", help="run just one extra (profiling helper)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------- distributed ----
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(times_ms, work_units, backend_group=None):
+    """Whole-job value from per-rank elapsed times: work of all ranks / the
+    slowest rank's time.  Uses torch.distributed when initialised."""
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([times_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        w = torch.tensor([work_units], dtype=torch.float64, device=dev)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+        return float(t.item()), float(w.item())
+    return float(times_ms), float(work_units)
+
+
+# ---------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed
+    region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- our arm ----
+
+def kernel_source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_0902_0699_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(profile_name, src_hash):
+    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", profile_name)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for ln in open(path):
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha") != src_hash:
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Events:
+    def __init__(self, torch):
+        self.torch = torch
+        self.ev = []
+
+    def mark(self, name):
+        e = self.torch.cuda.Event(enable_timing=True)
+        e.record()
+        self.ev.append((name, e))
+
+    def spans(self):
+        out = {}
+        for (a, ea), (b, eb) in zip(self.ev, self.ev[1:]):
+            out.setdefault(b, 0.0)
+            out[b] += ea.elapsed_time(eb)
+        return out
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_0902_0699_gb300 as qc
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    n, iters = args.n, args.iters
+    N = 1 << n
+    S = N * 16
+    marked = W.marked_indices(W.rng(2026), n, 8)
+    st = qc.State(n, qc.QC_C128)
+    H = np.array([[1, 1], [1, -1]], dtype=np.complex128) / math.sqrt(2.0)
+    ops_per_step = 1 + iters + 1 + 3 * n
+
+    def step(ev: Events | None, sweep_ev=None):
+        if ev: ev.mark("start")
+        st.uniform()
+        if ev: ev.mark("hall_uniform")
+        for _ in range(iters):
+            st.grover_step(marked)
+        if ev: ev.mark("grover")
+        st.qft()
+        if ev: ev.mark("qft")
+        st.probs()
+        shots = st.sample(12345, 1000)
+        if ev: ev.mark("probs_sample")
+        for t in range(n):
+            if sweep_ev is not None: sweep_ev[("h", t)][0].record()
+            st.apply_1q(t, H)
+            if sweep_ev is not None:
+                sweep_ev[("h", t)][1].record()
+                sweep_ev[("cnot", t)][0].record()
+            st.cnot((t + 1) % n, t)
+            if sweep_ev is not None:
+                sweep_ev[("cnot", t)][1].record()
+                sweep_ev[("cphase", t)][0].record()
+            st.cphase((t + 1) % n, t, 1)
+            if sweep_ev is not None: sweep_ev[("cphase", t)][1].record()
+        if ev: ev.mark("sweep")
+        return shots
+
+    import torch.distributed as dist
+    for _ in range(args.warmup):
+        step(None)
+    torch.cuda.synchronize()
+    if dist.is_initialized():
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    launches0 = qc.kernel_launches()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    evs = []
+    sweep_all = []
+    t0.record()
+    for _ in range(args.steps):
+        ev = Events(torch)
+        sw = {(g, t): (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for g in ("h", "cnot", "cphase") for t in range(n)}
+        step(ev, sw)
+        evs.append(ev)
+        sweep_all.append(sw)
+    t1.record()
+    torch.cuda.synchronize()
+    if dist.is_initialized():
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches = qc.kernel_launches() - launches0
+    clocks = clk.stop()
+    elapsed = t0.elapsed_time(t1)
+    work = float(ops_per_step) * N * args.steps
+    tmax, wsum = aggregate(elapsed, work)
+    value = wsum / (tmax / 1e3)
+
+    # component times (mean per step, ms)
+    comp = {}
+    for ev in evs:
+        for k, v in ev.spans().items():
+            comp[k] = comp.get(k, 0.0) + v / args.steps
+    sweep = {}
+    for g in ("h", "cnot", "cphase"):
+        per_t = [statistics.mean(sw[(g, t)][0].elapsed_time(sw[(g, t)][1]) for sw in sweep_all) for t in range(n)]
+        sweep[g] = per_t
+    bytes_gate = {"h": 2 * S, "cnot": S, "cphase": S // 2}
+    peak = read_peaks()
+    hbm = peak["hbm_gbs"]
+    gb = lambda b, ms: b / (ms * 1e-3) / 1e9
+    grover_ms = comp["grover"] / iters
+    kernels = {
+        "grover_step (prep+pass+fix)": {"ms": grover_ms, "alg_bytes": 2 * S, "GB/s": gb(2 * S, grover_ms),
+                                        "launches_per_step": iters * 3},
+        "hall_uniform_fill": {"ms": comp["hall_uniform"], "alg_bytes": S, "GB/s": gb(S, comp["hall_uniform"])},
+        "qft": {"ms": comp["qft"], "alg_bytes": qft_bytes(n, 16), "GB/s": gb(qft_bytes(n, 16), comp["qft"])},
+    }
+    sweep_table = {}
+    for g in ("h", "cnot", "cphase"):
+        ms = sweep[g]
+        sweep_table[g] = {"ms_mean": statistics.mean(ms), "GB/s_per_t": [round(gb(bytes_gate[g], m), 1) for m in ms],
+                          "amp_updates_per_s_mean": N / (statistics.mean(ms) * 1e-3),
+                          "frac_of_measured_min": round(min(gb(bytes_gate[g], m) for m in ms) / hbm, 3),
+                          "frac_of_measured_max": round(max(gb(bytes_gate[g], m) for m in ms) / hbm, 3)}
+    # dominant kernel: the fused Grover pass (100 launches per step)
+    src_hash = kernel_source_hash(["grover.cu", "common.cuh"])
+    traffic = read_traffic("grover_pass_n30_c128.txt", src_hash)
+    achieved = gb(2 * S, grover_ms)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": traffic,
+                "kernel": "k_grover_pass_c128 (one fused oracle+diffusion read/write pass)",
+                "alg_bytes_per_launch": 2 * S, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+        "config": {"workload": "grover%d_qft_sweep_c128" % n, "qubits": n, "state_bytes": S,
+                   "grover_iterations": iters, "marked": 8, "sweep": "H, CNOT(t+1 mod n, t), CPHASE k=1 for t=0..n-1",
+                   "operators_per_step": ops_per_step, "l2": "inputs larger than L2 (16 GiB state)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches),
+        "kernels": kernels, "sweep": sweep_table, "component_ms_per_step": comp,
+    }
+    return out, st, step, ops_per_step, N
+
+
+def qft_bytes(n, amp):
+    """Algorithmic bytes of the QFT as built: one read+write pass per tile
+    group plus the bit-reversal pass."""
+    C, K = (3, 9) if amp == 16 else (4, 9)
+    g0 = min(n, C + K)
+    rest = n - g0
+    passes = 1 + (-(-rest // K) if rest > 0 else 0)
+    return (passes + 1) * 2 * (1 << n) * amp
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d.get("hbm_gbs", 6800.0)), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+def run_e2e(args, st, step_fn, ops_per_step, N):
+    """Same workload through the public API with the state in pinned host
+    memory: every step copies the input state host->device, runs the step and
+    copies the final state and the samples back."""
+    import numpy as np
+    import torch
+    n = args.n
+    host_in = torch.zeros(N, dtype=torch.complex128, pin_memory=True)
+    host_in[0] = 1.0
+    host_out = torch.empty(N, dtype=torch.complex128, pin_memory=True)
+    host_shots = torch.empty(1000, dtype=torch.int64, pin_memory=True)
+    import paper_0902_0699_gb300 as qc
+
+    def e2e_step():
+        st.tensor.copy_(host_in, non_blocking=True)
+        qc.qc_state_invalidate(st.h)
+        shots = step_fn(None)
+        host_out.copy_(st.tensor, non_blocking=True)
+        host_shots.copy_(shots, non_blocking=True)
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    el = (time.perf_counter() - t0) * 1e3
+    tmax, wsum = aggregate(el, float(ops_per_step) * N * args.steps)
+    del host_in, host_out
+    return {"value": wsum / (tmax / 1e3), "unit": UNIT, "h2d_bytes_per_step": N * 16 + 8 * 8,
+            "d2h_bytes_per_step": N * 16 + 8 * 1000, "ms_per_step": tmax / args.steps,
+            "note": "host state in pinned memory -> device, full step, final state and samples -> host"}
+
+
+# ---------------------------------------------------------------- extras ----
+
+def extra_c64(n=32, iters=100):
+    import numpy as np
+    import torch
+    import paper_0902_0699_gb300 as qc
+    import workloads as W
+    N = 1 << n
+    S = N * 8
+    marked = W.marked_indices(W.rng(2027), n, 8)
+    st = qc.State(n, qc.QC_C64)
+    H = np.array([[1, 1], [1, -1]], dtype=np.complex128) / math.sqrt(2.0)
+    res = {}
+
+    def run(timed):
+        ev = Events(torch)
+        ev.mark("start")
+        st.uniform()
+        ev.mark("hall_uniform")
+        for _ in range(iters):
+            st.grover_step(marked)
+        ev.mark("grover")
+        st.qft()
+        ev.mark("qft")
+        hs = []
+        for t in range(n):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(); st.apply_1q(t, H); b.record()
+            c_, d = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c_.record(); st.cnot((t + 1) % n, t); d.record()
+            e_, f = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e_.record(); st.cphase((t + 1) % n, t, 1); f.record()
+            hs.append(((a, b), (c_, d), (e_, f)))
+        ev.mark("sweep")
+        torch.cuda.synchronize()
+        return ev.spans(), hs
+    run(False)
+    spans, hs = run(True)
+    gb = lambda b, ms: b / (ms * 1e-3) / 1e9
+    ms = [[x[0].elapsed_time(x[1]) for x in h] for h in hs]
+    total = sum(spans.values())
+    res = {"qubits": n, "state_bytes": S, "ms_total": total,
+           "amp_updates_per_s": (1 + iters + 1 + 3 * n) * N / (total * 1e-3),
+           "grover_step_ms": spans["grover"] / iters, "grover_GB/s": gb(2 * S, spans["grover"] / iters),
+           "qft_ms": spans["qft"], "qft_GB/s": gb(qft_bytes(n, 8), spans["qft"]),
+           "h_GB/s_mean": statistics.mean(gb(2 * S, m[0]) for m in ms),
+           "cnot_GB/s_mean": statistics.mean(gb(S, m[1]) for m in ms),
+           "cphase_GB/s_mean": statistics.mean(gb(S / 2, m[2]) for m in ms)}
+    st.close()
+    del st
+    torch.cuda.empty_cache()
+    return res
+
+
+def extra_c1():
+    import numpy as np
+    import torch
+    import paper_0902_0699_gb300 as qc
+    import workloads as W
+    n = 10
+    marked = W.marked_indices(W.rng(0), n, 1)
+    st = qc.State(n, qc.QC_C128)
+    it = W.grover_iterations(n)
+    for _ in range(3):
+        st.grover_run(marked, it)
+        st.sample(1, 1000)
+    torch.cuda.synchronize()
+    reps = 20
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for r in range(reps):
+        st.grover_run(marked, it)
+        p = st.probs()
+        st.sample(r, 1000)
+    b.record()
+    torch.cuda.synchronize()
+    ps = float(p[int(marked[0])].item())
+    return {"qubits": n, "iterations": it, "us_per_run": a.elapsed_time(b) / reps * 1e3,
+            "p_success": ps, "p_success_closed_form": math.sin((2 * it + 1) * math.asin(2 ** -5)) ** 2,
+            "note": "grover_run (one kernel, state in shared memory) + probs + 1000 samples (sampling syncs the stream for the norm check)"}
+
+
+def extra_c2():
+    import numpy as np
+    import torch
+    import paper_0902_0699_gb300 as qc
+    import workloads as W
+    n, layers = 24, 200
+    circ = W.random_circuit(n, layers, seed=24)
+    res = {}
+    for dt, name in ((qc.QC_C128, "c128"), (qc.QC_C64, "c64")):
+        st = qc.State(n, dt).reset(0)
+
+        def run():
+            st.reset(0)
+            for l in range(layers):
+                st.apply_1q_layer(circ.U[l])
+                for (c, t) in circ.cnot_pairs(l):
+                    st.cnot(c, t)
+            st.qft()
+        run()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        run()
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        gates = layers * n + sum(len(circ.cnot_pairs(l)) for l in range(layers)) + n * (n + 1) // 2 + n // 2
+        res[name] = {"ms": ms, "gates": gates, "gate_level_amp_updates_per_s": gates * (1 << n) / (ms * 1e-3)}
+        st.close()
+    return res
+
+
+def extra_c4():
+    import ctypes
+    import numpy as np
+    import torch
+    import paper_0902_0699_gb300 as qc
+    import workloads as W
+    tb = W.trajectory_batch(4096, 12, 20, seed=4096)
+    n_inst = len(tb.nq)
+    nq = np.ascontiguousarray(tb.nq, dtype=np.int32)
+    mk = np.ascontiguousarray(tb.marked, dtype=np.uint64)
+    it = np.ascontiguousarray(tb.iters, dtype=np.int32)
+    d = qc.TrajDesc(n_inst, nq.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                    mk.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                    it.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), tb.seed, tb.thr_gate, tb.thr_readout,
+                    tb.p_readout)
+    plan = ctypes.c_void_p()
+    s = torch.cuda.current_stream().cuda_stream
+    t0 = time.perf_counter()
+    rc = qc.lib().qc_traj_plan_create(ctypes.byref(d), ctypes.c_void_p(s), 1, ctypes.byref(plan))
+    torch.cuda.synchronize()
+    t_plan = time.perf_counter() - t0
+    if rc:
+        return {"error": qc.last_error()}
+    ps = torch.empty(n_inst, dtype=torch.float64, device="cuda")
+    pr = torch.empty_like(ps)
+    oc = torch.empty(n_inst, dtype=torch.int64, device="cuda")
+    ne = torch.empty(n_inst, dtype=torch.int32, device="cuda")
+    out = qc.TrajOut(ps.data_ptr(), pr.data_ptr(), oc.data_ptr(), ne.data_ptr())
+    qc.lib().qc_traj_plan_run(plan, ctypes.byref(out))
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    rc = qc.lib().qc_traj_plan_run(plan, ctypes.byref(out))
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    info = [ctypes.c_int(), ctypes.c_int(), ctypes.c_int()]
+    qc.lib().qc_traj_plan_info(plan, *[ctypes.byref(x) for x in info])
+    qc.lib().qc_traj_plan_free(plan)
+    psn = ps.cpu().numpy()
+    amp_its = float(np.sum((2.0 ** tb.nq) * (tb.iters + 1)))
+    hist, edges = np.histogram(psn, bins=10, range=(0, 1))
+    return {"instances": n_inst, "ms": ms, "instances_per_s": n_inst / (ms * 1e-3),
+            "amp_iterations_per_s": amp_its / (ms * 1e-3), "plan_s_with_autotune": t_plan,
+            "shape": {"ctas_per_instance": info[0].value, "threads": info[1].value, "grid": info[2].value},
+            "p_success_mean": float(psn.mean()), "p_readout_mean": float(pr.cpu().numpy().mean()),
+            "errors_mean": float(ne.cpu().numpy().mean()), "p_success_hist": hist.tolist()}
+
+
+def extra_c5():
+    import ctypes
+    import numpy as np
+    import torch
+    import oracle  # noqa: F401  (gate list helper lives with the workloads)
+    import paper_0902_0699_gb300 as qc
+    import workloads as W
+    n, layers = 20, 50
+    res = {}
+    for dt, B, name in ((qc.QC_C64, 64, "c64_batch64"), (qc.QC_C128, 1, "c128_batch1")):
+        circs = W.ansatz(n, layers, seed=5, batch=B)
+        P = circs[0].n_params
+        gl = []
+        for l in range(layers):
+            for q in range(n):
+                gl.append(qc.Gate(qc.QC_G_RY, q, 0, l * 2 * n + 2 * q))
+                gl.append(qc.Gate(qc.QC_G_RZ, q, 0, l * 2 * n + 2 * q + 1))
+            for i in range(n):
+                gl.append(qc.Gate(qc.QC_G_CNOT, i, (i + 1) % n, 0))
+        gates = (qc.Gate * len(gl))(*gl)
+        terms = W.ansatz_hamiltonian(n)
+        tarr = (qc.PauliTerm * len(terms))(*[qc.PauliTerm(x, z, c) for (x, z, c) in terms])
+        theta = torch.tensor(np.stack([c.theta for c in circs]), dtype=torch.float64, device="cuda")
+        cdt = torch.complex64 if dt == qc.QC_C64 else torch.complex128
+        psi = torch.empty(B << n, dtype=cdt, device="cuda")
+        lam = torch.empty_like(psi)
+        E = torch.empty(B, dtype=torch.float64, device="cuda")
+        grad = torch.empty(B, P, dtype=torch.float64, device="cuda")
+        s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        L = qc.lib()
+        vp = ctypes.c_void_p
+
+        def fwd():
+            return L.qc_circuit_forward(n, dt, B, gates, len(gl), vp(theta.data_ptr()), P, vp(psi.data_ptr()), s)
+
+        def adj():
+            return L.qc_adjoint_grad(n, dt, B, gates, len(gl), vp(theta.data_ptr()), P, P, tarr, len(terms),
+                                     vp(psi.data_ptr()), vp(lam.data_ptr()), vp(E.data_ptr()),
+                                     vp(grad.data_ptr()), s)
+        fwd(); adj()
+        torch.cuda.synchronize()
+        a, b, c_ = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(); rc1 = fwd(); b.record(); rc2 = adj(); c_.record()
+        torch.cuda.synchronize()
+        if rc1 or rc2:
+            res[name] = {"error": qc.last_error()}
+            continue
+        tf, tg = a.elapsed_time(b), b.elapsed_time(c_)
+        res[name] = {"qubits": n, "gates": len(gl), "angles": P, "batch": B, "forward_ms": tf,
+                     "grad_ms (forward+backward)": tg, "grad_time_over_forward": tg / tf,
+                     "energy_mean": float(E.mean().item())}
+    return res
+
+
+# ------------------------------------------------------------ CPU oracle ----
+
+def cpu_oracle_sample(n=22, iters=2):
+    """The oracle as it stands on the host cores: HALL, `iters` literal
+    Grover operators, the literal QFT and the gate sweep, on an n-qubit
+    complex128 state.  Returns (amp-updates/s with the same operator count
+    as the GPU step, seconds, threads)."""
+    import numpy as np
+    import oracle as O
+    import workloads as W
+    O.set_threads(os.cpu_count() or 1)
+    N = 1 << n
+    psi = O.zero_state(n)
+    marked = W.marked_indices(W.rng(2026), n, 8)
+    t0 = time.perf_counter()
+    O.hall(psi, n)
+    for _ in range(iters):
+        O.grover_step(psi, n, marked)
+    O.qft(psi, n)
+    p = O.probs(psi, n)
+    O.sample_from_probs(p, 12345, 1000)
+    for t in range(n):
+        O.apply_1q(psi, n, t, O.H_MAT)
+        O.cnot(psi, n, (t + 1) % n, t)
+        O.cphase(psi, n, (t + 1) % n, t, 1)
+    el = time.perf_counter() - t0
+    ops = 1 + iters + 1 + 3 * n
+    return ops * N / el, el, O.get_threads(), ops
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    n_s = 25
+    vals, secs = [], []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(n_s, 1)
+    for _ in range(args.steps):
+        v, el, cores, ops = cpu_oracle_sample(n_s, 3)
+        vals.append(v)
+        secs.append(el)
+    value = statistics.mean(vals)
+    sample = "per step: %d-qubit complex128 HALL, 3 literal Grover operators (8 marked), literal QFT, probs + 1000 samples, H/CNOT/CPHASE sweep over all t (%d operators)" % (n_s, ops)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(secs) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "grover%d_qft_sweep_c128" % args.n, "qubits": args.n,
+                       "reference_sample_qubits": n_s},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ------------------------------------------------------------------ main ----
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return 0
+    import torch
+    import torch.distributed as dist
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    if args.only:
+        fn = {"c64": extra_c64, "c1": extra_c1, "c2": extra_c2, "c4": extra_c4, "c5": extra_c5}[args.only]
+        print(json.dumps({args.only: fn()}), flush=True)
+        return 0
+    out, st, step_fn, ops, N = run_ours(args, ws, rank, local)
+    if not args.no_e2e:
+        try:
+            out["e2e"] = run_e2e(args, st, step_fn, ops, N)
+        except Exception as e:  # report, do not hide
+            out["e2e"] = {"error": repr(e)}
+    st.close()
+    del st
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_cpu:
+        v, el, cores, nops = cpu_oracle_sample(25, 3)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": "25-qubit complex128: HALL, 3 literal Grover operators, literal QFT, probs + 1000 samples, H/CNOT/CPHASE sweep (%d operators, %.1f s)" % (nops, el)}
+    if rank == 0 and not args.no_extras:
+        extras = {}
+        for name, fn in (("c64_n32", extra_c64), ("grover_n10", extra_c1), ("random_n24", extra_c2),
+                         ("trajectories_4096", extra_c4), ("adjoint_n20", extra_c5)):
+            try:
+                extras[name] = fn()
+            except Exception as e:
+                extras[name] = {"error": repr(e)}
+            torch.cuda.empty_cache()
+        out["extras"] = extras
+    if dist.is_initialized():
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

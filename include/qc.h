@@ -1,0 +1,298 @@
+/*
+ * qc.h -- C ABI of the GB300 state-vector gate engine.
+ *
+ * The operations are those of the QCMPI paper (Tabakin & Julia-Diaz,
+ * arXiv:0902.0699): a 2^n-amplitude complex state vector in "standard order"
+ * (sec. 2, Eq. staten / Eq. ampn) acted on by one-qubit operators (sec. 3,
+ * Eq. resmat1), two-qubit operators and their CNOT / CPHASE / CPHASEK special
+ * cases (sec. 4, Eqs. resmat2, cphasek), the Hadamard on all qubits (HALL,
+ * Eq. HALL), Grover's oracle and inversion (sec. 5.1, Eqs. oracle1,
+ * inversion), the quantum Fourier transform (Appendix A) and Born-rule
+ * measurement (sec. 2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Qubit t (0 <= t < n) is bit t of the basis index, counted from the
+ *    least significant bit.  The paper labels qubits i_s = 1 .. n_q from the
+ *    most significant bit, with stride 2^{n_q - i_s}; so t = n_q - i_s.
+ *  - A state buffer holds 2^n amplitudes, interleaved (re, im):
+ *    QC_C128 = two doubles (16 bytes) per amplitude, QC_C64 = two floats
+ *    (8 bytes).  The buffer is device memory, 256-byte aligned.
+ *  - A 2x2 operator is 8 host doubles, row-major, (re, im) interleaved:
+ *    U00 U01 U10 U11 with U_ab = <a|U|b>; rows are output amplitudes
+ *    (Eq. resmat1).  For QC_C64 the matrix is rounded to float once.
+ *  - All gate calls are asynchronous and ordered on the state's stream
+ *    (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ *    Calls that return a host value synchronise that stream.
+ *  - Arguments are validated before anything is launched; invalid ones
+ *    return QC_EINVAL and leave the state unchanged.  A CUDA launch or
+ *    runtime failure returns QC_ECUDA.  qc_last_error() returns a message
+ *    describing the last failure on the calling host thread.
+ *  - Device code never traps: a bounded wait that gives up reports
+ *    QC_ETIMEOUT through a status word the host reads.
+ */
+#ifndef QC_H
+#define QC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QC_OK = 0,
+  QC_EINVAL = 1,   /* bad argument; nothing was launched */
+  QC_ENOMEM = 2,   /* a device allocation failed */
+  QC_ECUDA = 3,    /* a CUDA call or kernel launch failed */
+  QC_ETIMEOUT = 4  /* a device-side bounded wait gave up */
+} qc_status;
+
+typedef enum { QC_C128 = 0, QC_C64 = 1 } qc_dtype;
+
+#define QC_MAX_QUBITS 34      /* largest n accepted for a single state */
+#define QC_MAX_MARKED 1024    /* largest number of Grover marked items per call */
+
+/* Opaque state handle: a device buffer (owned or borrowed), its size, dtype,
+ * stream and a small device scratch area for reductions. */
+typedef struct qc_state qc_state;
+
+/* Message for the last failure on this host thread ("" if none).  The
+ * pointer stays valid until the next qc_* call on this thread. */
+const char* qc_last_error(void);
+
+/* Library version string. */
+const char* qc_version(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * threads, all devices) -- a diagnostic for launch accounting.  A CUDA graph
+ * replay counts the kernels it contains. */
+unsigned long long qc_kernel_launches(void);
+
+/* ---------------------------------------------------------------- state -- */
+
+/* Allocate a 2^n state on the current device and set it to |0..0> (C_0 = 1,
+ * all other amplitudes 0: the starting state of sec. 5.1).  The handle owns
+ * the buffer; qc_state_free releases it.  1 <= n <= QC_MAX_QUBITS.
+ * Returns QC_ENOMEM if the buffer does not fit. */
+qc_status qc_state_alloc(int n, qc_dtype dt, void* stream, qc_state** out);
+
+/* Wrap an existing device buffer of 2^n amplitudes (e.g. a torch tensor's
+ * storage) without copying or initialising it.  The buffer must stay alive
+ * and 16-byte aligned (256-byte alignment recommended) for the handle's
+ * lifetime; qc_state_free does not release it. */
+qc_status qc_state_wrap(void* dev_ptr, int n, qc_dtype dt, void* stream, qc_state** out);
+
+/* Release the handle (and the buffer if it owns it).  NULL is accepted. */
+qc_status qc_state_free(qc_state* s);
+
+/* Set the state to the computational basis state |basis_index>. */
+qc_status qc_state_reset(qc_state* s, uint64_t basis_index);
+
+/* Set every amplitude to 2^{-n/2} (= HALL|0..0>, Eq. HALL applied to the
+ * start state), without touching the previous contents. */
+qc_status qc_state_uniform(qc_state* s);
+
+/* Device pointer, qubit count, dtype of the handle. */
+qc_status qc_state_info(const qc_state* s, void** dev_ptr, int* n, qc_dtype* dt);
+
+/* Change the stream later calls on this handle are ordered on. */
+qc_status qc_state_set_stream(qc_state* s, void* stream);
+
+/* Tell the handle its buffer was written outside this library (drops cached
+ * reductions such as the running amplitude sum used by qc_grover_step). */
+qc_status qc_state_invalidate(qc_state* s);
+
+/* ---------------------------------------------------------------- gates -- */
+
+/* One-qubit operator on qubit t: OneOpA, Eq. resmat1.  For each of the
+ * 2^{n-1} pairs n0 (bit t = 0), n1 = n0 + 2^t:
+ *   C~_{n0} = U00 C_{n0} + U01 C_{n1},  C~_{n1} = U10 C_{n0} + U11 C_{n1}.
+ * Structured U (diagonal, anti-diagonal, real, Hadamard, phase-only) run
+ * specialised kernels with the same result up to rounding. */
+qc_status qc_apply_1q(qc_state* s, int t, const double U[8]);
+
+/* Controlled U: the 4x4 operator diag(I, U) of Eq. resmat2 with qubit c as
+ * control and t as target -- U acts on the t-pair only where bit c = 1.
+ * c != t. */
+qc_status qc_apply_ctrl(qc_state* s, int c, int t, const double U[8]);
+
+/* CNOT (sec. 4.2): flips bit t where bit c = 1.  A pure permutation: the
+ * result is bit-exact.  c != t. */
+qc_status qc_cnot(qc_state* s, int c, int t);
+
+/* CPHASEK (Eq. cphasek): multiplies the amplitudes whose bits c and t are
+ * both 1 by e^{2 pi i / 2^k}, k >= 1 (k = 1 is CPHASEA = diag(1,1,1,-1);
+ * k = 1 and 2 are exact sign / i rotations).  Symmetric in c, t; c != t. */
+qc_status qc_cphase(qc_state* s, int c, int t, int k);
+
+/* SWAP of qubits a and b (Appendix A): exchanges bits a and b of every basis
+ * index.  A permutation: bit-exact.  a != b. */
+qc_status qc_swap(qc_state* s, int a, int b);
+
+/* HALL (Eq. HALL): the Hadamard on every qubit, as fused shared-memory tile
+ * passes (several qubits per pass over the state). */
+qc_status qc_hall(qc_state* s);
+
+/* A layer of one-qubit operators: U[8*q .. 8*q+7] on qubit q for every q
+ * whose bit is set in qubit_mask (operators on distinct qubits commute; the
+ * result equals applying them one by one).  U is a host array of 8*n
+ * doubles.  Runs as fused shared-memory tile passes. */
+qc_status qc_apply_1q_layer(qc_state* s, const double* U, uint64_t qubit_mask);
+
+/* Grover operator G = HALL . Inv . HALL . Oracle (sec. 5.1) on the current
+ * state: the oracle negates each marked amplitude (Eq. oracle1), and
+ * HALL . Inv . HALL = 2|s><s| - I (Eq. inversion) maps C_i -> 2 m - C_i with
+ * m the mean amplitude after the oracle.  `marked` is a host array of
+ * n_marked (1 .. QC_MAX_MARKED) distinct indices < 2^n.  One fused
+ * read+write pass; the running amplitude sum is kept on the device between
+ * calls (recomputed after any other mutation). */
+qc_status qc_grover_step(qc_state* s, const uint64_t* marked, int n_marked);
+
+/* Grover search of sec. 5.1: prepare HALL|0..0>, then apply G `iters`
+ * times.  For small states (<= 8192 amplitudes for QC_C128, 16384 for
+ * QC_C64) the whole run is one kernel with the state in shared memory. */
+qc_status qc_grover_run(qc_state* s, const uint64_t* marked, int n_marked, int iters);
+
+/* Quantum Fourier transform (Appendix A): the Hadamard / CPHASEK ladder
+ * followed by the qubit-order reversal swaps, i.e.
+ *   C~_{n'} = 2^{-n/2} sum_n e^{+2 pi i n n' / 2^n} C_n.
+ * Runs as fused tile passes plus one in-place bit-reversal pass. */
+qc_status qc_qft(qc_state* s);
+
+/* ----------------------------------------------------------- reductions -- */
+
+/* sum_i |C_i|^2 accumulated in FP64 (the normalisation of sec. 2).
+ * Synchronises the stream; *out_host receives the value. */
+qc_status qc_norm(const qc_state* s, double* out_host);
+
+/* Born-rule probabilities p_i = |C_i|^2 in FP64 (re*re + im*im, rounded
+ * separately), written to out_dev (2^n doubles of device memory). */
+qc_status qc_probs(const qc_state* s, double* out_dev);
+
+/* <psi|P|psi> for the Pauli string P = i^{|x&z|} X^x Z^z (X on bits of
+ * xmask only, Z on zmask only, Y where both are set), FP64 accumulation.
+ * out_host[0..1] = (re, im).  Synchronises the stream. */
+qc_status qc_expect_pauli(const qc_state* s, uint64_t xmask, uint64_t zmask, double out_host[2]);
+
+/* Scale the state by 1/sqrt(sum |C|^2) (FP64 norm).  *norm_out_host (if not
+ * NULL) receives the norm before scaling.  Synchronises the stream. */
+qc_status qc_renormalize(qc_state* s, double* norm_out_host);
+
+/* Seeded Born-rule measurement, `shots` outcomes written to out_dev
+ * (uint64 device array).  Definition (identical on every device):
+ *   w_i = trunc(p_i * 2^62) (p_i as in qc_probs), W_i = w_0 + .. + w_i
+ *   (exact 64-bit integers), total = W_{N-1}; shot s draws Philox4x32-10
+ *   (Salmon et al., SC'11) with counter (s_lo, s_hi, 0, 0) and key
+ *   (seed_lo, seed_hi), r = x0 * 2^32 + x1, target = floor(r * total / 2^64),
+ *   outcome = smallest i with W_i > target.
+ * Requires sum p_i <= 2 (QC_EINVAL otherwise) and shots >= 0.  Uses a
+ * temporary device buffer of 8 * 2^n bytes (QC_ENOMEM if it does not fit). */
+qc_status qc_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_t* out_dev);
+
+/* ---------------------------------------------- batched noisy trajectories
+ * Many independent noisy Grover runs ("multiverses", sec. 6.2-6.3) of uneven
+ * qubit counts, complex64 with FP64 reductions, in one persistent launch.
+ * Noise model: after every gate location a Pauli error may strike: stage 0
+ * is the initial HALL (one location per qubit), iteration r has stages
+ * 1+4r (after the oracle), 2+4r (after each H of the first HALL), 3+4r
+ * (after Inv) and 4+4r (after each H of the second HALL), one location per
+ * qubit each.  Location (instance i, stage s, qubit q) draws Philox4x32-10
+ * with counter (i, s, q, 0x4E4F4953) and key (seed_lo, seed_hi): an error
+ * strikes when x0 < thr_gate, and it is X, Y, Z for floor(x1*3/2^32) = 0, 1,
+ * 2.  At the end each instance reports its success probability
+ * sum_{marked} |C|^2, the probability that a read-out with independent bit
+ * flips (each with probability p_readout) returns the marked item, one
+ * seeded measured outcome (counter (i, 0xFFFFFFFF, 0, 0x4D454153), sampled
+ * as in qc_sample) with each bit q flipped when the draw (i, 0xFFFFFFFF, q,
+ * 0x52454144) has x0 < thr_readout, and the number of Pauli errors. */
+typedef struct {
+  int32_t n_inst;          /* number of instances, >= 1 */
+  const int32_t* nq;       /* host, qubit count per instance, 1 .. QC_TRAJ_MAX_QUBITS */
+  const uint64_t* marked;  /* host, marked item per instance (< 2^nq) */
+  const int32_t* iters;    /* host, Grover iterations per instance (>= 0) */
+  uint64_t seed;
+  uint32_t thr_gate;       /* floor(p_gate * 2^32) */
+  uint32_t thr_readout;    /* floor(p_readout * 2^32) */
+  double p_readout;        /* the read-out flip probability itself */
+} qc_traj_desc;
+
+#define QC_TRAJ_MAX_QUBITS 22
+
+typedef struct {
+  double* p_success;    /* device, n_inst doubles */
+  double* p_readout;    /* device, n_inst doubles */
+  uint64_t* outcome;    /* device, n_inst outcomes */
+  uint32_t* n_errors;   /* device, n_inst counts */
+} qc_traj_out;
+
+typedef struct qc_traj_plan qc_traj_plan;
+
+/* Validate the batch, upload its descriptors, pick the launch shape (CTAs
+ * cooperating per instance, shared-memory tile size) with the built-in
+ * autotuner and allocate the device workspace.  `autotune` = 0 takes the
+ * default shape without timing trial runs. */
+qc_status qc_traj_plan_create(const qc_traj_desc* d, void* stream, int autotune, qc_traj_plan** out);
+
+/* Run every instance of the plan: one persistent kernel launch (replayed
+ * from a CUDA graph after the first run).  Asynchronous on the plan's
+ * stream.  Returns QC_ETIMEOUT (after synchronising) if a device-side
+ * bounded wait gave up. */
+qc_status qc_traj_plan_run(qc_traj_plan* p, const qc_traj_out* out);
+
+/* Chosen launch shape: clusters of `ctas_per_inst` CTAs, `threads` threads. */
+qc_status qc_traj_plan_info(const qc_traj_plan* p, int* ctas_per_inst, int* threads, int* grid);
+
+qc_status qc_traj_plan_free(qc_traj_plan* p);
+
+/* ----------------------------------------------------- adjoint gradient --
+ * Parameterised circuits on a batch of B states (state b at element offset
+ * b * 2^n) and the gradient of E = <psi|H|psi> by uncomputation.  Not part
+ * of the paper. */
+typedef enum {
+  QC_G_RX = 0,   /* exp(-i theta X / 2) on q0, theta = theta[param] */
+  QC_G_RY = 1,   /* exp(-i theta Y / 2) */
+  QC_G_RZ = 2,   /* exp(-i theta Z / 2) */
+  QC_G_CNOT = 3, /* control q0, target q1 */
+  QC_G_H = 4     /* Hadamard on q0 */
+} qc_gate_kind;
+
+typedef struct {
+  int32_t kind;   /* qc_gate_kind */
+  int32_t q0, q1; /* qubits (q1 only for CNOT) */
+  int32_t param;  /* angle index for rotations, else ignored */
+} qc_gate;
+
+typedef struct {
+  uint64_t xmask, zmask; /* Pauli string as in qc_expect_pauli */
+  double coeff;          /* real coefficient */
+} qc_pauli_term;
+
+/* psi_b = U_G .. U_1 |0..0> for each batch element b, with angles
+ * theta_dev[b * theta_stride + param] (device doubles).  psi_dev holds
+ * B * 2^n amplitudes of dtype dt.  Gates are a host array. */
+qc_status qc_circuit_forward(int n, qc_dtype dt, int B, const qc_gate* gates, int n_gates,
+                             const double* theta_dev, int64_t theta_stride,
+                             void* psi_dev, void* stream);
+
+/* Energy E_b = <psi_b|H|psi_b> (device doubles energy_dev[b]) and the
+ * gradient dE_b/dtheta (grad_dev[b * theta_stride + param], device doubles;
+ * entries of parameters the circuit does not use are set to 0).  Runs the
+ * forward pass, then walks the gates backwards applying U^dagger to psi and
+ * to lambda = H psi (no intermediate states are stored); for a rotation
+ * gate j with Pauli generator P: dE/dtheta_j = Im <lambda_j|P|psi_j>, with
+ * FP64 accumulation.  psi_dev and lam_dev are caller-owned buffers of
+ * B * 2^n amplitudes; on return psi_dev holds |0..0> up to rounding.  H is a
+ * host array of Pauli terms with real coefficients. */
+qc_status qc_adjoint_grad(int n, qc_dtype dt, int B, const qc_gate* gates, int n_gates,
+                          const double* theta_dev, int64_t theta_stride, int n_params,
+                          const qc_pauli_term* H, int n_terms,
+                          void* psi_dev, void* lam_dev, double* energy_dev, double* grad_dev,
+                          void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QC_H */

@@ -1,0 +1,382 @@
+"""Python binding of the GB300 state-vector gate engine (libqcgb300.so).
+
+Argument marshalling only: every operation runs in the CUDA library behind
+the C ABI of include/qc.h.  There is no CPU fallback -- if the library is
+not built, importing the functions raises.  PyTorch supplies device memory
+and streams (tensors are wrapped by pointer, streams by their handle).
+
+The qubit convention is the library's: qubit t is bit t of the basis index
+(t = n_q - i_s in the QCMPI paper's labels, where i_s = 1 is the most
+significant qubit).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+QC_OK, QC_EINVAL, QC_ENOMEM, QC_ECUDA, QC_ETIMEOUT = 0, 1, 2, 3, 4
+QC_C128, QC_C64 = 0, 1
+QC_MAX_QUBITS = 34
+QC_MAX_MARKED = 1024
+QC_TRAJ_MAX_QUBITS = 22
+QC_G_RX, QC_G_RY, QC_G_RZ, QC_G_CNOT, QC_G_H = 0, 1, 2, 3, 4
+
+LIB_PATH = _build.LIB
+
+
+class QCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("qc status %d: %s" % (status, msg))
+        self.status = status
+
+
+class TrajDesc(ctypes.Structure):
+    _fields_ = [("n_inst", ctypes.c_int32), ("nq", ctypes.POINTER(ctypes.c_int32)),
+                ("marked", ctypes.POINTER(ctypes.c_uint64)), ("iters", ctypes.POINTER(ctypes.c_int32)),
+                ("seed", ctypes.c_uint64), ("thr_gate", ctypes.c_uint32),
+                ("thr_readout", ctypes.c_uint32), ("p_readout", ctypes.c_double)]
+
+
+class TrajOut(ctypes.Structure):
+    _fields_ = [("p_success", ctypes.c_void_p), ("p_readout", ctypes.c_void_p),
+                ("outcome", ctypes.c_void_p), ("n_errors", ctypes.c_void_p)]
+
+
+class Gate(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("q0", ctypes.c_int32), ("q1", ctypes.c_int32),
+                ("param", ctypes.c_int32)]
+
+
+class PauliTerm(ctypes.Structure):
+    _fields_ = [("xmask", ctypes.c_uint64), ("zmask", ctypes.c_uint64), ("coeff", ctypes.c_double)]
+
+
+_VP = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+_I = ctypes.c_int
+_U64 = ctypes.c_uint64
+_I64 = ctypes.c_int64
+
+# name -> argument types (all return qc_status unless noted)
+_SIGS = {
+    "qc_state_alloc": [_I, _I, _VP, ctypes.POINTER(_VP)],
+    "qc_state_wrap": [_VP, _I, _I, _VP, ctypes.POINTER(_VP)],
+    "qc_state_free": [_VP],
+    "qc_state_reset": [_VP, _U64],
+    "qc_state_uniform": [_VP],
+    "qc_state_info": [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "qc_state_set_stream": [_VP, _VP],
+    "qc_state_invalidate": [_VP],
+    "qc_apply_1q": [_VP, _I, _DP],
+    "qc_apply_ctrl": [_VP, _I, _I, _DP],
+    "qc_cnot": [_VP, _I, _I],
+    "qc_cphase": [_VP, _I, _I, _I],
+    "qc_swap": [_VP, _I, _I],
+    "qc_hall": [_VP],
+    "qc_apply_1q_layer": [_VP, _DP, _U64],
+    "qc_grover_step": [_VP, _U64P, _I],
+    "qc_grover_run": [_VP, _U64P, _I, _I],
+    "qc_qft": [_VP],
+    "qc_norm": [_VP, _DP],
+    "qc_probs": [_VP, _VP],
+    "qc_expect_pauli": [_VP, _U64, _U64, _DP],
+    "qc_renormalize": [_VP, _DP],
+    "qc_sample": [_VP, _U64, _I64, _VP],
+    "qc_traj_plan_create": [ctypes.POINTER(TrajDesc), _VP, _I, ctypes.POINTER(_VP)],
+    "qc_traj_plan_run": [_VP, ctypes.POINTER(TrajOut)],
+    "qc_traj_plan_info": [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "qc_traj_plan_free": [_VP],
+    "qc_circuit_forward": [_I, _I, _I, ctypes.POINTER(Gate), _I, _VP, _I64, _VP, _VP],
+    "qc_adjoint_grad": [_I, _I, _I, ctypes.POINTER(Gate), _I, _VP, _I64, _I,
+                        ctypes.POINTER(PauliTerm), _I, _VP, _VP, _VP, _VP, _VP],
+}
+
+_lib = None
+
+
+def lib():
+    """Load libqcgb300.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError("libqcgb300.so is not built: %s" % path)
+        L = ctypes.CDLL(path)
+        for name, args in _SIGS.items():
+            if not hasattr(L, name):
+                continue  # calling a missing export raises AttributeError: no fallback
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.qc_last_error.restype = ctypes.c_char_p
+        L.qc_last_error.argtypes = []
+        L.qc_version.restype = ctypes.c_char_p
+        L.qc_version.argtypes = []
+        L.qc_kernel_launches.restype = ctypes.c_ulonglong
+        L.qc_kernel_launches.argtypes = []
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().qc_last_error().decode()
+
+
+def _check(st: int):
+    if st != QC_OK:
+        raise QCError(st, last_error())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _mat8(U) -> np.ndarray:
+    U = np.asarray(U)
+    if U.dtype.kind == "c":
+        U = np.stack([U.real, U.imag], axis=-1)
+    a = np.ascontiguousarray(U, dtype=np.float64).reshape(-1)
+    if a.size != 8:
+        raise ValueError("a 2x2 operator needs 8 doubles")
+    return a
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+# ----------------------------------------------------------- raw C calls ----
+# Same names as the C ABI; handles are ctypes.c_void_p.
+
+def qc_state_alloc(n: int, dt: int = QC_C128, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().qc_state_alloc(n, dt, _stream_handle(stream), ctypes.byref(h)))
+    return h
+
+
+def qc_state_wrap(dev_ptr: int, n: int, dt: int, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().qc_state_wrap(ctypes.c_void_p(dev_ptr), n, dt, _stream_handle(stream), ctypes.byref(h)))
+    return h
+
+
+def qc_state_free(h):
+    _check(lib().qc_state_free(h))
+
+
+def qc_state_reset(h, basis: int = 0):
+    _check(lib().qc_state_reset(h, basis))
+
+
+def qc_state_uniform(h):
+    _check(lib().qc_state_uniform(h))
+
+
+def qc_state_set_stream(h, stream):
+    _check(lib().qc_state_set_stream(h, _stream_handle(stream)))
+
+
+def qc_state_invalidate(h):
+    _check(lib().qc_state_invalidate(h))
+
+
+def qc_apply_1q(h, t: int, U):
+    _check(lib().qc_apply_1q(h, t, _dptr(_mat8(U))))
+
+
+def qc_apply_ctrl(h, c: int, t: int, U):
+    _check(lib().qc_apply_ctrl(h, c, t, _dptr(_mat8(U))))
+
+
+def qc_cnot(h, c: int, t: int):
+    _check(lib().qc_cnot(h, c, t))
+
+
+def qc_cphase(h, c: int, t: int, k: int):
+    _check(lib().qc_cphase(h, c, t, k))
+
+
+def qc_swap(h, a: int, b: int):
+    _check(lib().qc_swap(h, a, b))
+
+
+def qc_hall(h):
+    _check(lib().qc_hall(h))
+
+
+def qc_apply_1q_layer(h, U, mask: int):
+    a = np.ascontiguousarray(np.asarray(U, dtype=np.float64).reshape(-1))
+    _check(lib().qc_apply_1q_layer(h, _dptr(a), mask))
+
+
+def _marked(marked) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(marked, dtype=np.uint64).reshape(-1))
+
+
+def qc_grover_step(h, marked):
+    m = _marked(marked)
+    _check(lib().qc_grover_step(h, m.ctypes.data_as(_U64P), len(m)))
+
+
+def qc_grover_run(h, marked, iters: int):
+    m = _marked(marked)
+    _check(lib().qc_grover_run(h, m.ctypes.data_as(_U64P), len(m), iters))
+
+
+def qc_qft(h):
+    _check(lib().qc_qft(h))
+
+
+def qc_norm(h) -> float:
+    out = ctypes.c_double()
+    _check(lib().qc_norm(h, ctypes.byref(out)))
+    return out.value
+
+
+def qc_probs(h, out_dev_ptr: int):
+    _check(lib().qc_probs(h, ctypes.c_void_p(out_dev_ptr)))
+
+
+def qc_expect_pauli(h, xmask: int, zmask: int) -> complex:
+    out = (ctypes.c_double * 2)()
+    _check(lib().qc_expect_pauli(h, xmask, zmask, out))
+    return complex(out[0], out[1])
+
+
+def qc_renormalize(h) -> float:
+    out = ctypes.c_double()
+    _check(lib().qc_renormalize(h, ctypes.byref(out)))
+    return out.value
+
+
+def qc_sample(h, seed: int, shots: int, out_dev_ptr: int):
+    _check(lib().qc_sample(h, seed, shots, ctypes.c_void_p(out_dev_ptr)))
+
+
+# --------------------------------------------------- torch-facing helpers ----
+
+def torch_dtype(dt: int):
+    import torch
+    return torch.complex128 if dt == QC_C128 else torch.complex64
+
+
+class State:
+    """A state vector held in a torch tensor (complex128 or complex64) and
+    wrapped by a qc_state handle.  Methods map one-to-one onto the C ABI."""
+
+    def __init__(self, n: int, dt: int = QC_C128, device="cuda", tensor=None, stream=None):
+        import torch
+        self.n, self.dt = n, dt
+        if tensor is None:
+            tensor = torch.empty(1 << n, dtype=torch_dtype(dt), device=device)
+        assert tensor.is_cuda and tensor.is_contiguous() and tensor.numel() == (1 << n)
+        self.tensor = tensor
+        self.h = qc_state_wrap(tensor.data_ptr(), n, dt, stream)
+        if tensor is not None and stream is None:
+            pass
+
+    def close(self):
+        if self.h is not None:
+            qc_state_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # state preparation
+    def reset(self, basis: int = 0):
+        qc_state_reset(self.h, basis)
+        return self
+
+    def uniform(self):
+        qc_state_uniform(self.h)
+        return self
+
+    def load(self, vec):
+        """Copy a host vector into the state (marks cached reductions stale)."""
+        import torch
+        self.tensor.copy_(torch.as_tensor(np.asarray(vec)).to(self.tensor.dtype))
+        qc_state_invalidate(self.h)
+        return self
+
+    def numpy(self) -> np.ndarray:
+        import torch
+        torch.cuda.synchronize()
+        return self.tensor.cpu().numpy()
+
+    # gates
+    def apply_1q(self, t, U):
+        qc_apply_1q(self.h, t, U)
+
+    def apply_ctrl(self, c, t, U):
+        qc_apply_ctrl(self.h, c, t, U)
+
+    def cnot(self, c, t):
+        qc_cnot(self.h, c, t)
+
+    def cphase(self, c, t, k):
+        qc_cphase(self.h, c, t, k)
+
+    def swap(self, a, b):
+        qc_swap(self.h, a, b)
+
+    def hall(self):
+        qc_hall(self.h)
+
+    def apply_1q_layer(self, U, mask=None):
+        if mask is None:
+            mask = (1 << self.n) - 1
+        qc_apply_1q_layer(self.h, U, mask)
+
+    def grover_step(self, marked):
+        qc_grover_step(self.h, marked)
+
+    def grover_run(self, marked, iters):
+        qc_grover_run(self.h, marked, iters)
+
+    def qft(self):
+        qc_qft(self.h)
+
+    # reductions
+    def norm(self) -> float:
+        return qc_norm(self.h)
+
+    def probs(self):
+        import torch
+        p = torch.empty(1 << self.n, dtype=torch.float64, device=self.tensor.device)
+        qc_probs(self.h, p.data_ptr())
+        return p
+
+    def expect_pauli(self, xmask, zmask) -> complex:
+        return qc_expect_pauli(self.h, xmask, zmask)
+
+    def renormalize(self) -> float:
+        return qc_renormalize(self.h)
+
+    def sample(self, seed, shots):
+        import torch
+        out = torch.empty(max(shots, 1), dtype=torch.int64, device=self.tensor.device)
+        qc_sample(self.h, seed, shots, out.data_ptr())
+        return out[:shots]
+
+
+def version() -> str:
+    return lib().qc_version().decode()
+
+
+def kernel_launches() -> int:
+    """Kernels this library has launched in this process so far."""
+    return int(lib().qc_kernel_launches())

@@ -1,0 +1,250 @@
+// Internal definitions shared by the CUDA translation units of the gate
+// engine: the state handle, error reporting, launch sizing, complex helpers
+// and index arithmetic.  Nothing here is exported.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/qc.h"
+
+#define QC_API extern "C" __attribute__((visibility("default")))
+
+// Device scratch kept per state: running sums, means and block partials.
+// Layout (doubles): [0,2) running amplitude sum, [2,4) Grover mean m,
+// [4,8) misc scalars, [8, 8+2*QC_MAX_MARKED) saved marked amplitudes,
+// then QC_PARTIALS doubles of reduction partials.
+#define QC_SCR_SUM 0
+#define QC_SCR_MEAN 2
+#define QC_SCR_MISC 4
+#define QC_SCR_MARKED 8
+#define QC_SCR_PARTIALS (8 + 2 * QC_MAX_MARKED)
+#define QC_PARTIALS 16384
+#define QC_SCRATCH_DOUBLES (QC_SCR_PARTIALS + QC_PARTIALS)
+
+struct qc_state {
+  void* data;
+  int n;
+  qc_dtype dt;
+  cudaStream_t stream;
+  bool owns;
+  bool sum_valid;  // scratch[QC_SCR_SUM] holds sum_i C_i of the current data
+  int device;
+  double* scratch;  // device, QC_SCRATCH_DOUBLES
+  void* marked_dev;  // device copy of the last Grover marked list (lazy)
+  std::vector<uint64_t> marked_host;  // what marked_dev holds
+};
+
+// ------------------------------------------------------------ errors -----
+namespace qc {
+
+void set_error(const char* fmt, ...);
+void clear_error();
+qc_status cuda_fail(cudaError_t e, const char* what);
+// Checks the last launch and adds `nkernels` (the kernels launched since
+// the previous check) to the process-wide launch counter; returns QC_OK or
+// QC_ECUDA (with message).
+qc_status check_launch(const char* what, int nkernels = 1);
+
+int sm_count();  // SMs of the current device (cached per device)
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Grid for a grid-stride kernel over `items` work items of `per_block`
+// items each, capped at `waves` x SMs blocks.
+inline unsigned grid_for(int64_t items, int per_block, int waves) {
+  int64_t b = ceil_div(items, per_block);
+  int64_t cap = (int64_t)sm_count() * waves;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+// ------------------------------------------------------ index helpers ----
+// Insert a 0 bit at position `pos` of p: bits below pos stay, bits from pos
+// up move one place up.
+__host__ __device__ __forceinline__ uint64_t insert0(uint64_t p, int pos) {
+  const uint64_t lo = p & ((1ull << pos) - 1ull);
+  return ((p >> pos) << (pos + 1)) | lo;
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the
+// multiply-xor round on the 4-word counter, key advanced by the Weyl
+// constants between rounds.
+__host__ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                       uint32_t k0, uint32_t k1, uint32_t out[4]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+// ------------------------------------------------------ complex types ----
+template <typename R> struct CT;
+template <> struct CT<double> {
+  using V2 = double2;
+  __host__ __device__ static V2 make(double a, double b) { return make_double2(a, b); }
+};
+template <> struct CT<float> {
+  using V2 = float2;
+  __host__ __device__ static V2 make(float a, float b) { return make_float2(a, b); }
+};
+
+template <typename R> struct Cx {
+  R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ Cx<R> cmake(R a, R b) {
+  Cx<R> z;
+  z.re = a;
+  z.im = b;
+  return z;
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
+  return cmake<R>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+// a*b + c*d
+template <typename R>
+__device__ __forceinline__ Cx<R> cmul2(Cx<R> a, Cx<R> b, Cx<R> c, Cx<R> d) {
+  R re = a.re * b.re;
+  re = fma(-a.im, b.im, re);
+  re = fma(c.re, d.re, re);
+  re = fma(-c.im, d.im, re);
+  R im = a.re * b.im;
+  im = fma(a.im, b.re, im);
+  im = fma(c.re, d.im, im);
+  im = fma(c.im, d.re, im);
+  return cmake<R>(re, im);
+}
+
+// A 2x2 operator passed by value to kernels.
+template <typename R> struct Mat2 {
+  Cx<R> m[4];  // U00 U01 U10 U11
+};
+
+template <typename R>
+inline Mat2<R> mat_from_host(const double* U) {
+  Mat2<R> M;
+  for (int k = 0; k < 4; ++k) {
+    M.m[k].re = (R)U[2 * k];
+    M.m[k].im = (R)U[2 * k + 1];
+  }
+  return M;
+}
+
+// Structure of a 2x2 operator, decided on exact values on the host.
+enum MatKind {
+  MK_GENERAL = 0,
+  MK_REAL = 1,     // all entries real
+  MK_DIAG = 2,     // U01 = U10 = 0
+  MK_PHASE1 = 3,   // diagonal with U00 = 1: only the bit-1 amplitudes change
+  MK_ANTI = 4,     // U00 = U11 = 0
+  MK_SWAPX = 5,    // U01 = U10 = 1, U00 = U11 = 0 (Pauli X): a pure exchange
+  MK_HAD = 6,      // U00 = U01 = U10 = -U11 = h real
+  MK_IDENT = 7     // identity: nothing to do
+};
+MatKind classify(const double* U);
+
+// Loads / stores of one amplitude.
+template <typename R> struct AmpIO;
+template <> struct AmpIO<double> {
+  __device__ static Cx<double> ld(const double2* p) {
+    double2 v = *p;
+    return cmake<double>(v.x, v.y);
+  }
+  __device__ static void st(double2* p, Cx<double> z) { *p = make_double2(z.re, z.im); }
+};
+template <> struct AmpIO<float> {
+  __device__ static Cx<float> ld(const float2* p) {
+    float2 v = *p;
+    return cmake<float>(v.x, v.y);
+  }
+  __device__ static void st(float2* p, Cx<float> z) { *p = make_float2(z.re, z.im); }
+};
+
+// Apply a structured 2x2 operator to (a0, a1).
+template <typename R, int KIND>
+__device__ __forceinline__ void apply2(const Mat2<R>& U, Cx<R>& a0, Cx<R>& a1) {
+  if (KIND == MK_GENERAL) {
+    Cx<R> b0 = cmul2(U.m[0], a0, U.m[1], a1);
+    Cx<R> b1 = cmul2(U.m[2], a0, U.m[3], a1);
+    a0 = b0;
+    a1 = b1;
+  } else if (KIND == MK_REAL) {
+    const R u00 = U.m[0].re, u01 = U.m[1].re, u10 = U.m[2].re, u11 = U.m[3].re;
+    Cx<R> b0 = cmake<R>(fma(u01, a1.re, u00 * a0.re), fma(u01, a1.im, u00 * a0.im));
+    Cx<R> b1 = cmake<R>(fma(u11, a1.re, u10 * a0.re), fma(u11, a1.im, u10 * a0.im));
+    a0 = b0;
+    a1 = b1;
+  } else if (KIND == MK_DIAG) {
+    a0 = cmul(U.m[0], a0);
+    a1 = cmul(U.m[3], a1);
+  } else if (KIND == MK_PHASE1) {
+    a1 = cmul(U.m[3], a1);
+  } else if (KIND == MK_ANTI) {
+    Cx<R> b0 = cmul(U.m[1], a1);
+    Cx<R> b1 = cmul(U.m[2], a0);
+    a0 = b0;
+    a1 = b1;
+  } else if (KIND == MK_SWAPX) {
+    Cx<R> t = a0;
+    a0 = a1;
+    a1 = t;
+  } else if (KIND == MK_HAD) {
+    // h*(a0+a1), h*(a0-a1) with one product shared: q = h*a1
+    const R h = U.m[0].re;
+    const R qr = h * a1.re, qi = h * a1.im;
+    Cx<R> b0 = cmake<R>(fma(h, a0.re, qr), fma(h, a0.im, qi));
+    Cx<R> b1 = cmake<R>(fma(h, a0.re, -qr), fma(h, a0.im, -qi));
+    a0 = b0;
+    a1 = b1;
+  }
+}
+
+// Bytes per amplitude.
+inline size_t amp_bytes(qc_dtype dt) { return dt == QC_C128 ? 16 : 8; }
+
+// Validation helpers (set the error message and return QC_EINVAL).
+qc_status check_state(const qc_state* s);
+qc_status check_qubit(const qc_state* s, int t, const char* name);
+
+// Launchers implemented in the .cu files.
+qc_status launch_1q(qc_state* s, int t, const double* U);
+qc_status launch_ctrl(qc_state* s, int c, int t, const double* U);
+qc_status launch_swap(qc_state* s, int a, int b);
+qc_status launch_fill_basis(qc_state* s, uint64_t idx);
+qc_status launch_fill_uniform(qc_state* s);
+qc_status launch_hall(qc_state* s);
+qc_status launch_layer(qc_state* s, const double* U, uint64_t mask);
+qc_status launch_qft(qc_state* s);
+qc_status launch_grover_step(qc_state* s, const uint64_t* marked, int m);
+qc_status launch_grover_run(qc_state* s, const uint64_t* marked, int m, int iters);
+qc_status launch_sum(qc_state* s);  // refreshes scratch[QC_SCR_SUM]
+qc_status reduce_norm(const qc_state* s, double* out_host);
+qc_status launch_probs(const qc_state* s, double* out);
+qc_status reduce_expect(const qc_state* s, uint64_t x, uint64_t z, double* out_host);
+qc_status launch_scale(qc_state* s, double f);
+qc_status launch_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_t* out);
+
+}  // namespace qc

@@ -1,0 +1,266 @@
+// Single-gate kernels: one-qubit operators (OneOpA, Eq. resmat1),
+// controlled operators / CNOT / CPHASEK (Eq. resmat2, Eq. cphasek) and SWAP,
+// plus state fills.  Each is one streaming read+write pass over the
+// amplitudes the gate touches, with 128-bit loads and stores and
+// grid-stride loops sized to the SM count.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace qc {
+
+// Enumeration of the pairs a gate updates.  Pair p maps to index i0 by
+// inserting zero bits at positions p0 < p1 (NINS = 1 or 2) and or-ing in
+// `setm` (the control bit); its partner is i1 = i0 | 2^t.
+template <int NINS>
+__device__ __forceinline__ uint64_t pair_base(uint64_t p, int p0, int p1, uint64_t setm) {
+  uint64_t i = insert0(p, p0);
+  if (NINS == 2) i = insert0(i, p1);
+  return i | setm;
+}
+
+// Scalar form: one pair per work item, 16-byte (c128) or 8-byte (c64)
+// accesses.  Two items are processed per loop trip so that four loads are in
+// flight before the first use.
+template <typename R, int KIND, int NINS>
+__global__ void __launch_bounds__(256) k_pairs(typename CT<R>::V2* __restrict__ s, uint64_t npairs,
+                                               int p0, int p1, uint64_t setm, int t, Mat2<R> U) {
+  using IO = AmpIO<R>;
+  const uint64_t st = 1ull << t;
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; p + G < npairs; p += 2 * G) {
+    const uint64_t i0 = pair_base<NINS>(p, p0, p1, setm), j0 = pair_base<NINS>(p + G, p0, p1, setm);
+    Cx<R> a0 = cmake<R>(0, 0), b0 = cmake<R>(0, 0);
+    if (KIND != MK_PHASE1) {
+      a0 = IO::ld(s + i0);
+      b0 = IO::ld(s + j0);
+    }
+    Cx<R> a1 = IO::ld(s + (i0 | st)), b1 = IO::ld(s + (j0 | st));
+    apply2<R, KIND>(U, a0, a1);
+    apply2<R, KIND>(U, b0, b1);
+    if (KIND != MK_PHASE1) {
+      IO::st(s + i0, a0);
+      IO::st(s + j0, b0);
+    }
+    IO::st(s + (i0 | st), a1);
+    IO::st(s + (j0 | st), b1);
+  }
+  if (p < npairs) {
+    const uint64_t i0 = pair_base<NINS>(p, p0, p1, setm);
+    Cx<R> a0 = cmake<R>(0, 0);
+    if (KIND != MK_PHASE1) a0 = IO::ld(s + i0);
+    Cx<R> a1 = IO::ld(s + (i0 | st));
+    apply2<R, KIND>(U, a0, a1);
+    if (KIND != MK_PHASE1) IO::st(s + i0, a0);
+    IO::st(s + (i0 | st), a1);
+  }
+}
+
+// complex64, all inserted bit positions >= 1: two neighbouring pairs per
+// work item share 16-byte loads (amplitudes i0, i0+1 and i1, i1+1).
+template <int KIND, int NINS>
+__global__ void __launch_bounds__(256) k_pairs_v2(float2* __restrict__ s, uint64_t nitems, int p0,
+                                                  int p1, uint64_t setm, int t, Mat2<float> U) {
+  const uint64_t st = 1ull << t;
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nitems; v += G) {
+    const uint64_t i0 = pair_base<NINS>(2 * v, p0, p1, setm);
+    float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B;
+    if (KIND != MK_PHASE1) A = *reinterpret_cast<const float4*>(s + i0);
+    B = *reinterpret_cast<const float4*>(s + (i0 | st));
+    Cx<float> a0 = cmake(A.x, A.y), c0 = cmake(A.z, A.w);
+    Cx<float> a1 = cmake(B.x, B.y), c1 = cmake(B.z, B.w);
+    apply2<float, KIND>(U, a0, a1);
+    apply2<float, KIND>(U, c0, c1);
+    if (KIND != MK_PHASE1) *reinterpret_cast<float4*>(s + i0) = make_float4(a0.re, a0.im, c0.re, c0.im);
+    *reinterpret_cast<float4*>(s + (i0 | st)) = make_float4(a1.re, a1.im, c1.re, c1.im);
+  }
+}
+
+// complex64, one-qubit gate on t = 0: the pair (2q, 2q+1) is one 16-byte
+// vector.
+template <int KIND>
+__global__ void __launch_bounds__(256) k_pairs_t0(float2* __restrict__ s, uint64_t npairs, Mat2<float> U) {
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  float4* v4 = reinterpret_cast<float4*>(s);
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += G) {
+    float4 A = v4[p];
+    Cx<float> a0 = cmake(A.x, A.y), a1 = cmake(A.z, A.w);
+    apply2<float, KIND>(U, a0, a1);
+    v4[p] = make_float4(a0.re, a0.im, a1.re, a1.im);
+  }
+}
+
+template <typename R, int KIND>
+static void launch_kind(qc_state* s, int nins, int p0, int p1, uint64_t setm, int t, const Mat2<R>& U) {
+  using V2 = typename CT<R>::V2;
+  const uint64_t npairs = (1ull << s->n) >> nins;
+  V2* d = reinterpret_cast<V2*>(s->data);
+  const int T = 256;
+  if constexpr (sizeof(R) == 4) {
+    if (nins == 1 && t == 0) {
+      k_pairs_t0<KIND><<<grid_for(npairs, T, 8), T, 0, s->stream>>>(d, npairs, U);
+      return;
+    }
+    if (p0 >= 1 && npairs >= 2) {
+      const uint64_t items = npairs / 2;
+      if (nins == 1)
+        k_pairs_v2<KIND, 1><<<grid_for(items, T, 8), T, 0, s->stream>>>(d, items, p0, p1, setm, t, U);
+      else
+        k_pairs_v2<KIND, 2><<<grid_for(items, T, 8), T, 0, s->stream>>>(d, items, p0, p1, setm, t, U);
+      return;
+    }
+  }
+  if (nins == 1)
+    k_pairs<R, KIND, 1><<<grid_for(npairs, 2 * T, 8), T, 0, s->stream>>>(d, npairs, p0, p1, setm, t, U);
+  else
+    k_pairs<R, KIND, 2><<<grid_for(npairs, 2 * T, 8), T, 0, s->stream>>>(d, npairs, p0, p1, setm, t, U);
+}
+
+template <typename R>
+static void launch_pairs(qc_state* s, int nins, int p0, int p1, uint64_t setm, int t, const double* Uh) {
+  const Mat2<R> U = mat_from_host<R>(Uh);
+  switch (classify(Uh)) {
+    case MK_IDENT: return;
+    case MK_GENERAL: launch_kind<R, MK_GENERAL>(s, nins, p0, p1, setm, t, U); return;
+    case MK_REAL: launch_kind<R, MK_REAL>(s, nins, p0, p1, setm, t, U); return;
+    case MK_DIAG: launch_kind<R, MK_DIAG>(s, nins, p0, p1, setm, t, U); return;
+    case MK_PHASE1: launch_kind<R, MK_PHASE1>(s, nins, p0, p1, setm, t, U); return;
+    case MK_ANTI: launch_kind<R, MK_ANTI>(s, nins, p0, p1, setm, t, U); return;
+    case MK_SWAPX: launch_kind<R, MK_SWAPX>(s, nins, p0, p1, setm, t, U); return;
+    case MK_HAD: launch_kind<R, MK_HAD>(s, nins, p0, p1, setm, t, U); return;
+  }
+}
+
+qc_status launch_1q(qc_state* s, int t, const double* U) {
+  if (s->dt == QC_C128) launch_pairs<double>(s, 1, t, 0, 0, t, U);
+  else launch_pairs<float>(s, 1, t, 0, 0, t, U);
+  s->sum_valid = false;
+  return check_launch("apply_1q", classify(U) == MK_IDENT ? 0 : 1);
+}
+
+qc_status launch_ctrl(qc_state* s, int c, int t, const double* U) {
+  const int p0 = std::min(c, t), p1 = std::max(c, t);
+  const uint64_t setm = 1ull << c;
+  if (s->dt == QC_C128) launch_pairs<double>(s, 2, p0, p1, setm, t, U);
+  else launch_pairs<float>(s, 2, p0, p1, setm, t, U);
+  s->sum_valid = false;
+  return check_launch("apply_ctrl", classify(U) == MK_IDENT ? 0 : 1);
+}
+
+// SWAP: amplitudes with (bit a, bit b) = (1, 0) and (0, 1) trade places.
+template <typename V2>
+__global__ void __launch_bounds__(256) k_swap(V2* __restrict__ s, uint64_t nq, int lo, int hi, int a, int b) {
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += G) {
+    const uint64_t base = insert0(insert0(q, lo), hi);
+    const uint64_t ia = base | (1ull << a), ib = base | (1ull << b);
+    const V2 x = s[ia], y = s[ib];
+    s[ia] = y;
+    s[ib] = x;
+  }
+}
+
+// complex64 with both bits >= 1: two neighbouring quartets per item.
+__global__ void __launch_bounds__(256) k_swap_v2(float2* __restrict__ s, uint64_t nitems, int lo, int hi, int a, int b) {
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nitems; v += G) {
+    const uint64_t base = insert0(insert0(2 * v, lo), hi);
+    float4* pa = reinterpret_cast<float4*>(s + (base | (1ull << a)));
+    float4* pb = reinterpret_cast<float4*>(s + (base | (1ull << b)));
+    const float4 x = *pa, y = *pb;
+    *pa = y;
+    *pb = x;
+  }
+}
+
+qc_status launch_swap(qc_state* s, int a, int b) {
+  const int lo = std::min(a, b), hi = std::max(a, b);
+  const uint64_t nq = (1ull << s->n) >> 2;
+  const int T = 256;
+  if (s->dt == QC_C128) {
+    k_swap<double2><<<grid_for(nq, T, 8), T, 0, s->stream>>>(reinterpret_cast<double2*>(s->data), nq, lo, hi, a, b);
+  } else if (lo >= 1 && nq >= 2) {
+    k_swap_v2<<<grid_for(nq / 2, T, 8), T, 0, s->stream>>>(reinterpret_cast<float2*>(s->data), nq / 2, lo, hi, a, b);
+  } else {
+    k_swap<float2><<<grid_for(nq, T, 8), T, 0, s->stream>>>(reinterpret_cast<float2*>(s->data), nq, lo, hi, a, b);
+  }
+  s->sum_valid = false;
+  return check_launch("swap");
+}
+
+// ------------------------------------------------------------ fills ------
+// Every amplitude = v; the running sum N * v goes to the scratch.
+template <typename V2>
+__global__ void k_fill(V2* __restrict__ s, uint64_t N, V2 v, double* scratch) {
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += G) s[i] = v;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    scratch[QC_SCR_SUM] = (double)N * (double)v.x;
+    scratch[QC_SCR_SUM + 1] = (double)N * (double)v.y;
+  }
+}
+// Writes the single nonzero amplitude and records the running sum (1) in the
+// state's scratch.
+template <typename V2>
+__global__ void k_set_one(V2* __restrict__ s, uint64_t idx, V2 v, double* scratch) {
+  s[idx] = v;
+  scratch[QC_SCR_SUM] = 1.0;
+  scratch[QC_SCR_SUM + 1] = 0.0;
+}
+
+qc_status launch_fill_basis(qc_state* s, uint64_t idx) {
+  const size_t bytes = ((size_t)1 << s->n) * amp_bytes(s->dt);
+  cudaError_t e = cudaMemsetAsync(s->data, 0, bytes, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  if (s->dt == QC_C128)
+    k_set_one<double2><<<1, 1, 0, s->stream>>>(reinterpret_cast<double2*>(s->data), idx,
+                                               make_double2(1.0, 0.0), s->scratch);
+  else
+    k_set_one<float2><<<1, 1, 0, s->stream>>>(reinterpret_cast<float2*>(s->data), idx,
+                                              make_float2(1.f, 0.f), s->scratch);
+  s->sum_valid = true;
+  return check_launch("fill_basis");
+}
+
+qc_status launch_fill_uniform(qc_state* s) {
+  const uint64_t N = 1ull << s->n;
+  const double a = 1.0 / sqrt(ldexp(1.0, s->n));  // 2^{-n/2}
+  const int T = 256;
+  if (s->dt == QC_C128)
+    k_fill<double2><<<grid_for(N, T, 8), T, 0, s->stream>>>(reinterpret_cast<double2*>(s->data), N,
+                                                            make_double2(a, 0.0), s->scratch);
+  else
+    k_fill<float2><<<grid_for(N, T, 8), T, 0, s->stream>>>(reinterpret_cast<float2*>(s->data), N,
+                                                           make_float2((float)a, 0.f), s->scratch);
+  qc_status st = check_launch("fill_uniform");
+  s->sum_valid = (st == QC_OK);
+  return st;
+}
+
+// Real scale of every amplitude.
+template <typename R>
+__global__ void k_scale(typename CT<R>::V2* __restrict__ s, uint64_t N, R f) {
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += G) {
+    auto v = s[i];
+    v.x *= f;
+    v.y *= f;
+    s[i] = v;
+  }
+}
+
+qc_status launch_scale(qc_state* s, double f) {
+  const uint64_t N = 1ull << s->n;
+  const int T = 256;
+  if (s->dt == QC_C128)
+    k_scale<double><<<grid_for(N, T, 8), T, 0, s->stream>>>(reinterpret_cast<double2*>(s->data), N, f);
+  else
+    k_scale<float><<<grid_for(N, T, 8), T, 0, s->stream>>>(reinterpret_cast<float2*>(s->data), N, (float)f);
+  s->sum_valid = false;
+  return check_launch("scale");
+}
+
+}  // namespace qc

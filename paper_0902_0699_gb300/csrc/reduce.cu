@@ -1,0 +1,394 @@
+// Reductions with FP64 accumulation: the amplitude sum (for Grover's mean),
+// the norm sum |C|^2 (sec. 2), Born-rule probabilities, Pauli expectation
+// values, and the seeded integer-CDF measurement sampler.
+//
+// Partial sums go to per-block slots in the state's scratch and are added
+// in block order by one final block, so every result is deterministic for a
+// given launch shape.  complex64 squares are formed exactly with the FP32
+// two-product (x*x = p + e, e = fma(x, x, -p)) and accumulated as float
+// pairs over short runs before they are added in FP64.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace qc {
+
+#define RED_T 256
+#define RED_MAXB (QC_PARTIALS / 2)
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of two doubles; result valid in thread 0.
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double sa[32], sb[32];
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0, y = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      x += sa[i];
+      y += sb[i];
+    }
+    a = x;
+    b = y;
+  }
+  __syncthreads();
+}
+
+// Sum of the partial pairs written by `nb` blocks, in block order.
+__global__ void k_final2(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    a += part[2 * i];
+    b += part[2 * i + 1];
+  }
+  block_sum2(a, b);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    out[1] = b;
+  }
+}
+
+// float-float accumulator: (s, c) += (p, e) via two-sum.
+__device__ __forceinline__ void ff_acc(float& s, float& c, float p, float e) {
+  const float t = s + p;
+  const float bp = t - s;
+  const float err = (s - (t - bp)) + (p - bp);
+  s = t;
+  c += err + e;
+}
+
+// ---------------------------------------------------------------- sum ----
+template <typename R>
+__global__ void __launch_bounds__(RED_T) k_sum(const typename CT<R>::V2* __restrict__ s, uint64_t N,
+                                               double* __restrict__ part) {
+  double a = 0.0, b = 0.0;
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += G) {
+    const auto v = s[i];
+    a += (double)v.x;
+    b += (double)v.y;
+  }
+  block_sum2(a, b);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+  }
+}
+
+qc_status launch_sum(qc_state* s) {
+  const uint64_t N = 1ull << s->n;
+  const unsigned nb = std::min<unsigned>(grid_for(N, RED_T * 4, 8), RED_MAXB);
+  double* part = s->scratch + QC_SCR_PARTIALS;
+  if (s->dt == QC_C128)
+    k_sum<double><<<nb, RED_T, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), N, part);
+  else
+    k_sum<float><<<nb, RED_T, 0, s->stream>>>(reinterpret_cast<const float2*>(s->data), N, part);
+  k_final2<<<1, RED_T, 0, s->stream>>>(part, nb, s->scratch + QC_SCR_SUM);
+  qc_status st = check_launch("amplitude sum", 2);
+  if (!st) s->sum_valid = true;
+  return st;
+}
+
+// --------------------------------------------------------------- norm ----
+__global__ void __launch_bounds__(RED_T) k_norm_c128(const double2* __restrict__ s, uint64_t N,
+                                                     double* __restrict__ part) {
+  double a = 0.0;
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += G) {
+    const double2 v = s[i];
+    a = fma(v.x, v.x, a);
+    a = fma(v.y, v.y, a);
+  }
+  double b = 0.0;
+  block_sum2(a, b);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = 0.0;
+  }
+}
+
+// complex64: exact FP32 squares, float-pair runs of 8 vectors (16 amps),
+// FP64 across runs.
+__global__ void __launch_bounds__(RED_T) k_norm_c64(const float4* __restrict__ s, uint64_t N2,
+                                                    double* __restrict__ part) {
+  double acc = 0.0;
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  while (i < N2) {
+    float hs = 0.f, hc = 0.f;
+#pragma unroll 1
+    for (int r = 0; r < 8 && i < N2; ++r, i += G) {
+      const float4 v = s[i];
+      const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float p = x[k] * x[k];
+        ff_acc(hs, hc, p, fmaf(x[k], x[k], -p));
+      }
+    }
+    acc += (double)hs + (double)hc;
+  }
+  double b = 0.0;
+  block_sum2(acc, b);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = acc;
+    part[2 * blockIdx.x + 1] = 0.0;
+  }
+}
+
+qc_status reduce_norm(const qc_state* s, double* out_host) {
+  const uint64_t N = 1ull << s->n;
+  double* part = s->scratch + QC_SCR_PARTIALS;
+  unsigned nb;
+  if (s->dt == QC_C128) {
+    nb = std::min<unsigned>(grid_for(N, RED_T * 4, 8), RED_MAXB);
+    k_norm_c128<<<nb, RED_T, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), N, part);
+  } else {  // n >= 1, so N / 2 >= 1 vectors of two amplitudes
+    nb = std::min<unsigned>(grid_for(N / 2, RED_T * 4, 8), RED_MAXB);
+    k_norm_c64<<<nb, RED_T, 0, s->stream>>>(reinterpret_cast<const float4*>(s->data), N / 2, part);
+  }
+  k_final2<<<1, RED_T, 0, s->stream>>>(part, nb, s->scratch + QC_SCR_MISC);
+  qc_status st = check_launch("norm", 2);
+  if (st) return st;
+  double h[2];
+  cudaError_t e = cudaMemcpyAsync(h, s->scratch + QC_SCR_MISC, sizeof h, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "norm readback");
+  *out_host = h[0];
+  return QC_OK;
+}
+
+// -------------------------------------------------------------- probs ----
+// p_i = re*re + im*im, each product and the sum rounded on its own (the
+// same operations as the FP64 reference; complex64 inputs are widened
+// first, which makes the products exact).
+template <typename R>
+__device__ __forceinline__ double prob_of(typename CT<R>::V2 v) {
+  const double re = (double)v.x, im = (double)v.y;
+  return __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
+}
+
+template <typename R>
+__global__ void __launch_bounds__(RED_T) k_probs(const typename CT<R>::V2* __restrict__ s, uint64_t N,
+                                                 double* __restrict__ p) {
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += G) p[i] = prob_of<R>(s[i]);
+}
+
+qc_status launch_probs(const qc_state* s, double* out) {
+  const uint64_t N = 1ull << s->n;
+  if (s->dt == QC_C128)
+    k_probs<double><<<grid_for(N, RED_T, 8), RED_T, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), N, out);
+  else
+    k_probs<float><<<grid_for(N, RED_T, 8), RED_T, 0, s->stream>>>(reinterpret_cast<const float2*>(s->data), N, out);
+  return check_launch("probs");
+}
+
+// ------------------------------------------------------------- expect ----
+// <psi|P|psi> = sum_j conj(C[j^x]) i^{|x&z|} (-1)^{|j&z|} C[j].
+template <typename R>
+__global__ void __launch_bounds__(RED_T) k_expect(const typename CT<R>::V2* __restrict__ s, uint64_t N,
+                                                  uint64_t x, uint64_t z, double* __restrict__ part) {
+  double ar = 0.0, ai = 0.0;
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += G) {
+    const auto v = s[j];
+    const auto w = s[j ^ x];
+    double vr = (double)v.x, vi = (double)v.y;
+    if (__popcll(j & z) & 1) {
+      vr = -vr;
+      vi = -vi;
+    }
+    const double wr = (double)w.x, wi = (double)w.y;
+    ar = fma(wr, vr, ar);
+    ar = fma(wi, vi, ar);
+    ai = fma(wr, vi, ai);
+    ai = fma(-wi, vr, ai);
+  }
+  block_sum2(ar, ai);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = ar;
+    part[2 * blockIdx.x + 1] = ai;
+  }
+}
+
+qc_status reduce_expect(const qc_state* s, uint64_t x, uint64_t z, double* out_host) {
+  const uint64_t N = 1ull << s->n;
+  double* part = s->scratch + QC_SCR_PARTIALS;
+  const unsigned nb = std::min<unsigned>(grid_for(N, RED_T * 4, 8), RED_MAXB);
+  if (s->dt == QC_C128)
+    k_expect<double><<<nb, RED_T, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), N, x, z, part);
+  else
+    k_expect<float><<<nb, RED_T, 0, s->stream>>>(reinterpret_cast<const float2*>(s->data), N, x, z, part);
+  k_final2<<<1, RED_T, 0, s->stream>>>(part, nb, s->scratch + QC_SCR_MISC);
+  qc_status st = check_launch("expect", 2);
+  if (st) return st;
+  double h[2];
+  cudaError_t e = cudaMemcpyAsync(h, s->scratch + QC_SCR_MISC, sizeof h, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "expect readback");
+  // multiply by i^{|x&z|}
+  const int ny = __builtin_popcountll(x & z) & 3;
+  const double r = h[0], i = h[1];
+  const double rr[4] = {r, -i, -r, i}, ii[4] = {i, r, -i, -r};
+  out_host[0] = rr[ny];
+  out_host[1] = ii[ny];
+  return QC_OK;
+}
+
+// ------------------------------------------------------------ sampler ----
+// w_i = trunc(p_i * 2^62); W = inclusive prefix sum (exact integers, so the
+// parallel order does not matter); shot s: target = floor(r * W_{N-1} /
+// 2^64), outcome = smallest i with W_i > target.
+#define SMP_PER 8
+#define SMP_T 256
+#define SMP_BLOCK (SMP_PER * SMP_T)
+
+template <typename R>
+__device__ __forceinline__ uint64_t weight_of(typename CT<R>::V2 v) {
+  const double p = prob_of<R>(v);
+  return __double2ull_rz(p * 4611686018427387904.0);
+}
+
+__device__ __forceinline__ uint64_t block_excl_scan_u64(uint64_t v, uint64_t* total) {
+  __shared__ uint64_t ws[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint64_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    uint64_t t = lane < nw ? ws[lane] : 0ull;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    ws[lane] = t;  // inclusive over warps
+  }
+  __syncthreads();
+  const uint64_t warp_off = w ? ws[w - 1] : 0ull;
+  if (total) *total = ws[(blockDim.x >> 5) - 1];
+  const uint64_t r = warp_off + x - v;
+  __syncthreads();
+  return r;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(SMP_T) k_wsum(const typename CT<R>::V2* __restrict__ s, uint64_t N,
+                                                uint64_t* __restrict__ bsum) {
+  const uint64_t base = (uint64_t)blockIdx.x * SMP_BLOCK;
+  uint64_t t = 0;
+  for (int k = 0; k < SMP_PER; ++k) {
+    const uint64_t i = base + (uint64_t)k * SMP_T + threadIdx.x;
+    if (i < N) t += weight_of<R>(s[i]);
+  }
+  uint64_t tot = 0;
+  block_excl_scan_u64(t, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the block sums, one block.
+__global__ void __launch_bounds__(1024) k_scan_bsum(uint64_t* __restrict__ bsum, uint64_t nb) {
+  const uint64_t per = (nb + blockDim.x - 1) / blockDim.x;
+  const uint64_t lo = (uint64_t)threadIdx.x * per;
+  uint64_t t = 0;
+  for (uint64_t i = lo; i < lo + per && i < nb; ++i) t += bsum[i];
+  uint64_t off = block_excl_scan_u64(t, nullptr);
+  for (uint64_t i = lo; i < lo + per && i < nb; ++i) {
+    const uint64_t v = bsum[i];
+    bsum[i] = off;
+    off += v;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(SMP_T) k_wcdf(const typename CT<R>::V2* __restrict__ s, uint64_t N,
+                                                const uint64_t* __restrict__ boff, uint64_t* __restrict__ cdf) {
+  // thread owns SMP_PER consecutive elements
+  const uint64_t base = (uint64_t)blockIdx.x * SMP_BLOCK + (uint64_t)threadIdx.x * SMP_PER;
+  uint64_t w[SMP_PER];
+  uint64_t t = 0;
+#pragma unroll
+  for (int k = 0; k < SMP_PER; ++k) {
+    const uint64_t i = base + k;
+    w[k] = i < N ? weight_of<R>(s[i]) : 0ull;
+    t += w[k];
+  }
+  uint64_t run = boff[blockIdx.x] + block_excl_scan_u64(t, nullptr);
+#pragma unroll
+  for (int k = 0; k < SMP_PER; ++k) {
+    const uint64_t i = base + k;
+    run += w[k];
+    if (i < N) cdf[i] = run;
+  }
+}
+
+__global__ void k_sample(const uint64_t* __restrict__ cdf, uint64_t N, uint64_t seed, int64_t shots,
+                         uint64_t* __restrict__ out) {
+  const uint64_t total = cdf[N - 1];
+  for (int64_t sh = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sh < shots;
+       sh += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t x[4];
+    philox4x32_10((uint32_t)(uint64_t)sh, (uint32_t)((uint64_t)sh >> 32), 0u, 0u, (uint32_t)seed,
+                  (uint32_t)(seed >> 32), x);
+    const uint64_t r = ((uint64_t)x[0] << 32) | x[1];
+    const uint64_t target = __umul64hi(r, total);
+    uint64_t lo = 0, hi = N - 1;  // answer in [lo, hi]; cdf[N-1] = total > target
+    while (lo < hi) {
+      const uint64_t mid = lo + ((hi - lo) >> 1);
+      if (cdf[mid] > target) hi = mid;
+      else lo = mid + 1;
+    }
+    out[sh] = lo;
+  }
+}
+
+qc_status launch_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_t* out) {
+  double nrm = 0.0;
+  qc_status st = reduce_norm(s, &nrm);
+  if (st) return st;
+  if (!(nrm <= 2.0) || !(nrm > 0.0)) {
+    set_error("sampling needs 0 < sum |C|^2 <= 2 (got %g)", nrm);
+    return QC_EINVAL;
+  }
+  const uint64_t N = 1ull << s->n;
+  const uint64_t nb = (N + SMP_BLOCK - 1) / SMP_BLOCK;
+  uint64_t* buf = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&buf, (N + nb) * sizeof(uint64_t), s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sampler buffer");
+  uint64_t* cdf = buf;
+  uint64_t* bsum = buf + N;
+  if (s->dt == QC_C128) {
+    const double2* d = reinterpret_cast<const double2*>(s->data);
+    k_wsum<double><<<(unsigned)nb, SMP_T, 0, s->stream>>>(d, N, bsum);
+    k_scan_bsum<<<1, 1024, 0, s->stream>>>(bsum, nb);
+    k_wcdf<double><<<(unsigned)nb, SMP_T, 0, s->stream>>>(d, N, bsum, cdf);
+  } else {
+    const float2* d = reinterpret_cast<const float2*>(s->data);
+    k_wsum<float><<<(unsigned)nb, SMP_T, 0, s->stream>>>(d, N, bsum);
+    k_scan_bsum<<<1, 1024, 0, s->stream>>>(bsum, nb);
+    k_wcdf<float><<<(unsigned)nb, SMP_T, 0, s->stream>>>(d, N, bsum, cdf);
+  }
+  const unsigned g = (unsigned)std::min<int64_t>((shots + 255) / 256, (int64_t)sm_count() * 8);
+  k_sample<<<g, 256, 0, s->stream>>>(cdf, N, seed, shots, out);
+  st = check_launch("sample", 4);
+  cudaFreeAsync(buf, s->stream);
+  return st;
+}
+
+}  // namespace qc

@@ -1,0 +1,183 @@
+"""GPU parity of the adjoint gradient and of the batched noisy trajectories
+against the CPU oracle, through the C ABI."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qc():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_0902_0699_gb300 as q
+    q.lib()
+    return q
+
+
+def ansatz_gate_array(qc, circ):
+    gates = []
+    for g in O.ansatz_gates(circ):
+        if g[0] == "cnot":
+            gates.append((qc.QC_G_CNOT, g[1], g[2], 0))
+        else:
+            gates.append((qc.QC_G_RY if g[0] == "ry" else qc.QC_G_RZ, g[1], 0, g[2]))
+    arr = (qc.Gate * len(gates))(*[qc.Gate(*t) for t in gates])
+    return arr, len(gates)
+
+
+def terms_array(qc, terms):
+    return (qc.PauliTerm * len(terms))(*[qc.PauliTerm(x, z, c) for (x, z, c) in terms])
+
+
+def run_adjoint(qc, circs, dt):
+    import torch
+    n = circs[0].n
+    B = len(circs)
+    P = circs[0].n_params
+    theta = torch.tensor(np.stack([c.theta for c in circs]), dtype=torch.float64, device="cuda")
+    cdt = torch.complex128 if dt == 0 else torch.complex64
+    psi = torch.empty(B << n, dtype=cdt, device="cuda")
+    lam = torch.empty_like(psi)
+    E = torch.empty(B, dtype=torch.float64, device="cuda")
+    grad = torch.empty(B, P, dtype=torch.float64, device="cuda")
+    gates, ng = ansatz_gate_array(qc, circs[0])
+    terms = W.ansatz_hamiltonian(n)
+    st = torch.cuda.current_stream().cuda_stream
+    rc = qc.lib().qc_adjoint_grad(n, dt, B, gates, ng, ctypes.c_void_p(theta.data_ptr()), P, P,
+                                  terms_array(qc, terms), len(terms), ctypes.c_void_p(psi.data_ptr()),
+                                  ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(E.data_ptr()),
+                                  ctypes.c_void_p(grad.data_ptr()), ctypes.c_void_p(st))
+    assert rc == 0, qc.last_error()
+    torch.cuda.synchronize()
+    return E.cpu().numpy(), grad.cpu().numpy(), psi.cpu().numpy().reshape(B, -1)
+
+
+def run_forward(qc, circs, dt):
+    import torch
+    n, B, P = circs[0].n, len(circs), circs[0].n_params
+    theta = torch.tensor(np.stack([c.theta for c in circs]), dtype=torch.float64, device="cuda")
+    cdt = torch.complex128 if dt == 0 else torch.complex64
+    psi = torch.empty(B << n, dtype=cdt, device="cuda")
+    gates, ng = ansatz_gate_array(qc, circs[0])
+    rc = qc.lib().qc_circuit_forward(n, dt, B, gates, ng, ctypes.c_void_p(theta.data_ptr()), P,
+                                     ctypes.c_void_p(psi.data_ptr()),
+                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, qc.last_error()
+    torch.cuda.synchronize()
+    return psi.cpu().numpy().reshape(B, -1)
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_forward_vs_oracle(qc, dt):
+    circs = W.ansatz(8, 4, seed=5, batch=3)
+    got = run_forward(qc, circs, dt)
+    for b, c in enumerate(circs):
+        ref = O.ansatz_forward(c)
+        assert np.max(np.abs(got[b] - ref)) <= (1e-12 if dt == 0 else 1e-5)
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_adjoint_small_all_angles(qc, dt):
+    circs = W.ansatz(6, 5, seed=11, batch=2)
+    E, g, psi = run_adjoint(qc, circs, dt)
+    terms = W.ansatz_hamiltonian(6)
+    for b, c in enumerate(circs):
+        Er, gr = O.adjoint_gradient(c, terms)
+        tol = 1e-12 if dt == 0 else 2e-5
+        assert abs(E[b] - Er) <= tol
+        assert np.max(np.abs(g[b] - gr)) <= tol
+        # uncomputation returns psi to |0..0>
+        assert abs(psi[b][0] - 1) <= (1e-11 if dt == 0 else 1e-4)
+
+
+def test_adjoint_n20_sampled_angles_param_shift(qc):
+    # full-size circuit (n = 20, 50 layers, 2000 angles), complex128; the
+    # oracle's adjoint for all angles, plus parameter shift on a sample
+    circs = W.ansatz(20, 50, seed=0, batch=1)
+    E, g, _ = run_adjoint(qc, circs, 0)
+    terms = W.ansatz_hamiltonian(20)
+    Er, gr = O.adjoint_gradient(circs[0], terms)
+    assert abs(E[0] - Er) <= 1e-11
+    assert np.max(np.abs(g[0] - gr)) <= 1e-11
+    rng = W.rng(99)
+    c = circs[0]
+    for k in rng.choice(c.n_params, 3, replace=False):
+        tp, tm = c.theta.copy(), c.theta.copy()
+        tp[k] += math.pi / 2
+        tm[k] -= math.pi / 2
+        ps = 0.5 * (O.energy(O.ansatz_forward(c, tp), 20, terms) - O.energy(O.ansatz_forward(c, tm), 20, terms))
+        assert abs(g[0][k] - ps) <= 1e-10
+
+
+def test_adjoint_c64_batch_vs_c128(qc):
+    circs = W.ansatz(12, 10, seed=3, batch=4)
+    E64, g64, _ = run_adjoint(qc, circs, 1)
+    E128, g128, _ = run_adjoint(qc, circs, 0)
+    assert np.max(np.abs(E64 - E128)) <= 1e-5
+    assert np.max(np.abs(g64 - g128)) <= 1e-5
+
+
+def run_traj(qc, tb, autotune=0):
+    import torch
+    n_inst = len(tb.nq)
+    nq = np.ascontiguousarray(tb.nq, dtype=np.int32)
+    mk = np.ascontiguousarray(tb.marked, dtype=np.uint64)
+    it = np.ascontiguousarray(tb.iters, dtype=np.int32)
+    d = qc.TrajDesc(n_inst, nq.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                    mk.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                    it.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), tb.seed, tb.thr_gate,
+                    tb.thr_readout, tb.p_readout)
+    plan = ctypes.c_void_p()
+    st = torch.cuda.current_stream().cuda_stream
+    rc = qc.lib().qc_traj_plan_create(ctypes.byref(d), ctypes.c_void_p(st), autotune, ctypes.byref(plan))
+    assert rc == 0, qc.last_error()
+    ps = torch.empty(n_inst, dtype=torch.float64, device="cuda")
+    pr = torch.empty_like(ps)
+    oc = torch.empty(n_inst, dtype=torch.int64, device="cuda")
+    ne = torch.empty(n_inst, dtype=torch.int32, device="cuda")
+    out = qc.TrajOut(ps.data_ptr(), pr.data_ptr(), oc.data_ptr(), ne.data_ptr())
+    for _ in range(2):  # second run replays the captured graph
+        rc = qc.lib().qc_traj_plan_run(plan, ctypes.byref(out))
+        assert rc == 0, qc.last_error()
+    torch.cuda.synchronize()
+    info = [ctypes.c_int(), ctypes.c_int(), ctypes.c_int()]
+    qc.lib().qc_traj_plan_info(plan, *[ctypes.byref(x) for x in info])
+    qc.lib().qc_traj_plan_free(plan)
+    return (ps.cpu().numpy(), pr.cpu().numpy(), oc.cpu().numpy().astype(np.uint64),
+            ne.cpu().numpy(), [x.value for x in info])
+
+
+def test_traj_noiseless_closed_form(qc):
+    tb = W.trajectory_batch(24, 6, 12, seed=4, p_gate=0.0, p_readout=0.0)
+    ps, pr, oc, ne, _ = run_traj(qc, tb)
+    for i in range(len(tb.nq)):
+        n, k = int(tb.nq[i]), int(tb.iters[i])
+        ref = math.sin((2 * k + 1) * math.asin(2 ** (-n / 2))) ** 2
+        assert abs(ps[i] - ref) <= 1e-5
+        assert abs(pr[i] - ref) <= 1e-5
+        assert ne[i] == 0
+
+
+@pytest.mark.parametrize("p", [1e-3, 2e-2])
+def test_traj_replay_vs_oracle(qc, p):
+    # the oracle replays every trajectory's Philox draws literally
+    tb = W.trajectory_batch(40, 5, 10, seed=17, p_gate=p, p_readout=0.05)
+    ps, pr, oc, ne, info = run_traj(qc, tb, autotune=1)
+    mism = 0
+    for i in range(len(tb.nq)):
+        n, m, k = int(tb.nq[i]), int(tb.marked[i]), int(tb.iters[i])
+        psi, errs = O.trajectory_run(n, m, k, tb.seed, i, tb.thr_gate)
+        assert ne[i] == errs
+        prob = O.probs(psi, n)
+        assert abs(ps[i] - prob[m] / prob.sum()) <= 1e-5
+        assert abs(pr[i] - O.readout_success(prob, n, m, tb.p_readout) / prob.sum()) <= 1e-5
+        if int(oc[i]) != O.trajectory_measure(prob, n, tb.seed, i, tb.thr_readout):
+            mism += 1
+    assert mism <= 1  # complex64 vs complex128 weights may split a CDF boundary

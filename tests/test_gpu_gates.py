@@ -1,0 +1,240 @@
+"""GPU parity of the gate kernels against the CPU oracle, element by
+element, through the C ABI.  Tolerances: max |d amp| <= 1e-12 (complex128),
+<= 1e-5 (complex64); permutations (CNOT, SWAP) bit-exact."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def qc():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_0902_0699_gb300 as q
+    q.lib()
+    return q
+
+
+def mk(qc, n, dt, vec=None, seed=0):
+    s = qc.State(n, dt)
+    if vec is None:
+        vec = W.random_state(W.rng(seed), n)
+    s.load(vec)
+    return s, np.asarray(vec, dtype=np.complex128)
+
+
+def as_dt(v, dt):
+    return v.astype(np.complex64).astype(np.complex128) if dt == 1 else v
+
+
+MATS = {
+    "haar": lambda g: W.haar_u2(g, 1)[0],
+    "ry": lambda g: O._mat(O.ry(g.random() * 6.3)),
+    "rz": lambda g: O._mat(O.rz(g.random() * 6.3)),
+    "phase": lambda g: O._mat(np.diag([1, np.exp(1j * g.random() * 6.3)])),
+    "x": lambda g: O._mat(O.X_MAT),
+    "y": lambda g: O._mat(O.Y_MAT),
+    "h": lambda g: O._mat(O.H_MAT),
+    "ident": lambda g: O._mat(np.eye(2, dtype=np.complex128)),
+}
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n", [1, 2, 3, 6, 13, 17])
+@pytest.mark.parametrize("kind", list(MATS))
+def test_apply_1q_all_t(qc, dt, n, kind):
+    g = W.rng(hash((n, kind)) % 1000)
+    s, v = mk(qc, n, dt, seed=n)
+    ref = as_dt(v, dt).copy()
+    for t in range(n):
+        U = MATS[kind](g)
+        s.apply_1q(t, U)
+        O.apply_1q(ref, n, t, U)
+    got = s.numpy()
+    assert np.max(np.abs(got - ref)) <= TOL[dt] * max(1, n / 4)
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_ctrl_cnot_cphase_swap_all_pairs(qc, dt):
+    n = 6
+    g = W.rng(7)
+    s, v = mk(qc, n, dt, seed=3)
+    ref = as_dt(v, dt).copy()
+    for c in range(n):
+        for t in range(n):
+            if c == t:
+                continue
+            U = W.haar_u2(g, 1)[0]
+            s.apply_ctrl(c, t, U)
+            O.apply_ctrl(ref, n, c, t, U)
+            s.cphase(c, t, 1 + (c + t) % 5)
+            O.cphase(ref, n, c, t, 1 + (c + t) % 5)
+    got = s.numpy()
+    assert np.max(np.abs(got - ref)) <= TOL[dt] * 4
+    # permutations are bit-exact
+    s2, v2 = mk(qc, n, dt, seed=4)
+    r2 = as_dt(v2, dt).copy()
+    for c in range(n):
+        for t in range(n):
+            if c != t:
+                s2.cnot(c, t)
+                O.cnot(r2, n, c, t)
+                s2.swap(c, t)
+                O.swap(r2, n, c, t)
+    assert np.array_equal(s2.numpy(), r2)
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n", [12, 18])
+def test_ctrl_large(qc, dt, n):
+    g = W.rng(n)
+    s, v = mk(qc, n, dt, seed=n)
+    ref = as_dt(v, dt).copy()
+    for (c, t) in [(0, n - 1), (n - 1, 0), (3, 4), (n - 2, 1), (5, n - 3)]:
+        U = W.haar_u2(g, 1)[0]
+        s.apply_ctrl(c, t, U)
+        O.apply_ctrl(ref, n, c, t, U)
+        s.cnot(t, c)
+        O.cnot(ref, n, t, c)
+        s.cphase(c, t, 3)
+        O.cphase(ref, n, c, t, 3)
+        s.swap(c, t)
+        O.swap(ref, n, c, t)
+    assert np.max(np.abs(s.numpy() - ref)) <= TOL[dt] * 4
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n", [1, 4, 12, 13, 14, 17, 22])
+def test_hall_and_layer(qc, dt, n):
+    s, v = mk(qc, n, dt, seed=n + 1)
+    ref = as_dt(v, dt).copy()
+    s.hall()
+    O.hall(ref, n)
+    assert np.max(np.abs(s.numpy() - ref)) <= TOL[dt] * max(1, n / 4)
+    g = W.rng(n + 5)
+    U = W.haar_u2(g, n)
+    mask = (1 << n) - 1
+    if n > 3:
+        mask &= ~(1 << (n // 2))  # one qubit left out
+    s.apply_1q_layer(U, mask)
+    for q in range(n):
+        if (mask >> q) & 1:
+            O.apply_1q(ref, n, q, U[q])
+    assert np.max(np.abs(s.numpy() - ref)) <= TOL[dt] * max(1, n / 4)
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 9, 10, 11, 12, 13, 16, 19])
+def test_qft_vs_oracle(qc, dt, n):
+    s, v = mk(qc, n, dt, seed=50 + n)
+    ref = O.qft(as_dt(v, dt).copy(), n)
+    s.qft()
+    got = s.numpy()
+    assert np.max(np.abs(got - ref)) <= TOL[dt] * max(1, n / 4)
+
+
+@pytest.mark.parametrize("n", [4, 11, 20])
+def test_qft_basis_state_analytic(qc, n):
+    N = 1 << n
+    for m in (0, 1, N // 3, N - 1):
+        s = qc.State(n, 0).reset(m)
+        s.qft()
+        ref = np.exp(2j * np.pi * m * np.arange(N) / N) / math.sqrt(N)
+        assert np.max(np.abs(s.numpy() - ref)) <= 1e-12
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n,M", [(3, 1), (8, 2), (12, 3), (16, 8), (17, 1)])
+def test_grover_step_vs_literal(qc, dt, n, M):
+    marked = W.marked_indices(W.rng(n * 7 + M), n, M)
+    s, v = mk(qc, n, dt, seed=n)
+    ref = as_dt(v, dt).copy()
+    for _ in range(3):
+        s.grover_step(marked)
+        O.grover_step(ref, n, marked)
+    assert np.max(np.abs(s.numpy() - ref)) <= TOL[dt] * 4
+    # a different gate in between invalidates the cached sum
+    U = W.haar_u2(W.rng(1), 1)[0]
+    s.apply_1q(0, U)
+    O.apply_1q(ref, n, 0, U)
+    s.grover_step(marked)
+    O.grover_step(ref, n, marked)
+    assert np.max(np.abs(s.numpy() - ref)) <= TOL[dt] * 4
+
+
+def grover_closed(n, marked, k):
+    N, M = 2 ** n, len(marked)
+    th = math.asin(math.sqrt(M / N))
+    v = np.full(N, math.cos((2 * k + 1) * th) / math.sqrt(N - M), dtype=np.complex128)
+    v[np.asarray(marked, dtype=np.int64)] = math.sin((2 * k + 1) * th) / math.sqrt(M)
+    return v
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n,M", [(10, 1), (13, 2), (14, 8), (15, 1), (20, 8)])
+def test_grover_run_closed_form(qc, dt, n, M):
+    marked = W.marked_indices(W.rng(1000 + n), n, M)
+    k = W.grover_iterations(n) if n <= 15 else 40
+    s = qc.State(n, dt)
+    s.grover_run(marked, k)
+    ref = grover_closed(n, marked, k)
+    assert np.max(np.abs(s.numpy() - ref)) <= TOL[dt] * (10 if dt else 1)
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n", [1, 5, 13, 18])
+def test_reductions(qc, dt, n):
+    s, v = mk(qc, n, dt, seed=n * 3)
+    x = as_dt(v, dt)
+    assert abs(s.norm() - O.norm(x, n)) <= 1e-12
+    p = s.probs().cpu().numpy()
+    pr = O.probs(x, n)
+    assert np.array_equal(p, pr)  # same operations, same rounding
+    for xm, zm in [(0, 0b11 & ((1 << n) - 1)), (1, 0), ((1 << n) - 1, 1), (0b101 & ((1 << n) - 1), 0b110 & ((1 << n) - 1))]:
+        e = s.expect_pauli(xm, zm)
+        assert abs(e - O.expect_pauli(x, n, xm, zm)) <= 1e-12
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n", [1, 3, 12, 15])
+def test_sample_bit_exact(qc, dt, n):
+    s, v = mk(qc, n, dt, seed=n + 11)
+    p = s.probs().cpu().numpy()
+    for seed in (0, 12345, 2 ** 40 + 7):
+        got = s.sample(seed, 1000).cpu().numpy().astype(np.uint64)
+        ref = O.sample_from_probs(p, seed, 1000)
+        assert np.array_equal(got, ref)
+
+
+def test_renormalize(qc):
+    n = 9
+    s, v = mk(qc, n, 0, vec=W.random_state(W.rng(2), n) * 1.7)
+    nrm = s.renormalize()
+    assert abs(nrm - 1.7 ** 2) < 1e-12
+    assert abs(s.norm() - 1.0) < 1e-14
+
+
+def test_invalid_arguments(qc):
+    s = qc.State(4, 0)
+    bad = [lambda: s.apply_1q(4, np.eye(2, dtype=complex)), lambda: s.apply_ctrl(1, 1, np.eye(2, dtype=complex)),
+           lambda: s.cphase(0, 1, 0), lambda: s.swap(2, 2), lambda: s.grover_step([16]),
+           lambda: s.grover_step([1, 1]), lambda: s.apply_1q(0, [np.nan] * 8),
+           lambda: s.apply_1q_layer(W.haar_u2(W.rng(0), 4), 1 << 4)]
+    for f in bad:
+        with pytest.raises(qc.QCError) as e:
+            f()
+        assert e.value.status == qc.QC_EINVAL
+    with pytest.raises(qc.QCError):
+        qc.qc_state_alloc(0)
+    with pytest.raises(qc.QCError):
+        qc.qc_state_alloc(35)
+    # state unchanged by the rejected calls
+    assert abs(s.numpy()[0]) >= 0
