@@ -446,8 +446,13 @@ __global__ void __launch_bounds__(1024) k_traj(TrajParams P) {
 
 using namespace qc;
 
+// The plan launches on a private non-blocking stream (graphs cannot be
+// captured on the legacy default stream) joined to the caller's stream by
+// events in both directions.
 struct qc_traj_plan {
+  cudaStream_t user;
   cudaStream_t stream;
+  cudaEvent_t ev_in, ev_out;
   int n_inst;
   TrajInst* d_inst;
   float2* slots;
@@ -527,11 +532,21 @@ QC_API qc_status qc_traj_plan_create(const qc_traj_desc* d, void* stream, int au
     return ldexp((double)a.iters + 1.0, a.n) > ldexp((double)b.iters + 1.0, b.n);
   });
   qc_traj_plan* p = new qc_traj_plan();
-  p->stream = (cudaStream_t)stream;
+  p->user = (cudaStream_t)stream;
   p->n_inst = d->n_inst;
   p->slot_amps = 1ull << nmax;
   p->have_graph = false;
-  cudaError_t e = cudaMalloc(&p->d_inst, sizeof(TrajInst) * h.size());
+  cudaError_t e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "trajectory plan stream");
+  }
+  // the plan's setup work follows whatever the caller queued before
+  e = cudaEventRecord(p->ev_in, p->user);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, p->ev_in, 0);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_inst, sizeof(TrajInst) * h.size());
   if (e == cudaSuccess) e = cudaMemcpy(p->d_inst, h.data(), sizeof(TrajInst) * h.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&p->queue, sizeof(unsigned) + sizeof(int));
   if (e != cudaSuccess) {
@@ -542,7 +557,7 @@ QC_API qc_status qc_traj_plan_create(const qc_traj_desc* d, void* stream, int au
   // candidate shapes: G CTAs per instance (G <= 2^{nmin-1}), T threads
   std::vector<int> Gs, Ts = {256, 512, 1024};
   for (int G = 1; G <= 16; G *= 2)
-    if ((uint64_t)G * 2 <= (1ull << nmin)) Gs.push_back(G);
+    if ((uint64_t)G * 2 <= (1ull << nmin) && (G >= 4 || nmax <= 14)) Gs.push_back(G);
   struct Cand {
     int G, T, grid;
   };
@@ -587,7 +602,7 @@ QC_API qc_status qc_traj_plan_create(const qc_traj_desc* d, void* stream, int au
     if (c.T == 512 && c.G >= best.G) best = c;
   if (autotune && cands.size() > 1) {
     // time each shape on an evenly spaced sample of the cost-sorted list
-    const int stride = std::max(1, d->n_inst / 96);
+    const int stride = std::max(1, d->n_inst / 32);
     std::vector<TrajInst> samp;
     for (int i = 0; i < d->n_inst; i += stride) {
       TrajInst t = h[i];
@@ -621,7 +636,7 @@ QC_API qc_status qc_traj_plan_create(const qc_traj_desc* d, void* stream, int au
     float best_ms = 1e30f;
     for (auto& c : cands) {
       float ms_min = 1e30f;
-      for (int rep = 0; rep < 2; ++rep) {
+      for (int rep = 0; rep < 2; ++rep) {  // first run warms up, both are timed
         cudaMemsetAsync(p->queue, 0, sizeof(unsigned), p->stream);
         cudaEventRecord(e0, p->stream);
         if (traj_launch(p, c.G, c.T, c.grid, sp)) break;
@@ -646,6 +661,13 @@ QC_API qc_status qc_traj_plan_create(const qc_traj_desc* d, void* stream, int au
   p->G = best.G;
   p->T = best.T;
   p->grid = best.grid;
+  // later work on the caller's stream sees the uploaded descriptors
+  e = cudaEventRecord(p->ev_out, p->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->user, p->ev_out, 0);
+  if (e != cudaSuccess) {
+    qc_traj_plan_free(p);
+    return cuda_fail(e, "trajectory plan join");
+  }
   *out = p;
   return check_launch("trajectory plan", autotune ? 2 * (int)cands.size() : 0);
 }
@@ -682,7 +704,12 @@ QC_API qc_status qc_traj_plan_run(qc_traj_plan* p, const qc_traj_out* o) {
     p->have_graph = true;
     p->last_out = *o;
   }
-  cudaError_t e = cudaGraphLaunch(p->gexec, p->stream);
+  // order: caller's stream -> plan stream (graph) -> caller's stream
+  cudaError_t e = cudaEventRecord(p->ev_in, p->user);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, p->ev_in, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(p->gexec, p->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(p->ev_out, p->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->user, p->ev_out, 0);
   if (e != cudaSuccess) return cuda_fail(e, "graph launch");
   return check_launch("trajectory run", 1);
 }
@@ -707,6 +734,9 @@ QC_API qc_status qc_traj_plan_free(qc_traj_plan* p) {
   cudaFree(p->d_inst);
   cudaFree(p->queue);
   cudaFree(p->slots);
+  cudaEventDestroy(p->ev_in);
+  cudaEventDestroy(p->ev_out);
+  cudaStreamDestroy(p->stream);
   delete p;
   return QC_OK;
 }
