@@ -191,6 +191,38 @@ qc_status qc_renormalize(qc_state* s, double* norm_out_host);
  * temporary device buffer of 8 * 2^n bytes (QC_ENOMEM if it does not fit). */
 qc_status qc_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_t* out_dev);
 
+/* Seeded measurement for callers that cannot allocate device memory.  The
+ * paper has no counterpart; this entry point exists for library users.
+ *
+ * Who needs it: a host framework that has already claimed the device memory
+ * for its own pool (a cudaMalloc here would fail or force it to give memory
+ * back), and code on a latency-critical path that cannot take the
+ * device-wide synchronisation that cudaMalloc / cudaFree imply.  qc_sample
+ * allocates its 8 * 2^n-byte CDF per call and needs a qc_state handle, whose
+ * creation allocates scratch too; this variant takes the raw state pointer
+ * and calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Result: the same outcomes as qc_sample for the same state, seed and shots
+ * (the definition written there), written to out_dev (`shots` uint64 in
+ * device memory).  psi_dev holds 2^n amplitudes of dtype dt.
+ *
+ * Limits and scratch: n must be <= QC_SAMPLE_NOALLOC_MAX_QUBITS (20); larger
+ * states return QC_EINVAL with a message.  The scratch is a fixed array of
+ * 2^20 + 512 + 32 uint64 (about 8 MiB) in the library's own device memory,
+ * held on every GPU that loads the library until the process exits.  The
+ * first call on a device looks up that array's device address, so make the
+ * first call on each device before any stream capture.  The array keeps the
+ * last call's contents (each call resets what must start at zero); calls
+ * whose work overlaps on the GPU -- on different streams or threads -- race
+ * on it and must be serialised by the caller.
+ *
+ * Validation: every |C_i|^2 must lie in [0, 2] and
+ * 0 < sum_i trunc(p_i 2^62) <= 2^63; otherwise QC_EINVAL (checked on the
+ * device; the call synchronises `stream` once to read the verdict). */
+#define QC_SAMPLE_NOALLOC_MAX_QUBITS 20
+qc_status qc_sample_noalloc(const void* psi_dev, int n, qc_dtype dt, uint64_t seed, int64_t shots,
+                            uint64_t* out_dev, void* stream);
+
 /* ---------------------------------------------- batched noisy trajectories
  * Many independent noisy Grover runs ("multiverses", sec. 6.2-6.3) of uneven
  * qubit counts, complex64 with FP64 reductions, in one persistent launch.

@@ -87,6 +87,7 @@ _SIGS = {
     "qc_expect_pauli": [_VP, _U64, _U64, _DP],
     "qc_renormalize": [_VP, _DP],
     "qc_sample": [_VP, _U64, _I64, _VP],
+    "qc_sample_noalloc": [_VP, _I, _I, _U64, _I64, _VP, _VP],
     "qc_traj_plan_create": [ctypes.POINTER(TrajDesc), _VP, _I, ctypes.POINTER(_VP)],
     "qc_traj_plan_run": [_VP, ctypes.POINTER(TrajOut)],
     "qc_traj_plan_info": [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],

@@ -391,4 +391,105 @@ qc_status launch_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_
   return st;
 }
 
+// ------------------------------------------- sampler without allocation --
+// Scratch for qc_sample_noalloc, resident on every device that loads this
+// library until the process exits: the integer CDF of up to 2^20
+// amplitudes, the per-block weight sums and a status word.
+#define NA_MAX_N QC_SAMPLE_NOALLOC_MAX_QUBITS
+#define NA_CDF (1ull << NA_MAX_N)
+#define NA_BSUM ((NA_CDF + SMP_BLOCK - 1) / SMP_BLOCK)
+static __device__ __align__(256) uint64_t g_noalloc_scratch[NA_CDF + NA_BSUM + 32];
+
+// Device address of the scratch per device (host code only sees a host-side
+// stand-in for the symbol, so the address is looked up once per device).
+static uint64_t* g_noalloc_ptr[64] = {nullptr};
+
+// Status bits: 1 = some p_i outside [0, 2] (or NaN), 2 = total weight zero or
+// above 2^63.
+template <typename R>
+__global__ void k_noalloc_check(const typename CT<R>::V2* __restrict__ s, uint64_t N, uint64_t* __restrict__ status) {
+  bool bad = false;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
+    const double p = prob_of<R>(s[i]);
+    bad |= !(p >= 0.0 && p <= 2.0);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr((unsigned long long*)status, 1ull);
+}
+
+__global__ void k_noalloc_total(const uint64_t* __restrict__ cdf, uint64_t N, uint64_t* __restrict__ status) {
+  const uint64_t total = cdf[N - 1];
+  if (total == 0 || total > (1ull << 63)) atomicOr((unsigned long long*)status, 2ull);
+}
+
 }  // namespace qc
+
+using namespace qc;
+
+QC_API qc_status qc_sample_noalloc(const void* psi_dev, int n, qc_dtype dt, uint64_t seed, int64_t shots,
+                                   uint64_t* out_dev, void* stream) {
+  clear_error();
+  if (n < 1 || n > NA_MAX_N) {
+    set_error("qc_sample_noalloc: n = %d out of range [1, %d] (its fixed scratch holds 2^%d amplitudes)", n,
+              NA_MAX_N, NA_MAX_N);
+    return QC_EINVAL;
+  }
+  if (dt != QC_C128 && dt != QC_C64) {
+    set_error("unknown dtype %d", (int)dt);
+    return QC_EINVAL;
+  }
+  if (!psi_dev || shots < 0 || (shots > 0 && !out_dev)) {
+    set_error("qc_sample_noalloc: NULL state, negative shots or NULL output");
+    return QC_EINVAL;
+  }
+  if (shots == 0) return QC_OK;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "qc_sample_noalloc: device");
+  if (dev < 0 || dev >= 64) {
+    set_error("qc_sample_noalloc: device ordinal %d not supported", dev);
+    return QC_EINVAL;
+  }
+  if (!g_noalloc_ptr[dev]) {  // first call on this device: look up the scratch address
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "qc_sample_noalloc: scratch address");
+    g_noalloc_ptr[dev] = reinterpret_cast<uint64_t*>(ptr);
+  }
+  uint64_t* cdf = g_noalloc_ptr[dev];
+  uint64_t* bsum = cdf + NA_CDF;
+  uint64_t* status = bsum + NA_BSUM;
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint64_t N = 1ull << n;
+  const uint64_t nb = (N + SMP_BLOCK - 1) / SMP_BLOCK;
+  e = cudaMemsetAsync(status, 0, sizeof(uint64_t), st);  // the previous call's status is stale
+  if (e != cudaSuccess) return cuda_fail(e, "qc_sample_noalloc: status reset");
+  const unsigned gc = (unsigned)std::min<uint64_t>((N + 255) / 256, (uint64_t)sm_count() * 4);
+  if (dt == QC_C128) {
+    const double2* d = reinterpret_cast<const double2*>(psi_dev);
+    k_noalloc_check<double><<<gc, 256, 0, st>>>(d, N, status);
+    k_wsum<double><<<(unsigned)nb, SMP_T, 0, st>>>(d, N, bsum);
+    k_scan_bsum<<<1, 1024, 0, st>>>(bsum, nb);
+    k_wcdf<double><<<(unsigned)nb, SMP_T, 0, st>>>(d, N, bsum, cdf);
+  } else {
+    const float2* d = reinterpret_cast<const float2*>(psi_dev);
+    k_noalloc_check<float><<<gc, 256, 0, st>>>(d, N, status);
+    k_wsum<float><<<(unsigned)nb, SMP_T, 0, st>>>(d, N, bsum);
+    k_scan_bsum<<<1, 1024, 0, st>>>(bsum, nb);
+    k_wcdf<float><<<(unsigned)nb, SMP_T, 0, st>>>(d, N, bsum, cdf);
+  }
+  k_noalloc_total<<<1, 1, 0, st>>>(cdf, N, status);
+  qc_status rs = check_launch("qc_sample_noalloc: cdf", 5);
+  if (rs) return rs;
+  uint64_t hstat = 0;
+  e = cudaMemcpyAsync(&hstat, status, sizeof hstat, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "qc_sample_noalloc: status readback");
+  if (hstat) {
+    set_error("qc_sample_noalloc: probabilities unusable (status %llu: need every |C_i|^2 in [0, 2] and "
+              "0 < sum trunc(p_i 2^62) <= 2^63)", (unsigned long long)hstat);
+    return QC_EINVAL;
+  }
+  const unsigned g = (unsigned)std::min<int64_t>((shots + 255) / 256, (int64_t)sm_count() * 8);
+  k_sample<<<g, 256, 0, st>>>(cdf, N, seed, shots, out_dev);
+  return check_launch("qc_sample_noalloc: sample", 1);
+}
