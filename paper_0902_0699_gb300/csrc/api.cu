@@ -5,7 +5,10 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -51,6 +54,24 @@ int sm_count() {
   return cache[dev];
 }
 
+int resident_blocks(const void* kernel, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, size_t, int>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(kernel, threads, smem, dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess || nb < 1) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  cache[key] = nb;
+  return nb;
+}
+
 static bool is0(double re, double im) { return re == 0.0 && im == 0.0; }
 
 MatKind classify(const double* U) {
@@ -59,6 +80,9 @@ MatKind classify(const double* U) {
   if (offz) {
     if (u00[0] == 1.0 && u00[1] == 0.0) {
       if (u11[0] == 1.0 && u11[1] == 0.0) return MK_IDENT;
+      if (u11[0] == -1.0 && u11[1] == 0.0) return MK_PH_NEG;
+      if (u11[0] == 0.0 && u11[1] == 1.0) return MK_PH_I;
+      if (u11[0] == 0.0 && u11[1] == -1.0) return MK_PH_MI;
       return MK_PHASE1;
     }
     return MK_DIAG;

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/qc.h"
+#include "ff.cuh"
 
 #define QC_API extern "C" __attribute__((visibility("default")))
 
@@ -59,6 +60,20 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline unsigned grid_for(int64_t items, int per_block, int waves) {
   int64_t b = ceil_div(items, per_block);
   int64_t cap = (int64_t)sm_count() * waves;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+// Blocks of `kernel` that fit on one SM at once (cached per kernel).
+int resident_blocks(const void* kernel, int threads, size_t smem);
+
+// Grid for a grid-stride kernel: no more blocks than are resident at once
+// (a second partial wave would leave most SMs idle at the end).
+template <typename K>
+inline unsigned resident_grid(K kernel, int threads, int64_t items, int per_block, size_t smem = 0) {
+  int64_t b = ceil_div(items, per_block);
+  const int64_t cap = (int64_t)sm_count() * resident_blocks((const void*)kernel, threads, smem);
   if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (unsigned)b;
@@ -162,9 +177,19 @@ enum MatKind {
   MK_ANTI = 4,     // U00 = U11 = 0
   MK_SWAPX = 5,    // U01 = U10 = 1, U00 = U11 = 0 (Pauli X): a pure exchange
   MK_HAD = 6,      // U00 = U01 = U10 = -U11 = h real
-  MK_IDENT = 7     // identity: nothing to do
+  MK_IDENT = 7,    // identity: nothing to do
+  MK_PH_NEG = 8,   // diag(1, -1): the bit-1 amplitudes change sign (exact)
+  MK_PH_I = 9,     // diag(1, i): (re, im) -> (-im, re) on bit 1 (exact)
+  MK_PH_MI = 10    // diag(1, -i): (re, im) -> (im, -re) on bit 1 (exact)
 };
 MatKind classify(const double* U);
+
+// Exact sign change of a double or float by flipping the sign bit with an
+// integer operation (no floating-point instruction is issued).
+__device__ __forceinline__ double neg_exact(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+__device__ __forceinline__ float neg_exact(float x) { return __uint_as_float(__float_as_uint(x) ^ 0x80000000u); }
 
 // Loads / stores of one amplitude.
 template <typename R> struct AmpIO;
@@ -202,6 +227,12 @@ __device__ __forceinline__ void apply2(const Mat2<R>& U, Cx<R>& a0, Cx<R>& a1) {
     a1 = cmul(U.m[3], a1);
   } else if (KIND == MK_PHASE1) {
     a1 = cmul(U.m[3], a1);
+  } else if (KIND == MK_PH_NEG) {
+    a1 = cmake<R>(neg_exact(a1.re), neg_exact(a1.im));
+  } else if (KIND == MK_PH_I) {
+    a1 = cmake<R>(neg_exact(a1.im), a1.re);
+  } else if (KIND == MK_PH_MI) {
+    a1 = cmake<R>(a1.im, neg_exact(a1.re));
   } else if (KIND == MK_ANTI) {
     Cx<R> b0 = cmul(U.m[1], a1);
     Cx<R> b1 = cmul(U.m[2], a0);
@@ -220,6 +251,56 @@ __device__ __forceinline__ void apply2(const Mat2<R>& U, Cx<R>& a0, Cx<R>& a1) {
     a0 = b0;
     a1 = b1;
   }
+}
+
+// True for the kinds that only touch the bit-1 amplitude of a pair.
+__host__ __device__ constexpr bool touches_bit1_only(int k) {
+  return k == MK_PHASE1 || k == MK_PH_NEG || k == MK_PH_I || k == MK_PH_MI;
+}
+
+// ---------------------------------------- complex128 in double-float -----
+// A 2x2 operator split into double-float entries (built on the host).
+struct Mat2ff {
+  ffc m[4];
+};
+inline Mat2ff mat2ff_from_host(const double* U) {
+  Mat2ff r;
+  for (int k = 0; k < 4; ++k) r.m[k] = ffc_from_d(U[2 * k], U[2 * k + 1]);
+  return r;
+}
+
+// The arithmetic kinds of apply2 in double-float (the exact kinds -- swaps,
+// sign flips, identity -- never need it).
+template <int KIND>
+__device__ __forceinline__ void apply2_ff(const Mat2ff& U, ffc& a0, ffc& a1) {
+  if (KIND == MK_GENERAL) {
+    const ffc b0 = ffc_mul2(U.m[0], a0, U.m[1], a1);
+    a1 = ffc_mul2(U.m[2], a0, U.m[3], a1);
+    a0 = b0;
+  } else if (KIND == MK_REAL) {
+    const ffc b0 = ffc_make(ff_dot2p(U.m[0].re, a0.re, U.m[1].re, a1.re), ff_dot2p(U.m[0].re, a0.im, U.m[1].re, a1.im));
+    a1 = ffc_make(ff_dot2p(U.m[2].re, a0.re, U.m[3].re, a1.re), ff_dot2p(U.m[2].re, a0.im, U.m[3].re, a1.im));
+    a0 = b0;
+  } else if (KIND == MK_DIAG) {
+    a0 = ffc_mul(U.m[0], a0);
+    a1 = ffc_mul(U.m[3], a1);
+  } else if (KIND == MK_PHASE1) {
+    a1 = ffc_mul(U.m[3], a1);
+  } else if (KIND == MK_ANTI) {
+    const ffc b0 = ffc_mul(U.m[1], a1);
+    a1 = ffc_mul(U.m[2], a0);
+    a0 = b0;
+  } else if (KIND == MK_HAD) {
+    const ff h = U.m[0].re;
+    const ffc b0 = ffc_scale(ffc_add(a0, a1), h);
+    a1 = ffc_scale(ffc_sub(a0, a1), h);
+    a0 = b0;
+  }
+}
+
+// Kinds whose complex128 form runs in double-float.
+__host__ __device__ constexpr bool uses_ff(int k) {
+  return k == MK_GENERAL || k == MK_REAL || k == MK_DIAG || k == MK_ANTI || k == MK_HAD;
 }
 
 // Bytes per amplitude.

@@ -2,13 +2,53 @@
 // controlled operators / CNOT / CPHASEK (Eq. resmat2, Eq. cphasek) and SWAP,
 // plus state fills.  Each is one streaming read+write pass over the
 // amplitudes the gate touches, with 128-bit loads and stores and
-// grid-stride loops sized to the SM count.
+// grid-stride loops sized to the resident blocks.
+//
+// complex64 operators compute in FP32.  complex128 operators with real
+// arithmetic (general, real, diagonal, anti-diagonal, Hadamard) compute in
+// double-float on the FP32 pipe (ff.cuh): on GB300 the FP64 pipe does 0.5
+// Top/s, fewer than 2.5 FP64 operations per amplitude in the time one HBM
+// pass takes at 30 qubits.  Exchanges (X, CNOT, SWAP) and the phases -1, +i,
+// -i are exact moves and sign flips; other phases use one FP64 complex
+// multiply on the touched quarter.
 #include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
 
 namespace qc {
+
+// Operator as passed to the gate kernels: the native matrix, and for
+// complex128 its double-float split.
+template <typename R> struct GateArg;
+template <> struct GateArg<float> {
+  Mat2<float> U;
+};
+template <> struct GateArg<double> {
+  Mat2<double> U;
+  Mat2ff F;
+};
+
+template <typename R, int KIND>
+__device__ __forceinline__ void apply_gate(const GateArg<R>& G, Cx<R>& a0, Cx<R>& a1) {
+  if constexpr (sizeof(R) == 8 && KIND == MK_HAD) {
+    // both pipes: real parts in FP64 (1.5 FP64 operations per amplitude),
+    // imaginary parts in double-float on the FP32 pipe
+    const double h = G.U.m[0].re;
+    const double q = h * a1.re;
+    const double r0 = fma(h, a0.re, q), r1 = fma(h, a0.re, -q);
+    const ff x0 = ff_from_d(a0.im), x1 = ff_from_d(a1.im), hf = G.F.m[0].re;
+    a0 = cmake<R>(r0, ff_to_d(ff_mul(ff_add(x0, x1), hf)));
+    a1 = cmake<R>(r1, ff_to_d(ff_mul(ff_sub(x0, x1), hf)));
+  } else if constexpr (sizeof(R) == 8 && uses_ff(KIND)) {
+    ffc b0 = ffc_from_d(a0.re, a0.im), b1 = ffc_from_d(a1.re, a1.im);
+    apply2_ff<KIND>(G.F, b0, b1);
+    a0 = cmake<R>(ff_to_d(b0.re), ff_to_d(b0.im));
+    a1 = cmake<R>(ff_to_d(b1.re), ff_to_d(b1.im));
+  } else {
+    apply2<R, KIND>(G.U, a0, a1);
+  }
+}
 
 // Enumeration of the pairs a gate updates.  Pair p maps to index i0 by
 // inserting zero bits at positions p0 < p1 (NINS = 1 or 2) and or-ing in
@@ -24,23 +64,24 @@ __device__ __forceinline__ uint64_t pair_base(uint64_t p, int p0, int p1, uint64
 // accesses.  Two items are processed per loop trip so that four loads are in
 // flight before the first use.
 template <typename R, int KIND, int NINS>
-__global__ void __launch_bounds__(256) k_pairs(typename CT<R>::V2* __restrict__ s, uint64_t npairs,
-                                               int p0, int p1, uint64_t setm, int t, Mat2<R> U) {
+__global__ void __launch_bounds__(256) k_pairs(typename CT<R>::V2* __restrict__ s, uint64_t npairs, int p0,
+                                               int p1, uint64_t setm, int t, GateArg<R> G) {
   using IO = AmpIO<R>;
+  constexpr bool B1 = touches_bit1_only(KIND);
   const uint64_t st = 1ull << t;
-  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t GS = (uint64_t)gridDim.x * blockDim.x;
   uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (; p + G < npairs; p += 2 * G) {
-    const uint64_t i0 = pair_base<NINS>(p, p0, p1, setm), j0 = pair_base<NINS>(p + G, p0, p1, setm);
+  for (; p + GS < npairs; p += 2 * GS) {
+    const uint64_t i0 = pair_base<NINS>(p, p0, p1, setm), j0 = pair_base<NINS>(p + GS, p0, p1, setm);
     Cx<R> a0 = cmake<R>(0, 0), b0 = cmake<R>(0, 0);
-    if (KIND != MK_PHASE1) {
+    if (!B1) {
       a0 = IO::ld(s + i0);
       b0 = IO::ld(s + j0);
     }
     Cx<R> a1 = IO::ld(s + (i0 | st)), b1 = IO::ld(s + (j0 | st));
-    apply2<R, KIND>(U, a0, a1);
-    apply2<R, KIND>(U, b0, b1);
-    if (KIND != MK_PHASE1) {
+    apply_gate<R, KIND>(G, a0, a1);
+    apply_gate<R, KIND>(G, b0, b1);
+    if (!B1) {
       IO::st(s + i0, a0);
       IO::st(s + j0, b0);
     }
@@ -50,10 +91,10 @@ __global__ void __launch_bounds__(256) k_pairs(typename CT<R>::V2* __restrict__ 
   if (p < npairs) {
     const uint64_t i0 = pair_base<NINS>(p, p0, p1, setm);
     Cx<R> a0 = cmake<R>(0, 0);
-    if (KIND != MK_PHASE1) a0 = IO::ld(s + i0);
+    if (!B1) a0 = IO::ld(s + i0);
     Cx<R> a1 = IO::ld(s + (i0 | st));
-    apply2<R, KIND>(U, a0, a1);
-    if (KIND != MK_PHASE1) IO::st(s + i0, a0);
+    apply_gate<R, KIND>(G, a0, a1);
+    if (!B1) IO::st(s + i0, a0);
     IO::st(s + (i0 | st), a1);
   }
 }
@@ -61,20 +102,21 @@ __global__ void __launch_bounds__(256) k_pairs(typename CT<R>::V2* __restrict__ 
 // complex64, all inserted bit positions >= 1: two neighbouring pairs per
 // work item share 16-byte loads (amplitudes i0, i0+1 and i1, i1+1).
 template <int KIND, int NINS>
-__global__ void __launch_bounds__(256) k_pairs_v2(float2* __restrict__ s, uint64_t nitems, int p0,
-                                                  int p1, uint64_t setm, int t, Mat2<float> U) {
+__global__ void __launch_bounds__(256) k_pairs_v2(float2* __restrict__ s, uint64_t nitems, int p0, int p1,
+                                                  uint64_t setm, int t, GateArg<float> G) {
+  constexpr bool B1 = touches_bit1_only(KIND);
   const uint64_t st = 1ull << t;
-  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nitems; v += G) {
+  const uint64_t GS = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nitems; v += GS) {
     const uint64_t i0 = pair_base<NINS>(2 * v, p0, p1, setm);
     float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B;
-    if (KIND != MK_PHASE1) A = *reinterpret_cast<const float4*>(s + i0);
+    if (!B1) A = *reinterpret_cast<const float4*>(s + i0);
     B = *reinterpret_cast<const float4*>(s + (i0 | st));
     Cx<float> a0 = cmake(A.x, A.y), c0 = cmake(A.z, A.w);
     Cx<float> a1 = cmake(B.x, B.y), c1 = cmake(B.z, B.w);
-    apply2<float, KIND>(U, a0, a1);
-    apply2<float, KIND>(U, c0, c1);
-    if (KIND != MK_PHASE1) *reinterpret_cast<float4*>(s + i0) = make_float4(a0.re, a0.im, c0.re, c0.im);
+    apply2<float, KIND>(G.U, a0, a1);
+    apply2<float, KIND>(G.U, c0, c1);
+    if (!B1) *reinterpret_cast<float4*>(s + i0) = make_float4(a0.re, a0.im, c0.re, c0.im);
     *reinterpret_cast<float4*>(s + (i0 | st)) = make_float4(a1.re, a1.im, c1.re, c1.im);
   }
 }
@@ -82,55 +124,71 @@ __global__ void __launch_bounds__(256) k_pairs_v2(float2* __restrict__ s, uint64
 // complex64, one-qubit gate on t = 0: the pair (2q, 2q+1) is one 16-byte
 // vector.
 template <int KIND>
-__global__ void __launch_bounds__(256) k_pairs_t0(float2* __restrict__ s, uint64_t npairs, Mat2<float> U) {
-  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+__global__ void __launch_bounds__(256) k_pairs_t0(float2* __restrict__ s, uint64_t npairs, GateArg<float> G) {
+  const uint64_t GS = (uint64_t)gridDim.x * blockDim.x;
   float4* v4 = reinterpret_cast<float4*>(s);
-  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += G) {
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += GS) {
     float4 A = v4[p];
     Cx<float> a0 = cmake(A.x, A.y), a1 = cmake(A.z, A.w);
-    apply2<float, KIND>(U, a0, a1);
+    apply2<float, KIND>(G.U, a0, a1);
     v4[p] = make_float4(a0.re, a0.im, a1.re, a1.im);
   }
 }
 
 template <typename R, int KIND>
-static void launch_kind(qc_state* s, int nins, int p0, int p1, uint64_t setm, int t, const Mat2<R>& U) {
+static void launch_kind(qc_state* s, int nins, int p0, int p1, uint64_t setm, int t, const GateArg<R>& G) {
   using V2 = typename CT<R>::V2;
   const uint64_t npairs = (1ull << s->n) >> nins;
   V2* d = reinterpret_cast<V2*>(s->data);
   const int T = 256;
   if constexpr (sizeof(R) == 4) {
     if (nins == 1 && t == 0) {
-      k_pairs_t0<KIND><<<grid_for(npairs, T, 8), T, 0, s->stream>>>(d, npairs, U);
+      auto k = k_pairs_t0<KIND>;
+      k<<<resident_grid(k, T, npairs, T), T, 0, s->stream>>>(d, npairs, G);
       return;
     }
     if (p0 >= 1 && npairs >= 2) {
       const uint64_t items = npairs / 2;
-      if (nins == 1)
-        k_pairs_v2<KIND, 1><<<grid_for(items, T, 8), T, 0, s->stream>>>(d, items, p0, p1, setm, t, U);
-      else
-        k_pairs_v2<KIND, 2><<<grid_for(items, T, 8), T, 0, s->stream>>>(d, items, p0, p1, setm, t, U);
+      auto k = (nins == 1) ? k_pairs_v2<KIND, 1> : k_pairs_v2<KIND, 2>;
+      k<<<resident_grid(k, T, items, T), T, 0, s->stream>>>(d, items, p0, p1, setm, t, G);
       return;
     }
   }
-  if (nins == 1)
-    k_pairs<R, KIND, 1><<<grid_for(npairs, 2 * T, 8), T, 0, s->stream>>>(d, npairs, p0, p1, setm, t, U);
-  else
-    k_pairs<R, KIND, 2><<<grid_for(npairs, 2 * T, 8), T, 0, s->stream>>>(d, npairs, p0, p1, setm, t, U);
+  auto k = (nins == 1) ? k_pairs<R, KIND, 1> : k_pairs<R, KIND, 2>;
+  k<<<resident_grid(k, T, npairs, 2 * T), T, 0, s->stream>>>(d, npairs, p0, p1, setm, t, G);
+}
+
+template <typename R>
+static GateArg<R> gate_arg(const double* Uh);
+template <>
+GateArg<float> gate_arg<float>(const double* Uh) {
+  GateArg<float> G;
+  G.U = mat_from_host<float>(Uh);
+  return G;
+}
+template <>
+GateArg<double> gate_arg<double>(const double* Uh) {
+  GateArg<double> G;
+  G.U = mat_from_host<double>(Uh);
+  G.F = mat2ff_from_host(Uh);
+  return G;
 }
 
 template <typename R>
 static void launch_pairs(qc_state* s, int nins, int p0, int p1, uint64_t setm, int t, const double* Uh) {
-  const Mat2<R> U = mat_from_host<R>(Uh);
+  const GateArg<R> G = gate_arg<R>(Uh);
   switch (classify(Uh)) {
     case MK_IDENT: return;
-    case MK_GENERAL: launch_kind<R, MK_GENERAL>(s, nins, p0, p1, setm, t, U); return;
-    case MK_REAL: launch_kind<R, MK_REAL>(s, nins, p0, p1, setm, t, U); return;
-    case MK_DIAG: launch_kind<R, MK_DIAG>(s, nins, p0, p1, setm, t, U); return;
-    case MK_PHASE1: launch_kind<R, MK_PHASE1>(s, nins, p0, p1, setm, t, U); return;
-    case MK_ANTI: launch_kind<R, MK_ANTI>(s, nins, p0, p1, setm, t, U); return;
-    case MK_SWAPX: launch_kind<R, MK_SWAPX>(s, nins, p0, p1, setm, t, U); return;
-    case MK_HAD: launch_kind<R, MK_HAD>(s, nins, p0, p1, setm, t, U); return;
+    case MK_GENERAL: launch_kind<R, MK_GENERAL>(s, nins, p0, p1, setm, t, G); return;
+    case MK_REAL: launch_kind<R, MK_REAL>(s, nins, p0, p1, setm, t, G); return;
+    case MK_DIAG: launch_kind<R, MK_DIAG>(s, nins, p0, p1, setm, t, G); return;
+    case MK_PHASE1: launch_kind<R, MK_PHASE1>(s, nins, p0, p1, setm, t, G); return;
+    case MK_PH_NEG: launch_kind<R, MK_PH_NEG>(s, nins, p0, p1, setm, t, G); return;
+    case MK_PH_I: launch_kind<R, MK_PH_I>(s, nins, p0, p1, setm, t, G); return;
+    case MK_PH_MI: launch_kind<R, MK_PH_MI>(s, nins, p0, p1, setm, t, G); return;
+    case MK_ANTI: launch_kind<R, MK_ANTI>(s, nins, p0, p1, setm, t, G); return;
+    case MK_SWAPX: launch_kind<R, MK_SWAPX>(s, nins, p0, p1, setm, t, G); return;
+    case MK_HAD: launch_kind<R, MK_HAD>(s, nins, p0, p1, setm, t, G); return;
   }
 }
 
@@ -181,11 +239,14 @@ qc_status launch_swap(qc_state* s, int a, int b) {
   const uint64_t nq = (1ull << s->n) >> 2;
   const int T = 256;
   if (s->dt == QC_C128) {
-    k_swap<double2><<<grid_for(nq, T, 8), T, 0, s->stream>>>(reinterpret_cast<double2*>(s->data), nq, lo, hi, a, b);
+    k_swap<double2><<<resident_grid(k_swap<double2>, T, nq, T), T, 0, s->stream>>>(
+        reinterpret_cast<double2*>(s->data), nq, lo, hi, a, b);
   } else if (lo >= 1 && nq >= 2) {
-    k_swap_v2<<<grid_for(nq / 2, T, 8), T, 0, s->stream>>>(reinterpret_cast<float2*>(s->data), nq / 2, lo, hi, a, b);
+    k_swap_v2<<<resident_grid(k_swap_v2, T, nq / 2, T), T, 0, s->stream>>>(reinterpret_cast<float2*>(s->data),
+                                                                            nq / 2, lo, hi, a, b);
   } else {
-    k_swap<float2><<<grid_for(nq, T, 8), T, 0, s->stream>>>(reinterpret_cast<float2*>(s->data), nq, lo, hi, a, b);
+    k_swap<float2><<<resident_grid(k_swap<float2>, T, nq, T), T, 0, s->stream>>>(
+        reinterpret_cast<float2*>(s->data), nq, lo, hi, a, b);
   }
   s->sum_valid = false;
   return check_launch("swap");

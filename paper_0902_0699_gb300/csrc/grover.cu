@@ -57,20 +57,24 @@ __global__ void k_grover_prep(const typename CT<R>::V2* __restrict__ s, uint64_t
   }
 }
 
-// C -> 2m - C over the whole state.
+// C -> 2m - C over the whole state.  Real parts on the FP64 pipe, imaginary
+// parts in double-float on the FP32 pipe, so that neither pipe limits the
+// pass (GB300's FP64 rate allows under 2.5 operations per amplitude at HBM
+// speed).
+__device__ __forceinline__ double2 grover_c128(double2 a, double tr, ff ti) {
+  return make_double2(tr - a.x, ff_to_d(ff_sub(ti, ff_from_d(a.y))));
+}
 __global__ void __launch_bounds__(256) k_grover_pass_c128(double2* __restrict__ s, uint64_t N, const double* __restrict__ scr) {
-  const double tr = 2.0 * scr[QC_SCR_MEAN], ti = 2.0 * scr[QC_SCR_MEAN + 1];
+  const double tr = 2.0 * scr[QC_SCR_MEAN];
+  const ff ti = ff_from_d(2.0 * scr[QC_SCR_MEAN + 1]);
   const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
   uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (; i + G < N; i += 2 * G) {
     double2 a = s[i], b = s[i + G];
-    s[i] = make_double2(tr - a.x, ti - a.y);
-    s[i + G] = make_double2(tr - b.x, ti - b.y);
+    s[i] = grover_c128(a, tr, ti);
+    s[i + G] = grover_c128(b, tr, ti);
   }
-  if (i < N) {
-    double2 a = s[i];
-    s[i] = make_double2(tr - a.x, ti - a.y);
-  }
+  if (i < N) s[i] = grover_c128(s[i], tr, ti);
 }
 
 __global__ void __launch_bounds__(256) k_grover_pass_c64(float4* __restrict__ s, uint64_t N2, const double* __restrict__ scr) {
@@ -138,13 +142,15 @@ static qc_status step_with(qc_state* s, const MarkedList* dml) {
   const int T = 256;
   if (s->dt == QC_C128) {
     k_grover_prep<double><<<1, 256, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), N, dml, s->scratch);
-    k_grover_pass_c128<<<grid_for(N, 2 * T, 8), T, 0, s->stream>>>(reinterpret_cast<double2*>(s->data), N, s->scratch);
+    k_grover_pass_c128<<<resident_grid(k_grover_pass_c128, T, N, 2 * T), T, 0, s->stream>>>(
+        reinterpret_cast<double2*>(s->data), N, s->scratch);
     k_grover_fix<double><<<1, 256, 0, s->stream>>>(reinterpret_cast<double2*>(s->data), dml, s->scratch);
   } else {
     k_grover_prep<float><<<1, 256, 0, s->stream>>>(reinterpret_cast<const float2*>(s->data), N, dml, s->scratch);
     const uint64_t N2 = N / 2;
     if (N2 > 0)
-      k_grover_pass_c64<<<grid_for(N2, 2 * T, 8), T, 0, s->stream>>>(reinterpret_cast<float4*>(s->data), N2, s->scratch);
+      k_grover_pass_c64<<<resident_grid(k_grover_pass_c64, T, N2, 2 * T), T, 0, s->stream>>>(
+          reinterpret_cast<float4*>(s->data), N2, s->scratch);
     k_grover_fix<float><<<1, 256, 0, s->stream>>>(reinterpret_cast<float2*>(s->data), dml, s->scratch);
   }
   return check_launch("grover step", 3);
