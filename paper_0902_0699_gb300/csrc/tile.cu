@@ -6,43 +6,146 @@
 // pass: a CTA stages a tile -- all 2^k values of the group bits, times the
 // 2^c lowest index bits kept contiguous for 128-byte rows -- in shared
 // memory, applies the group's gates there, and writes the tile back.
-// HALL (Eq. HALL) and layers of one-qubit operators take ceil(n / k)-ish
-// passes instead of n.
+// HALL (Eq. HALL) and layers of one-qubit operators take a few passes
+// instead of n.  Hadamards are applied as unnormalised butterflies
+// (a0 + a1, a0 - a1) and the pass multiplies by 2^{-p/2} once at the end.
 //
 // The QFT circuit of Appendix A processes qubits from the most significant
 // down: Hadamard on t, then CPHASEK(t, t') for every lower t' with phase
 // e^{2 pi i / 2^{t-t'+1}}.  For a group [lo, hi] the phases with t' inside
 // the group are applied right after the group's Hadamard on t (a diagonal
-// "ladder"); those with t' < lo commute with the rest of the group's gates
-// and are applied at the end of the pass as one twiddle factor
-//   exp(2 pi i * L * f / 2^{hi+1}),  L = index bits below lo,
-//   f = the group bits in reversed order,
-// read from two tables of 2^n-th roots of unity.  The final SWAPs are one
-// in-place blocked bit-reversal pass.
+// "ladder" e^{2 pi i x / 2^{j+1}}, x = group bits below group qubit j);
+// those with t' < lo commute with the rest of the group's gates and are
+// applied at the end of the pass as one twiddle factor
+//   Omega_{hi+1}^{L f},  Omega_m = e^{2 pi i / 2^m},
+//   L = index bits below lo, f = the group bits in reversed order.
+// With L = Ltile + l (Ltile fixed per tile, l the c contiguous low bits)
+// the twiddle is V[f] * Omega^{l f}: V is built once per tile from global
+// root tables, Omega^{l f} (l f < 2^{c+k}) comes from a two-level table in
+// shared memory, the ladder phases from a direct table.  The final SWAPs
+// are one in-place blocked bit-reversal pass.
+//
+// complex64 tiles compute in FP32.  complex128 tiles compute in double-float
+// (ff.cuh) on the FP32 pipe: the FP64 pipe of GB300 (0.5 Top/s) would
+// otherwise bound every pass many times over the memory time.
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace qc {
 
-enum TileOpKind { TOP_U2 = 0, TOP_QFTLEVEL = 1 };
+enum TileOpKind { TOP_U2 = 0, TOP_QFTLEVEL = 1, TOP_HB = 2 };
 #define QC_TILE_MAXOPS 36
+
+// ------------------------------------------------ arithmetic policies ----
+template <typename R> struct TA;
+
+template <> struct TA<float> {
+  using E = Cx<float>;
+  using V2 = float2;
+  using M = Mat2<float>;
+  static M mat(const double* U) { return mat_from_host<float>(U); }
+  __device__ static E from(V2 v) { return cmake<float>(v.x, v.y); }
+  __device__ static V2 to(E z) { return make_float2(z.re, z.im); }
+  __device__ static E add(E a, E b) { return cmake<float>(a.re + b.re, a.im + b.im); }
+  __device__ static E sub(E a, E b) { return cmake<float>(a.re - b.re, a.im - b.im); }
+  __device__ static E mul(E a, E b) { return cmul(a, b); }
+  __device__ static E root(uint64_t num, int m) {  // e^{2 pi i num / 2^m}
+    double s, c;
+    sincospi(ldexp((double)num, 1 - m), &s, &c);
+    return cmake<float>((float)c, (float)s);
+  }
+  __device__ static E fromd(double re, double im) { return cmake<float>((float)re, (float)im); }
+  // 2^{-p/2}, computed once per thread, and the multiplication by it
+  using S = float;
+  __device__ static S scale_const(int p) { return (float)exp2(-0.5 * p); }
+  __device__ static E scale_by(E a, S s) { return cmake<float>(a.re * s, a.im * s); }
+  __device__ static void u2(int kind, const M& U, E& a0, E& a1) {
+    switch (kind) {
+      case MK_GENERAL: apply2<float, MK_GENERAL>(U, a0, a1); break;
+      case MK_REAL: apply2<float, MK_REAL>(U, a0, a1); break;
+      case MK_DIAG: apply2<float, MK_DIAG>(U, a0, a1); break;
+      case MK_PHASE1: apply2<float, MK_PHASE1>(U, a0, a1); break;
+      case MK_PH_NEG: apply2<float, MK_PH_NEG>(U, a0, a1); break;
+      case MK_PH_I: apply2<float, MK_PH_I>(U, a0, a1); break;
+      case MK_PH_MI: apply2<float, MK_PH_MI>(U, a0, a1); break;
+      case MK_ANTI: apply2<float, MK_ANTI>(U, a0, a1); break;
+      case MK_SWAPX: apply2<float, MK_SWAPX>(U, a0, a1); break;
+      case MK_HAD: apply2<float, MK_HAD>(U, a0, a1); break;
+      default: break;
+    }
+  }
+};
+
+template <> struct TA<double> {
+  using E = ffc;
+  using V2 = double2;
+  using M = Mat2ff;
+  static M mat(const double* U) { return mat2ff_from_host(U); }
+  __device__ static E from(V2 v) { return ffc_from_d(v.x, v.y); }
+  __device__ static V2 to(E z) { return make_double2(ff_to_d(z.re), ff_to_d(z.im)); }
+  __device__ static E add(E a, E b) { return ffc_add(a, b); }
+  __device__ static E sub(E a, E b) { return ffc_sub(a, b); }
+  __device__ static E mul(E a, E b) { return ffc_mul(a, b); }
+  __device__ static E root(uint64_t num, int m) {
+    double s, c;
+    sincospi(ldexp((double)num, 1 - m), &s, &c);
+    return ffc_from_d(c, s);
+  }
+  __device__ static E fromd(double re, double im) { return ffc_from_d(re, im); }
+  // 2^{-p/2} = 2^{-floor(p/2)} (exact) times 1/sqrt(2) when p is odd
+  using S = ff;
+  __device__ static S scale_const(int p) {
+    ff s = ff_make(ff_bitsf((uint32_t)(127 - p / 2) << 23), 0.f);
+    if (p & 1) s = ff_mul(s, ff_from_d(0.70710678118654752440));
+    return s;
+  }
+  __device__ static E scale_by(E a, S s) { return ffc_scale(a, s); }
+  __device__ static void u2(int kind, const M& U, E& a0, E& a1) {
+    switch (kind) {
+      case MK_GENERAL: apply2_ff<MK_GENERAL>(U, a0, a1); break;
+      case MK_REAL: apply2_ff<MK_REAL>(U, a0, a1); break;
+      case MK_DIAG: apply2_ff<MK_DIAG>(U, a0, a1); break;
+      case MK_PHASE1: apply2_ff<MK_PHASE1>(U, a0, a1); break;
+      case MK_ANTI: apply2_ff<MK_ANTI>(U, a0, a1); break;
+      case MK_HAD: apply2_ff<MK_HAD>(U, a0, a1); break;
+      case MK_PH_NEG: a1 = ffc_make(ff_neg(a1.re), ff_neg(a1.im)); break;
+      case MK_PH_I: a1 = ffc_make(ff_neg(a1.im), a1.re); break;
+      case MK_PH_MI: a1 = ffc_make(a1.im, ff_neg(a1.re)); break;
+      case MK_SWAPX: {
+        const E t = a0;
+        a0 = a1;
+        a1 = t;
+        break;
+      }
+      default: break;
+    }
+  }
+};
 
 template <typename R> struct TileProg {
   int nops;
-  int lo, k, c;   // group [lo, lo+k), c low contiguous bits (c <= lo)
+  int lo, k, c;     // group [lo, lo+k), c low contiguous bits (c <= lo)
   int n;
-  int twiddle;    // apply the QFT cross phase with the bits below lo
-  int nl;         // twiddle table split: low table has 2^nl entries
+  int twiddle;      // apply the QFT cross phase with the bits below lo
+  int qft;          // the program contains QFT levels (build the ladder table)
+  int nl;           // global root table split: low table has 2^nl entries
+  int scale_p;      // unnormalised butterflies: multiply by 2^{-scale_p/2} at the end
   int8_t kind[QC_TILE_MAXOPS];
   int8_t q[QC_TILE_MAXOPS];   // group-relative qubit
   int8_t mk[QC_TILE_MAXOPS];  // MatKind of a TOP_U2 operator
-  Mat2<R> U[QC_TILE_MAXOPS];
+  typename TA<R>::M U[QC_TILE_MAXOPS];
 };
 
-template <typename R>
+// Shared memory after the tile: V[2^k] (twiddle passes), LAD[2^k - 1]
+// (QFT passes: level j's 2^j ladder phases e^{2 pi i x / 2^{j+1}} at
+// LAD[2^j - 1 + x], so a warp reads consecutive entries), TWA[128], TWB[64].
+#define TS_TWA 128
+#define TS_TWB 64
+
 __device__ __forceinline__ uint64_t tile_global(uint64_t e, uint64_t T, int lo, int k, int c) {
   const uint64_t cm = (1ull << c) - 1ull;
   const uint64_t tmid = T & ((1ull << (lo - c)) - 1ull);
@@ -50,109 +153,165 @@ __device__ __forceinline__ uint64_t tile_global(uint64_t e, uint64_t T, int lo, 
   return (e & cm) | (tmid << c) | ((e >> c) << lo) | (thi << (lo + k));
 }
 
-template <typename R, int KIND>
-__device__ __forceinline__ void tile_u2(Cx<R>* sm, int E, int b, const Mat2<R>& U) {
-  for (int p = threadIdx.x; p < (E >> 1); p += blockDim.x) {
-    const int e0 = (int)insert0((uint64_t)p, b), e1 = e0 | (1 << b);
-    Cx<R> a0 = sm[e0], a1 = sm[e1];
-    apply2<R, KIND>(U, a0, a1);
-    sm[e0] = a0;
-    sm[e1] = a1;
-  }
-}
-
-// Root of unity Omega^r, Omega = e^{2 pi i / 2^n}, from the two tables.
+// Root of unity Omega_n^r from the two global tables.
 template <typename R>
-__device__ __forceinline__ Cx<R> omega(const typename CT<R>::V2* __restrict__ tlo,
-                                       const typename CT<R>::V2* __restrict__ thi, uint64_t r, int nl) {
+__device__ __forceinline__ typename TA<R>::E omega(const typename CT<R>::V2* __restrict__ tlo,
+                                                   const typename CT<R>::V2* __restrict__ thi, uint64_t r, int nl) {
   const auto a = tlo[r & ((1ull << nl) - 1ull)];
   const auto b = thi[r >> nl];
-  return cmul(cmake<R>(a.x, a.y), cmake<R>(b.x, b.y));
+  return TA<R>::mul(TA<R>::from(a), TA<R>::from(b));
 }
 
 template <typename R>
 __global__ void __launch_bounds__(512) k_tile(typename CT<R>::V2* __restrict__ s, uint64_t ntiles,
                                               const TileProg<R> P, const typename CT<R>::V2* __restrict__ tlo,
                                               const typename CT<R>::V2* __restrict__ thi) {
+  using A = TA<R>;
+  using E = typename A::E;
   using V2 = typename CT<R>::V2;
   extern __shared__ __align__(16) unsigned char smraw[];
-  Cx<R>* sm = reinterpret_cast<Cx<R>*>(smraw);
+  E* sm = reinterpret_cast<E*>(smraw);
   const int lo = P.lo, k = P.k, c = P.c;
-  const int E = 1 << (k + c);
+  const int NE = 1 << (k + c);
+  E* V = sm + NE;
+  E* LAD = V + (P.twiddle ? (1 << k) : 0);
+  E* TWA = LAD + (P.qft ? ((1 << k) - 1) : 0);
+  E* TWB = TWA + TS_TWA;
+  const int hi = lo + k - 1;
+  const typename A::S sc = A::scale_const(P.scale_p);
+  if (P.qft) {
+    // ladder tables, one per level: LAD[2^j - 1 + x] = e^{2 pi i x / 2^{j+1}}
+    for (int a = threadIdx.x; a < (1 << k) - 1; a += blockDim.x) {
+      const int j = 31 - __clz(a + 1);
+      LAD[a] = A::root((uint64_t)(a + 1 - (1 << j)), j + 1);
+    }
+    // twiddle remainder: Omega_{hi+1}^x = TWA[x & 127] * TWB[x >> 7], x < 2^{c+k}
+    if (P.twiddle)
+      for (int i = threadIdx.x; i < TS_TWA + TS_TWB; i += blockDim.x) {
+        if (i < TS_TWA) TWA[i] = A::root((uint64_t)i, hi + 1);
+        else TWB[i - TS_TWA] = A::root((uint64_t)(i - TS_TWA) << 7, hi + 1);
+      }
+  }
   for (uint64_t T = blockIdx.x; T < ntiles; T += gridDim.x) {
+    if (P.twiddle) {
+      // V[f] = 2^{-p/2} Omega_{hi+1}^{Ltile f}, Ltile = the tile's bits between c and lo
+      const uint64_t Lt = (T & ((1ull << (lo - c)) - 1ull)) << c;
+      for (int f = threadIdx.x; f < (1 << k); f += blockDim.x) {
+        const uint64_t r = (Lt * (uint64_t)f) & ((2ull << hi) - 1ull);
+        V[f] = A::scale_by(omega<R>(tlo, thi, r << (P.n - hi - 1), P.nl), sc);
+      }
+    }
     // load: 16-byte vectors; for complex64 two neighbouring elements (c >= 1
     // or a fully contiguous tile, so e and e+1 are neighbours in memory)
     if (sizeof(R) == 8) {
-      for (int e = threadIdx.x; e < E; e += blockDim.x) {
-        const V2 v = s[tile_global<R>(e, T, lo, k, c)];
-        sm[e] = cmake<R>(v.x, v.y);
-      }
+      for (int e = threadIdx.x; e < NE; e += blockDim.x) sm[e] = A::from(s[tile_global(e, T, lo, k, c)]);
     } else {
-      for (int e = 2 * threadIdx.x; e < E; e += 2 * blockDim.x) {
-        const float4 v = *reinterpret_cast<const float4*>(s + tile_global<R>(e, T, lo, k, c));
-        sm[e] = cmake<R>(v.x, v.y);
-        sm[e + 1] = cmake<R>(v.z, v.w);
+      for (int e = 2 * threadIdx.x; e < NE; e += 2 * blockDim.x) {
+        const float4 v = *reinterpret_cast<const float4*>(s + tile_global(e, T, lo, k, c));
+        sm[e] = A::from(CT<R>::make(v.x, v.y));
+        sm[e + 1] = A::from(CT<R>::make(v.z, v.w));
       }
     }
     __syncthreads();
     for (int o = 0; o < P.nops; ++o) {
       const int b = c + P.q[o];
-      if (P.kind[o] == TOP_U2) {
-        switch (P.mk[o]) {
-          case MK_GENERAL: tile_u2<R, MK_GENERAL>(sm, E, b, P.U[o]); break;
-          case MK_REAL: tile_u2<R, MK_REAL>(sm, E, b, P.U[o]); break;
-          case MK_DIAG: tile_u2<R, MK_DIAG>(sm, E, b, P.U[o]); break;
-          case MK_PHASE1: tile_u2<R, MK_PHASE1>(sm, E, b, P.U[o]); break;
-          case MK_ANTI: tile_u2<R, MK_ANTI>(sm, E, b, P.U[o]); break;
-          case MK_SWAPX: tile_u2<R, MK_SWAPX>(sm, E, b, P.U[o]); break;
-          case MK_HAD: tile_u2<R, MK_HAD>(sm, E, b, P.U[o]); break;
-          default: break;
+      const int kind = P.kind[o];
+      // two butterfly levels on neighbouring qubits: one shared-memory round
+      // trip (radix 4).  QFT levels come in descending order j, j-1; plain
+      // Hadamard butterflies commute, so any neighbouring pair qualifies.
+      if (kind != TOP_U2 && o + 1 < P.nops && P.kind[o + 1] == kind &&
+          (P.q[o + 1] == P.q[o] - 1 || (kind == TOP_HB && P.q[o + 1] == P.q[o] + 1))) {
+        const int jh = max(P.q[o], P.q[o + 1]), jl = jh - 1;  // levels jh then jl
+        const int bh = c + jh, bl = c + jl;
+        const bool lad = (kind == TOP_QFTLEVEL);
+        for (int p = threadIdx.x; p < (NE >> 2); p += blockDim.x) {
+          const int e00 = (int)insert0(insert0((uint64_t)p, bl), bh);
+          const int e01 = e00 | (1 << bl), e10 = e00 | (1 << bh), e11 = e01 | (1 << bh);
+          const E a00 = sm[e00], a01 = sm[e01], a10 = sm[e10], a11 = sm[e11];
+          // level jh on bit bh: pairs (e00, e10), (e01, e11)
+          E s0 = A::add(a00, a10), d0 = A::sub(a00, a10);
+          E s1 = A::add(a01, a11), d1 = A::sub(a01, a11);
+          const int xl = (e00 >> c) & ((1 << jl) - 1);  // group bits below jl
+          if (lad) {
+            const int x0 = xl, x1 = xl | (1 << jl);  // group bits below jh
+            if (x0) d0 = A::mul(LAD[(1 << jh) - 1 + x0], d0);
+            d1 = A::mul(LAD[(1 << jh) - 1 + x1], d1);
+          }
+          // level jl on bit bl: pairs (s0, s1), (d0, d1)
+          E t0 = A::add(s0, s1), u0 = A::sub(s0, s1);
+          E t1 = A::add(d0, d1), u1 = A::sub(d0, d1);
+          if (lad && xl) {
+            const E w = LAD[(1 << jl) - 1 + xl];
+            u0 = A::mul(w, u0);
+            u1 = A::mul(w, u1);
+          }
+          sm[e00] = t0;
+          sm[e01] = u0;
+          sm[e10] = t1;
+          sm[e11] = u1;
+        }
+        __syncthreads();
+        ++o;
+        continue;
+      }
+      if (kind == TOP_U2) {
+        const int mk = P.mk[o];
+        for (int p = threadIdx.x; p < (NE >> 1); p += blockDim.x) {
+          const int e0 = (int)insert0((uint64_t)p, b), e1 = e0 | (1 << b);
+          E a0 = sm[e0], a1 = sm[e1];
+          A::u2(mk, P.U[o], a0, a1);
+          sm[e0] = a0;
+          sm[e1] = a1;
         }
       } else {
-        // Hadamard on group qubit j, then the ladder phase
-        // e^{2 pi i x / 2^{j+1}} on the bit-1 half, x = group bits below j.
+        // unnormalised butterfly (a0 + a1, a0 - a1); for a QFT level the
+        // bit-1 half then takes the ladder phase e^{2 pi i x / 2^{j+1}}
+        // = omega_k^{x 2^{k-j-1}}, x = group bits below group qubit j
         const int j = P.q[o];
-        const R h = (R)0.70710678118654752440;
-        for (int p = threadIdx.x; p < (E >> 1); p += blockDim.x) {
+        const bool lad = (kind == TOP_QFTLEVEL);
+        for (int p = threadIdx.x; p < (NE >> 1); p += blockDim.x) {
           const int e0 = (int)insert0((uint64_t)p, b), e1 = e0 | (1 << b);
-          const Cx<R> a0 = sm[e0], a1 = sm[e1];
-          const R qr = h * a1.re, qi = h * a1.im;
-          Cx<R> b1 = cmake<R>(fma(h, a0.re, -qr), fma(h, a0.im, -qi));
-          sm[e0] = cmake<R>(fma(h, a0.re, qr), fma(h, a0.im, qi));
-          const uint64_t x = (uint64_t)((e0 >> c) & ((1 << j) - 1));
-          if (x) b1 = cmul(omega<R>(tlo, thi, x << (P.n - j - 1), P.nl), b1);
-          sm[e1] = b1;
+          const E a0 = sm[e0], a1 = sm[e1];
+          sm[e0] = A::add(a0, a1);
+          E d = A::sub(a0, a1);
+          if (lad) {
+            const int x = (e0 >> c) & ((1 << j) - 1);
+            if (x) d = A::mul(LAD[(1 << j) - 1 + x], d);
+          }
+          sm[e1] = d;
         }
       }
       __syncthreads();
     }
-    // store (with the QFT cross twiddle when requested)
-    const int hi = lo + k - 1;
+    // store: twiddle (which carries the 2^{-p/2} scale) or the bare scale
     if (sizeof(R) == 8) {
-      for (int e = threadIdx.x; e < E; e += blockDim.x) {
-        const uint64_t g = tile_global<R>(e, T, lo, k, c);
-        Cx<R> z = sm[e];
+      for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+        E z = sm[e];
         if (P.twiddle) {
-          const uint64_t L = g & ((1ull << lo) - 1ull);
-          const uint64_t f = __brevll((unsigned long long)(e >> c)) >> (64 - k);
-          const uint64_t r = L * f;  // < 2^{hi+1}
-          if (r) z = cmul(omega<R>(tlo, thi, r << (P.n - hi - 1), P.nl), z);
+          const int f = (int)(__brev((unsigned)(e >> c)) >> (32 - k));
+          const int x = (e & ((1 << c) - 1)) * f;  // < 2^{c+k}
+          z = A::mul(A::mul(V[f], A::mul(TWA[x & 127], TWB[x >> 7])), z);
+        } else if (P.scale_p) {
+          z = A::scale_by(z, sc);
         }
-        s[g] = CT<R>::make(z.re, z.im);
+        s[tile_global(e, T, lo, k, c)] = A::to(z);
       }
     } else {
-      for (int e = 2 * threadIdx.x; e < E; e += 2 * blockDim.x) {
-        const uint64_t g = tile_global<R>(e, T, lo, k, c);
-        Cx<R> z0 = sm[e], z1 = sm[e + 1];
+      for (int e = 2 * threadIdx.x; e < NE; e += 2 * blockDim.x) {
+        E z0 = sm[e], z1 = sm[e + 1];
         if (P.twiddle) {
-          const uint64_t L = g & ((1ull << lo) - 1ull);
-          const uint64_t f0 = __brevll((unsigned long long)(e >> c)) >> (64 - k);
-          const uint64_t f1 = __brevll((unsigned long long)((e + 1) >> c)) >> (64 - k);
-          const uint64_t r0 = L * f0, r1 = (L + ((c > 0) ? 1 : 0)) * f1;
-          if (r0) z0 = cmul(omega<R>(tlo, thi, r0 << (P.n - hi - 1), P.nl), z0);
-          if (r1) z1 = cmul(omega<R>(tlo, thi, r1 << (P.n - hi - 1), P.nl), z1);
+          // e and e+1 share the group bits (c >= 1 whenever lo > 0)
+          const int f = (int)(__brev((unsigned)(e >> c)) >> (32 - k));
+          const int x0 = (e & ((1 << c) - 1)) * f, x1 = x0 + f;
+          const E v = V[f];
+          z0 = A::mul(A::mul(v, A::mul(TWA[x0 & 127], TWB[x0 >> 7])), z0);
+          z1 = A::mul(A::mul(v, A::mul(TWA[x1 & 127], TWB[x1 >> 7])), z1);
+        } else if (P.scale_p) {
+          z0 = A::scale_by(z0, sc);
+          z1 = A::scale_by(z1, sc);
         }
-        *reinterpret_cast<float4*>(s + g) = make_float4(z0.re, z0.im, z1.re, z1.im);
+        const V2 w0 = A::to(z0), w1 = A::to(z1);
+        *reinterpret_cast<float4*>(s + tile_global(e, T, lo, k, c)) = make_float4(w0.x, w0.y, w1.x, w1.y);
       }
     }
     __syncthreads();
@@ -183,8 +342,8 @@ __global__ void k_roots(typename CT<R>::V2* tlo, typename CT<R>::V2* thi, int n,
 // Tile-size choices: c low contiguous bits give 128-byte rows; k group bits;
 // the tile holds 2^{k+c} amplitudes (64 KiB).
 template <typename R> struct TileCfg;
-template <> struct TileCfg<double> { static constexpr int C = 3, K = 9; };
-template <> struct TileCfg<float> { static constexpr int C = 4, K = 9; };
+template <> struct TileCfg<double> { static constexpr int C = 3, K = 9, BOT = 12; };
+template <> struct TileCfg<float> { static constexpr int C = 4, K = 9, BOT = 12; };
 
 struct Group {
   int lo, k;
@@ -196,7 +355,8 @@ template <typename R>
 static std::vector<Group> plan_groups(int n) {
   const int C = TileCfg<R>::C, K = TileCfg<R>::K;
   std::vector<Group> g;
-  const int g0 = std::min(n, C + K);
+  (void)C;
+  const int g0 = std::min(n, TileCfg<R>::BOT);
   g.push_back({0, g0});
   int rest = n - g0;
   if (rest > 0) {
@@ -213,6 +373,13 @@ static std::vector<Group> plan_groups(int n) {
 }
 
 template <typename R>
+static size_t tile_smem(int k, int c, bool twiddle, bool qft) {
+  using E = typename TA<R>::E;
+  return sizeof(E) * (((size_t)1 << (k + c)) + (twiddle ? ((size_t)1 << k) : 0) +
+                      (qft ? ((size_t)1 << k) - 1 : 0) + TS_TWA + TS_TWB);
+}
+
+template <typename R>
 static qc_status run_tile(qc_state* s, TileProg<R>& P, const typename CT<R>::V2* tlo,
                           const typename CT<R>::V2* thi) {
   using V2 = typename CT<R>::V2;
@@ -220,14 +387,14 @@ static qc_status run_tile(qc_state* s, TileProg<R>& P, const typename CT<R>::V2*
   P.n = s->n;
   const int tb = P.k + P.c;
   const uint64_t ntiles = 1ull << (s->n - tb);
-  const size_t smem = sizeof(Cx<R>) << tb;
+  const size_t smem = tile_smem<R>(P.k, P.c, P.twiddle != 0, P.qft != 0);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_tile<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   const int threads = 512;
-  const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)sm_count() * 3);
+  const unsigned grid = resident_grid(k_tile<R>, threads, (int64_t)ntiles, 1, smem);
   k_tile<R><<<grid, threads, smem, s->stream>>>(reinterpret_cast<V2*>(s->data), ntiles, P, tlo, thi);
   return check_launch("tile pass");
 }
@@ -241,7 +408,16 @@ static void prog_init(TileProg<R>& P, const Group& g, int n) {
   P.c = std::min(C, g.lo);
   P.n = n;
   P.twiddle = 0;
+  P.qft = 0;
   P.nl = 0;
+  P.scale_p = 0;
+}
+
+// Hadamards (operators that are exactly h [[1,1],[1,-1]] with h = 1/sqrt 2)
+// become unnormalised butterflies with the scale deferred to the store.
+static bool is_exact_hadamard(const double* u) {
+  const double h = 1.0 / sqrt(2.0);
+  return u[0] == h && u[2] == h && u[4] == h && u[6] == -h && u[1] == 0 && u[3] == 0 && u[5] == 0 && u[7] == 0;
 }
 
 template <typename R>
@@ -254,10 +430,16 @@ static qc_status layer_impl(qc_state* s, const double* U, uint64_t mask) {
       if (!((mask >> q) & 1)) continue;
       const MatKind mk = classify(U + 8 * q);
       if (mk == MK_IDENT) continue;
-      P.kind[P.nops] = TOP_U2;
       P.q[P.nops] = (int8_t)j;
-      P.mk[P.nops] = (int8_t)mk;
-      P.U[P.nops] = mat_from_host<R>(U + 8 * q);
+      if (is_exact_hadamard(U + 8 * q)) {
+        P.kind[P.nops] = TOP_HB;
+        P.mk[P.nops] = 0;
+        ++P.scale_p;
+      } else {
+        P.kind[P.nops] = TOP_U2;
+        P.mk[P.nops] = (int8_t)mk;
+        P.U[P.nops] = TA<R>::mat(U + 8 * q);
+      }
       ++P.nops;
     }
     qc_status st = run_tile<R>(s, P, nullptr, nullptr);
@@ -349,7 +531,7 @@ static qc_status bitrev_impl(qc_state* s) {
   }
   const size_t smem = 2 * (size_t)(1 << b) * ((1 << b) + 1) * sizeof(V2);
   const uint64_t M = 1ull << (n - 2 * b);
-  const unsigned grid = (unsigned)std::min<uint64_t>(M, (uint64_t)sm_count() * 8);
+  const unsigned grid = resident_grid(k_bitrev<R>, 256, (int64_t)M, 1, smem);
   k_bitrev<R><<<grid, 256, smem, s->stream>>>(d, n, b);
   return check_launch("bitrev");
 }
@@ -376,12 +558,14 @@ static qc_status qft_impl(qc_state* s) {
     TileProg<R> P;
     prog_init(P, g, n);
     P.nl = nl;
+    P.qft = 1;
     for (int j = g.k - 1; j >= 0; --j) {
       P.kind[P.nops] = TOP_QFTLEVEL;
       P.q[P.nops] = (int8_t)j;
       P.mk[P.nops] = 0;
       ++P.nops;
     }
+    P.scale_p = g.k;
     P.twiddle = g.lo > 0;
     st = run_tile<R>(s, P, tlo, thi);
   }
