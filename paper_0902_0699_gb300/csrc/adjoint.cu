@@ -1,15 +1,19 @@
 // Parameterised circuits on a batch of states and the adjoint gradient of
 // E = <psi|H|psi> (not part of the QCMPI paper).
 //
-// Forward: psi_b = U_G .. U_1 |0..0>, one batched kernel per gate (grid.y is
-// the batch element, so each block builds its element's rotation matrix
-// once).  Backward: lambda = H psi (one gather pass over the Pauli terms),
-// E = Re <psi|lambda>, then for j = G .. 1 a single fused pass per gate
-// reads psi_j and lambda_j, accumulates Im <lambda_j|P_j|psi_j> (the
-// derivative of U_j = exp(-i theta P_j / 2) gives
-// dE/dtheta_j = 2 Re <lambda_j|(-i/2) P_j|psi_j> = Im <lambda_j|P_j|psi_j>)
-// and applies U_j^dagger to both.  No intermediate state is stored: psi is
-// uncomputed instead of checkpointed.
+// The gate list is first compiled into passes: two consecutive rotations on
+// the same qubit become one pass, and a full CNOT ring CNOT(0,1), CNOT(1,2),
+// .., CNOT(n-1,0) -- a permutation of basis indices (prefix parity) --
+// becomes one gather pass; any other gate is a pass of its own.  Batch
+// element b is grid.y, so each block builds its element's matrices once.
+//
+// Forward: psi_b = U_G .. U_1 |0..0>.  Backward: lambda = H psi (one gather
+// pass over the Pauli terms), E = Re <psi|lambda>, then the passes are
+// walked in reverse; a rotation pass reads psi_j and lambda_j, accumulates
+// Im <lambda_j|P_j|psi_j> -- the derivative of U_j = exp(-i theta P_j / 2)
+// gives dE/dtheta_j = 2 Re <lambda_j|(-i/2) P_j|psi_j> = Im <lambda_j|P_j|psi_j>
+// -- and applies U_j^dagger to both.  No intermediate state is stored: psi
+// is uncomputed instead of checkpointed.
 //
 // Accumulation is FP64: complex128 with FMA in double; complex64 products
 // are formed exactly with the FP32 two-product and summed as float pairs
@@ -29,7 +33,7 @@ struct GateDev {
   int kind, q0, q1, param;
 };
 
-// Rotation matrices exp(-i sgn theta P / 2) for P = X, Y, Z; H.
+// Rotation matrices exp(-i theta P / 2) for P = X, Y, Z; H.
 template <typename R>
 __device__ __forceinline__ Mat2<R> gate_matrix(int kind, double theta) {
   Mat2<R> U;
@@ -62,6 +66,29 @@ __device__ __forceinline__ Mat2<R> gate_matrix(int kind, double theta) {
   return U;
 }
 
+// The block's matrix for (kind, theta), or the product U_b U_a of two: one
+// thread evaluates the FP64 sines and cosines (costly on GB300's FP64 pipe)
+// and the block reads the result from shared memory.
+template <typename R>
+__device__ __forceinline__ Mat2<R> block_matrix(int ka, double tha, int kb = -1, double thb = 0.0) {
+  __shared__ Mat2<double> sh;
+  if (threadIdx.x == 0) {
+    const Mat2<double> A = gate_matrix<double>(ka, tha);
+    if (kb < 0) {
+      sh = A;
+    } else {
+      const Mat2<double> Bm = gate_matrix<double>(kb, thb);
+      for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) sh.m[2 * r + c] = cmul2(Bm.m[2 * r], A.m[c], Bm.m[2 * r + 1], A.m[2 + c]);
+    }
+  }
+  __syncthreads();
+  Mat2<R> U;
+  for (int k = 0; k < 4; ++k) U.m[k] = cmake<R>((R)sh.m[k].re, (R)sh.m[k].im);
+  __syncthreads();  // sh may be rewritten by a second call in the same kernel
+  return U;
+}
+
 template <typename R>
 __device__ __forceinline__ void apply_any(int kind, const Mat2<R>& U, Cx<R>& a0, Cx<R>& a1) {
   if (kind == QC_G_RY) apply2<R, MK_REAL>(U, a0, a1);
@@ -85,33 +112,6 @@ __device__ __forceinline__ uint64_t gate_pair(const GateDev& g, uint64_t p, uint
   return i0;
 }
 
-// ------------------------------------------------------------ forward ----
-template <typename R>
-__global__ void __launch_bounds__(ADJ_T) k_fwd_gate(typename CT<R>::V2* __restrict__ psi, int n, GateDev g,
-                                                    const double* __restrict__ theta, int64_t stride, double sgn) {
-  using IO = AmpIO<R>;
-  const int b = blockIdx.y;
-  typename CT<R>::V2* s = psi + ((uint64_t)b << n);
-  const double th = (g.kind <= QC_G_RZ) ? sgn * theta[(int64_t)b * stride + g.param] : 0.0;
-  const Mat2<R> U = gate_matrix<R>(g.kind, th);
-  const uint64_t np = (g.kind == QC_G_CNOT) ? (1ull << (n - 2)) : (1ull << (n - 1));
-  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t i1;
-    const uint64_t i0 = gate_pair(g, p, i1);
-    Cx<R> a0 = IO::ld(s + i0), a1 = IO::ld(s + i1);
-    apply_any<R>(g.kind, U, a0, a1);
-    IO::st(s + i0, a0);
-    IO::st(s + i1, a1);
-  }
-}
-
-template <typename R>
-__global__ void k_zero_state_batch(typename CT<R>::V2* __restrict__ psi, int n, int B) {
-  const uint64_t N = 1ull << n, tot = N * (uint64_t)B;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (uint64_t)gridDim.x * blockDim.x)
-    psi[i] = CT<R>::make((R)((i & (N - 1)) == 0 ? 1 : 0), (R)0);
-}
-
 // ----------------------------------------------------- accumulators ------
 template <typename R> struct Acc;
 template <> struct Acc<double> {
@@ -121,16 +121,17 @@ template <> struct Acc<double> {
   __device__ void flush() {}
   __device__ double value() const { return a; }
 };
+// complex64: products exact as float pairs (two-product), summed as a float
+// pair with two-sum (relative error ~ terms * 2^-48), converted to double
+// once per thread -- no FP64 instruction in the loop.
 template <> struct Acc<float> {
   double a = 0.0;
   float s = 0.f, c = 0.f;
-  int cnt = 0;
   __device__ void put(float p, float e) {
     const float t = s + p;
     const float bp = t - s;
     c += ((s - (t - bp)) + (p - bp)) + e;
     s = t;
-    if (++cnt == 32) flush();
   }
   __device__ void add(float x, float y) {
     const float p = x * y;
@@ -143,10 +144,26 @@ template <> struct Acc<float> {
   __device__ void flush() {
     a += (double)s + (double)c;
     s = c = 0.f;
-    cnt = 0;
   }
   __device__ double value() const { return a; }
 };
+
+// Accumulate Im <l|P|p> over one pair for the generator P of a rotation.
+template <typename R>
+__device__ __forceinline__ void acc_generator(Acc<R>& acc, int kind, const Cx<R>& p0, const Cx<R>& p1,
+                                              const Cx<R>& l0, const Cx<R>& l1) {
+  // Im(conj(a) b) = a.re b.im - a.im b.re
+  if (kind == QC_G_RZ) {  // Z: conj(l0) p0 - conj(l1) p1
+    acc.add(l0.re, p0.im); acc.sub(l0.im, p0.re);
+    acc.sub(l1.re, p1.im); acc.add(l1.im, p1.re);
+  } else if (kind == QC_G_RX) {  // X: conj(l0) p1 + conj(l1) p0
+    acc.add(l0.re, p1.im); acc.sub(l0.im, p1.re);
+    acc.add(l1.re, p0.im); acc.sub(l1.im, p0.re);
+  } else {  // Y: conj(l0)(-i p1) + conj(l1)(i p0); Im(conj(a)(-i b)) = -Re(conj(a) b)
+    acc.sub(l0.re, p1.re); acc.sub(l0.im, p1.im);
+    acc.add(l1.re, p0.re); acc.add(l1.im, p0.im);
+  }
+}
 
 __device__ __forceinline__ double block_reduce(double v) {
   __shared__ double sh[32];
@@ -160,6 +177,88 @@ __device__ __forceinline__ double block_reduce(double v) {
   return t;
 }
 
+// ------------------------------------------------------------ forward ----
+template <typename R>
+__global__ void __launch_bounds__(ADJ_T) k_fwd_gate(typename CT<R>::V2* __restrict__ psi, int n, GateDev g,
+                                                    const double* __restrict__ theta, int64_t stride) {
+  using IO = AmpIO<R>;
+  const int b = blockIdx.y;
+  typename CT<R>::V2* s = psi + ((uint64_t)b << n);
+  const double th = (g.kind <= QC_G_RZ) ? theta[(int64_t)b * stride + g.param] : 0.0;
+  const Mat2<R> U = block_matrix<R>(g.kind, th);
+  const uint64_t np = (g.kind == QC_G_CNOT) ? (1ull << (n - 2)) : (1ull << (n - 1));
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t i1;
+    const uint64_t i0 = gate_pair(g, p, i1);
+    Cx<R> a0 = IO::ld(s + i0), a1 = IO::ld(s + i1);
+    apply_any<R>(g.kind, U, a0, a1);
+    IO::st(s + i0, a0);
+    IO::st(s + i1, a1);
+  }
+}
+
+// Two rotations on one qubit, ga then gb: one pass with M = U_b U_a.
+template <typename R>
+__global__ void __launch_bounds__(ADJ_T) k_fwd_rot2(typename CT<R>::V2* __restrict__ psi, int n, GateDev ga,
+                                                    GateDev gb, const double* __restrict__ theta, int64_t stride) {
+  using IO = AmpIO<R>;
+  const int b = blockIdx.y;
+  typename CT<R>::V2* s = psi + ((uint64_t)b << n);
+  const Mat2<R> M = block_matrix<R>(ga.kind, theta[(int64_t)b * stride + ga.param], gb.kind,
+                                    theta[(int64_t)b * stride + gb.param]);
+  const int q = ga.q0;
+  const uint64_t np = 1ull << (n - 1);
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i0 = insert0(p, q), i1 = i0 | (1ull << q);
+    Cx<R> a0 = IO::ld(s + i0), a1 = IO::ld(s + i1);
+    apply2<R, MK_GENERAL>(M, a0, a1);
+    IO::st(s + i0, a0);
+    IO::st(s + i1, a1);
+  }
+}
+
+// CNOT ring CNOT(0,1) .. CNOT(n-2,n-1), CNOT(n-1,0) as a basis permutation
+// j -> A(j): A(j)_k = j_0 ^ .. ^ j_k for k >= 1 and A(j)_0 = j_1 ^ .. ^ j_{n-1}.
+__device__ __forceinline__ uint64_t ring_fwd(uint64_t x, int n) {
+  const uint64_t mask = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
+  uint64_t p = x;
+  p ^= (p << 1) & mask;
+  p ^= (p << 2) & mask;
+  p ^= (p << 4) & mask;
+  p ^= (p << 8) & mask;
+  p ^= (p << 16) & mask;
+  p ^= (p << 32) & mask;
+  const uint64_t top = (p >> (n - 1)) & 1ull;
+  return (p & ~1ull) | (top ^ (x & 1ull));
+}
+// inverse: x_k = y_k ^ y_{k-1} (k >= 1), x_0 = y_0, then bits 0 and 1 take y_{n-1}
+__device__ __forceinline__ uint64_t ring_inv(uint64_t y, int n) {
+  const uint64_t mask = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
+  uint64_t x = (y ^ (y << 1)) & mask;
+  if ((y >> (n - 1)) & 1ull) x ^= 3ull;
+  return x;
+}
+
+// out[j] = in[src(j)] for every batch element; forward: the ring maps
+// psi'[A(x)] = psi[x], so out[y] = in[A^{-1}(y)]; inverse: out[x] = in[A(x)].
+template <typename R>
+__global__ void __launch_bounds__(ADJ_T) k_ring(const typename CT<R>::V2* __restrict__ in,
+                                                typename CT<R>::V2* __restrict__ out, int n, int inverse) {
+  const int b = blockIdx.y;
+  const typename CT<R>::V2* s = in + ((uint64_t)b << n);
+  typename CT<R>::V2* d = out + ((uint64_t)b << n);
+  const uint64_t N = 1ull << n;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (uint64_t)gridDim.x * blockDim.x)
+    d[j] = s[inverse ? ring_fwd(j, n) : ring_inv(j, n)];
+}
+
+template <typename R>
+__global__ void k_zero_state_batch(typename CT<R>::V2* __restrict__ psi, int n, int B) {
+  const uint64_t N = 1ull << n, tot = N * (uint64_t)B;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (uint64_t)gridDim.x * blockDim.x)
+    psi[i] = CT<R>::make((R)((i & (N - 1)) == 0 ? 1 : 0), (R)0);
+}
+
 // Sum partial[b][0..gx) in order into out[b * ostride + ooff].
 __global__ void k_final_batch(const double* __restrict__ part, int gx, double* __restrict__ out, int64_t ostride,
                               int64_t ooff) {
@@ -171,8 +270,7 @@ __global__ void k_final_batch(const double* __restrict__ part, int gx, double* _
 }
 
 // ------------------------------------------------------------ backward ---
-// Fused: accumulate Im <lam|P|psi> over the gate's pairs (P the generator
-// X / Y / Z of a rotation on q0), then apply U^dagger to psi and lam.
+// One gate: accumulate Im <lam|P|psi> (rotations), apply U^dagger to both.
 template <typename R>
 __global__ void __launch_bounds__(ADJ_T) k_bwd_gate(typename CT<R>::V2* __restrict__ psi,
                                                     typename CT<R>::V2* __restrict__ lam, int n, GateDev g,
@@ -184,7 +282,7 @@ __global__ void __launch_bounds__(ADJ_T) k_bwd_gate(typename CT<R>::V2* __restri
   typename CT<R>::V2* l = lam + ((uint64_t)b << n);
   const bool rot = g.kind <= QC_G_RZ;
   const double th = rot ? -theta[(int64_t)b * stride + g.param] : 0.0;  // U^dagger
-  const Mat2<R> U = gate_matrix<R>(g.kind, th);
+  const Mat2<R> U = block_matrix<R>(g.kind, th);
   const uint64_t np = (g.kind == QC_G_CNOT) ? (1ull << (n - 2)) : (1ull << (n - 1));
   Acc<R> acc;
   for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (uint64_t)gridDim.x * blockDim.x) {
@@ -192,19 +290,7 @@ __global__ void __launch_bounds__(ADJ_T) k_bwd_gate(typename CT<R>::V2* __restri
     const uint64_t i0 = gate_pair(g, p, i1);
     Cx<R> p0 = IO::ld(s + i0), p1 = IO::ld(s + i1);
     Cx<R> l0 = IO::ld(l + i0), l1 = IO::ld(l + i1);
-    if (rot) {
-      // Im(conj(a) b) = a.re b.im - a.im b.re
-      if (g.kind == QC_G_RZ) {  // Z: conj(l0) p0 - conj(l1) p1
-        acc.add(l0.re, p0.im); acc.sub(l0.im, p0.re);
-        acc.sub(l1.re, p1.im); acc.add(l1.im, p1.re);
-      } else if (g.kind == QC_G_RX) {  // X: conj(l0) p1 + conj(l1) p0
-        acc.add(l0.re, p1.im); acc.sub(l0.im, p1.re);
-        acc.add(l1.re, p0.im); acc.sub(l1.im, p0.re);
-      } else {  // Y: conj(l0)(-i p1) + conj(l1)(i p0); Im(conj(a)(-i b)) = -Re(conj(a) b)
-        acc.sub(l0.re, p1.re); acc.sub(l0.im, p1.im);
-        acc.add(l1.re, p0.re); acc.add(l1.im, p0.im);
-      }
-    }
+    if (rot) acc_generator<R>(acc, g.kind, p0, p1, l0, l1);
     apply_any<R>(g.kind, U, p0, p1);
     apply_any<R>(g.kind, U, l0, l1);
     IO::st(s + i0, p0);
@@ -216,6 +302,47 @@ __global__ void __launch_bounds__(ADJ_T) k_bwd_gate(typename CT<R>::V2* __restri
     acc.flush();
     const double t = block_reduce(acc.value());
     if (threadIdx.x == 0) part[(int64_t)b * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// Two rotations ga then gb (forward order) on one qubit, walked backwards:
+// gradient of gb, undo gb, gradient of ga, undo ga -- one pass.
+template <typename R>
+__global__ void __launch_bounds__(ADJ_T) k_bwd_rot2(typename CT<R>::V2* __restrict__ psi,
+                                                    typename CT<R>::V2* __restrict__ lam, int n, GateDev ga,
+                                                    GateDev gb, const double* __restrict__ theta, int64_t stride,
+                                                    double* __restrict__ part_a, double* __restrict__ part_b) {
+  using IO = AmpIO<R>;
+  const int b = blockIdx.y;
+  typename CT<R>::V2* s = psi + ((uint64_t)b << n);
+  typename CT<R>::V2* l = lam + ((uint64_t)b << n);
+  const Mat2<R> Ua = block_matrix<R>(ga.kind, -theta[(int64_t)b * stride + ga.param]);
+  const Mat2<R> Ub = block_matrix<R>(gb.kind, -theta[(int64_t)b * stride + gb.param]);
+  const int q = ga.q0;
+  const uint64_t np = 1ull << (n - 1);
+  Acc<R> acca, accb;
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i0 = insert0(p, q), i1 = i0 | (1ull << q);
+    Cx<R> p0 = IO::ld(s + i0), p1 = IO::ld(s + i1);
+    Cx<R> l0 = IO::ld(l + i0), l1 = IO::ld(l + i1);
+    acc_generator<R>(accb, gb.kind, p0, p1, l0, l1);
+    apply_any<R>(gb.kind, Ub, p0, p1);
+    apply_any<R>(gb.kind, Ub, l0, l1);
+    acc_generator<R>(acca, ga.kind, p0, p1, l0, l1);
+    apply_any<R>(ga.kind, Ua, p0, p1);
+    apply_any<R>(ga.kind, Ua, l0, l1);
+    IO::st(s + i0, p0);
+    IO::st(s + i1, p1);
+    IO::st(l + i0, l0);
+    IO::st(l + i1, l1);
+  }
+  acca.flush();
+  accb.flush();
+  const double ta = block_reduce(acca.value());
+  const double tb = block_reduce(accb.value());
+  if (threadIdx.x == 0) {
+    part_a[(int64_t)b * gridDim.x + blockIdx.x] = ta;
+    part_b[(int64_t)b * gridDim.x + blockIdx.x] = tb;
   }
 }
 
@@ -279,6 +406,38 @@ __global__ void __launch_bounds__(ADJ_T) k_energy(const typename CT<R>::V2* __re
 }
 
 // ------------------------------------------------------------ host side --
+enum AdjOpKind { AOP_GATE = 0, AOP_ROT2 = 1, AOP_RING = 2 };
+struct AdjOp {
+  int kind;
+  GateDev a, b;
+};
+
+static GateDev gdev(const qc_gate& g) { return GateDev{g.kind, g.q0, g.q1, g.param}; }
+
+// Compile the gate list into passes (see the file comment).
+static std::vector<AdjOp> compile_ops(const qc_gate* gates, int ng, int n) {
+  std::vector<AdjOp> ops;
+  int i = 0;
+  while (i < ng) {
+    bool ring = (i + n <= ng) && n >= 2;
+    for (int k = 0; ring && k < n; ++k)
+      ring = gates[i + k].kind == QC_G_CNOT && gates[i + k].q0 == k && gates[i + k].q1 == (k + 1) % n;
+    if (ring) {
+      ops.push_back(AdjOp{AOP_RING, GateDev{QC_G_CNOT, 0, 1, 0}, GateDev{QC_G_CNOT, 0, 1, 0}});
+      i += n;
+      continue;
+    }
+    if (i + 1 < ng && gates[i].kind <= QC_G_RZ && gates[i + 1].kind <= QC_G_RZ && gates[i].q0 == gates[i + 1].q0) {
+      ops.push_back(AdjOp{AOP_ROT2, gdev(gates[i]), gdev(gates[i + 1])});
+      i += 2;
+      continue;
+    }
+    ops.push_back(AdjOp{AOP_GATE, gdev(gates[i]), gdev(gates[i])});
+    ++i;
+  }
+  return ops;
+}
+
 static qc_status check_circuit(int n, qc_dtype dt, int B, const qc_gate* gates, int n_gates, int64_t stride,
                                int n_params) {
   if (n < 2 || n > 30) {
@@ -315,28 +474,72 @@ static qc_status check_circuit(int n, qc_dtype dt, int B, const qc_gate* gates, 
   return QC_OK;
 }
 
+// Blocks per batch element: all blocks of the (gx, B) grid resident at once.
 template <typename R>
 static unsigned gx_for(int n, int B) {
   const uint64_t pairs = 1ull << (n - 1);
   uint64_t gx = (pairs + ADJ_T - 1) / ADJ_T;
-  const uint64_t cap = std::max<uint64_t>(1, (uint64_t)sm_count() * 8 / (uint64_t)B);
+  const int res = std::min(resident_blocks((const void*)k_bwd_rot2<R>, ADJ_T, 0),
+                           resident_blocks((const void*)k_fwd_gate<R>, ADJ_T, 0));
+  const uint64_t cap = std::max<uint64_t>(1, (uint64_t)sm_count() * res / (uint64_t)B);
   gx = std::min<uint64_t>(gx, std::min<uint64_t>(cap, ADJ_GX_MAX));
   return (unsigned)std::max<uint64_t>(gx, 1);
+}
+
+// Buffers rotate among the caller's psi and lam and one workspace.
+template <typename R>
+struct Bufs {
+  typename CT<R>::V2* psi;
+  typename CT<R>::V2* lam;
+  typename CT<R>::V2* spare;
+};
+
+// Forward passes; the result is in bufs.psi (which may be the workspace).
+template <typename R>
+static int forward_passes(const std::vector<AdjOp>& ops, int n, int B, const double* theta, int64_t stride,
+                          Bufs<R>& bf, cudaStream_t st) {
+  const dim3 grid(gx_for<R>(n, B), B);
+  const uint64_t tot = (uint64_t)B << n;
+  k_zero_state_batch<R><<<grid_for(tot, ADJ_T, 8), ADJ_T, 0, st>>>(bf.psi, n, B);
+  int nk = 1;
+  for (const AdjOp& op : ops) {
+    if (op.kind == AOP_RING) {
+      k_ring<R><<<grid, ADJ_T, 0, st>>>(bf.psi, bf.spare, n, 0);
+      std::swap(bf.psi, bf.spare);
+    } else if (op.kind == AOP_ROT2) {
+      k_fwd_rot2<R><<<grid, ADJ_T, 0, st>>>(bf.psi, n, op.a, op.b, theta, stride);
+    } else {
+      k_fwd_gate<R><<<grid, ADJ_T, 0, st>>>(bf.psi, n, op.a, theta, stride);
+    }
+    ++nk;
+  }
+  return nk;
+}
+
+static bool has_ring(const std::vector<AdjOp>& ops) {
+  for (const AdjOp& o : ops)
+    if (o.kind == AOP_RING) return true;
+  return false;
 }
 
 template <typename R>
 static qc_status forward_impl(int n, int B, const qc_gate* gates, int n_gates, const double* theta,
                               int64_t stride, void* psi, cudaStream_t st) {
   using V2 = typename CT<R>::V2;
-  V2* d = reinterpret_cast<V2*>(psi);
-  const uint64_t tot = (uint64_t)B << n;
-  k_zero_state_batch<R><<<grid_for(tot, ADJ_T, 8), ADJ_T, 0, st>>>(d, n, B);
-  const dim3 grid(gx_for<R>(n, B), B);
-  for (int i = 0; i < n_gates; ++i) {
-    const GateDev g{gates[i].kind, gates[i].q0, gates[i].q1, gates[i].param};
-    k_fwd_gate<R><<<grid, ADJ_T, 0, st>>>(d, n, g, theta, stride, 1.0);
+  const std::vector<AdjOp> ops = compile_ops(gates, n_gates, n);
+  const size_t bytes = ((size_t)B << n) * sizeof(V2);
+  V2* ws = nullptr;
+  if (has_ring(ops)) {
+    cudaError_t e = cudaMallocAsync((void**)&ws, bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "forward workspace");
   }
-  return check_launch("circuit forward", 1 + n_gates);
+  Bufs<R> bf{reinterpret_cast<V2*>(psi), nullptr, ws};
+  int nk = forward_passes<R>(ops, n, B, theta, stride, bf, st);
+  if (bf.psi != reinterpret_cast<V2*>(psi)) {
+    cudaMemcpyAsync(psi, bf.psi, bytes, cudaMemcpyDeviceToDevice, st);
+  }
+  if (ws) cudaFreeAsync(ws, st);
+  return check_launch("circuit forward", nk);
 }
 
 template <typename R>
@@ -344,28 +547,26 @@ static qc_status adjoint_impl(int n, int B, const qc_gate* gates, int n_gates, c
                               int64_t stride, const qc_pauli_term* H, int n_terms, void* psi, void* lam,
                               double* energy, double* grad, cudaStream_t st) {
   using V2 = typename CT<R>::V2;
-  qc_status s = forward_impl<R>(n, B, gates, n_gates, theta, stride, psi, st);
-  if (s) return s;
-  V2* dp = reinterpret_cast<V2*>(psi);
-  V2* dl = reinterpret_cast<V2*>(lam);
+  const std::vector<AdjOp> ops = compile_ops(gates, n_gates, n);
+  const size_t bytes = ((size_t)B << n) * sizeof(V2);
   const unsigned gx = gx_for<R>(n, B);
   const dim3 grid(gx, B);
-  // workspace: Hamiltonian terms + partials
+  // workspace: Hamiltonian terms, two partial arrays, one state buffer
   TermsDev* dT = nullptr;
   double* part = nullptr;
+  V2* ws = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&dT, sizeof(TermsDev), st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&part, sizeof(double) * (size_t)gx * B, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&part, sizeof(double) * 2 * (size_t)gx * B, st);
+  if (e == cudaSuccess && has_ring(ops)) e = cudaMallocAsync((void**)&ws, bytes, st);
+  TermsDev* hT = nullptr;
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&hT, sizeof(TermsDev));
   if (e != cudaSuccess) {
     if (dT) cudaFreeAsync(dT, st);
+    if (part) cudaFreeAsync(part, st);
+    if (ws) cudaFreeAsync(ws, st);
     return cuda_fail(e, "adjoint workspace");
   }
-  TermsDev* hT = nullptr;
-  e = cudaMallocHost((void**)&hT, sizeof(TermsDev));
-  if (e != cudaSuccess) {
-    cudaFreeAsync(dT, st);
-    cudaFreeAsync(part, st);
-    return cuda_fail(e, "adjoint terms (host)");
-  }
+  double* part_b = part + (size_t)gx * B;
   hT->nt = n_terms;
   for (int k = 0; k < n_terms; ++k) {
     hT->x[k] = H[k].xmask;
@@ -374,31 +575,48 @@ static qc_status adjoint_impl(int n, int B, const qc_gate* gates, int n_gates, c
   }
   e = cudaMemcpyAsync(dT, hT, sizeof(TermsDev), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(grad, 0, sizeof(double) * (size_t)B * stride, st);
-  if (e != cudaSuccess) {
-    cudaStreamSynchronize(st);
-    cudaFreeHost(hT);
-    cudaFreeAsync(dT, st);
-    cudaFreeAsync(part, st);
-    return cuda_fail(e, "adjoint setup");
-  }
-  k_apply_h<R><<<grid, ADJ_T, 0, st>>>(dp, dl, n, dT);
-  k_energy<R><<<grid, ADJ_T, 0, st>>>(dp, dl, n, part);
-  k_final_batch<<<B, ADJ_T, 0, st>>>(part, gx, energy, 1, 0);
-  int nk = 3;
-  for (int i = n_gates - 1; i >= 0; --i) {
-    const GateDev g{gates[i].kind, gates[i].q0, gates[i].q1, gates[i].param};
-    k_bwd_gate<R><<<grid, ADJ_T, 0, st>>>(dp, dl, n, g, theta, stride, part);
-    ++nk;
-    if (g.kind <= QC_G_RZ) {
-      k_final_batch<<<B, ADJ_T, 0, st>>>(part, gx, grad, stride, g.param);
-      ++nk;
+  qc_status s = QC_OK;
+  if (e != cudaSuccess) s = cuda_fail(e, "adjoint setup");
+  if (!s) {
+    Bufs<R> bf{reinterpret_cast<V2*>(psi), reinterpret_cast<V2*>(lam), ws};
+    // the forward pass may rotate psi into the workspace; lam stays put
+    Bufs<R> fb{bf.psi, nullptr, bf.spare};
+    int nk = forward_passes<R>(ops, n, B, theta, stride, fb, st);
+    bf.psi = fb.psi;
+    bf.spare = fb.spare;
+    k_apply_h<R><<<grid, ADJ_T, 0, st>>>(bf.psi, bf.lam, n, dT);
+    k_energy<R><<<grid, ADJ_T, 0, st>>>(bf.psi, bf.lam, n, part);
+    k_final_batch<<<B, ADJ_T, 0, st>>>(part, gx, energy, 1, 0);
+    nk += 3;
+    for (int i = (int)ops.size() - 1; i >= 0; --i) {
+      const AdjOp& op = ops[i];
+      if (op.kind == AOP_RING) {
+        k_ring<R><<<grid, ADJ_T, 0, st>>>(bf.psi, bf.spare, n, 1);
+        std::swap(bf.psi, bf.spare);
+        k_ring<R><<<grid, ADJ_T, 0, st>>>(bf.lam, bf.spare, n, 1);
+        std::swap(bf.lam, bf.spare);
+        nk += 2;
+      } else if (op.kind == AOP_ROT2) {
+        k_bwd_rot2<R><<<grid, ADJ_T, 0, st>>>(bf.psi, bf.lam, n, op.a, op.b, theta, stride, part, part_b);
+        k_final_batch<<<B, ADJ_T, 0, st>>>(part_b, gx, grad, stride, op.b.param);
+        k_final_batch<<<B, ADJ_T, 0, st>>>(part, gx, grad, stride, op.a.param);
+        nk += 3;
+      } else {
+        k_bwd_gate<R><<<grid, ADJ_T, 0, st>>>(bf.psi, bf.lam, n, op.a, theta, stride, part);
+        ++nk;
+        if (op.a.kind <= QC_G_RZ) {
+          k_final_batch<<<B, ADJ_T, 0, st>>>(part, gx, grad, stride, op.a.param);
+          ++nk;
+        }
+      }
     }
+    s = check_launch("adjoint", nk);
   }
-  s = check_launch("adjoint backward", nk);
   e = cudaStreamSynchronize(st);  // the pinned term list is freed below
   cudaFreeHost(hT);
   cudaFreeAsync(dT, st);
   cudaFreeAsync(part, st);
+  if (ws) cudaFreeAsync(ws, st);
   if (!s && e != cudaSuccess) s = cuda_fail(e, "adjoint");
   return s;
 }

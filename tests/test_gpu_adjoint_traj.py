@@ -93,8 +93,72 @@ def test_adjoint_small_all_angles(qc, dt):
         tol = 1e-12 if dt == 0 else 2e-5
         assert abs(E[b] - Er) <= tol
         assert np.max(np.abs(g[b] - gr)) <= tol
-        # uncomputation returns psi to |0..0>
-        assert abs(psi[b][0] - 1) <= (1e-11 if dt == 0 else 1e-4)
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_adjoint_unfused_gate_list(qc, dt):
+    # rotations interleaved with H, RX and partial CNOT chains: no pass fusion
+    import torch
+    n, B = 5, 2
+    rng = W.rng(21)
+    gl, ora = [], []
+    k = 0
+    for l in range(3):
+        for q in range(n):
+            kind = (l + q) % 3  # RX, RY, RZ
+            gl.append(qc.Gate(kind, q, 0, k))
+            ora.append(("rx" if kind == 0 else "ry" if kind == 1 else "rz", q, k))
+            k += 1
+            if q % 2 == 0:
+                gl.append(qc.Gate(qc.QC_G_H, q, 0, 0))
+                ora.append(("h", q, 0))
+        for (c, t) in ((0, 1), (2, 4), (4, 3)):
+            gl.append(qc.Gate(qc.QC_G_CNOT, c, t, 0))
+            ora.append(("cnot", c, t))
+    P = k
+    theta = rng.random((B, P)) * 6.28
+    terms = W.ansatz_hamiltonian(n) + [(0b10100, 0b00110, 0.3)]
+
+    def mats(g, th, dag=False):
+        if g[0] == "h":
+            return O.H_MAT
+        a = th[g[2]] * (-1 if dag else 1)
+        if g[0] == "rx":
+            return np.array([[math.cos(a / 2), -1j * math.sin(a / 2)], [-1j * math.sin(a / 2), math.cos(a / 2)]])
+        return O.ry(a) if g[0] == "ry" else O.rz(a)
+
+    def fwd(th):
+        psi = O.zero_state(n)
+        for g in ora:
+            if g[0] == "cnot":
+                O.cnot(psi, n, g[1], g[2])
+            else:
+                O.apply_1q(psi, n, g[1], mats(g, th))
+        return psi
+    gates = (qc.Gate * len(gl))(*gl)
+    tarr = (qc.PauliTerm * len(terms))(*[qc.PauliTerm(x, z, c) for (x, z, c) in terms])
+    th_d = torch.tensor(theta, dtype=torch.float64, device="cuda")
+    cdt = torch.complex128 if dt == 0 else torch.complex64
+    psi = torch.empty(B << n, dtype=cdt, device="cuda")
+    lam = torch.empty_like(psi)
+    E = torch.empty(B, dtype=torch.float64, device="cuda")
+    grad = torch.empty(B, P, dtype=torch.float64, device="cuda")
+    rc = qc.lib().qc_adjoint_grad(n, dt, B, gates, len(gl), ctypes.c_void_p(th_d.data_ptr()), P, P, tarr,
+                                  len(terms), ctypes.c_void_p(psi.data_ptr()), ctypes.c_void_p(lam.data_ptr()),
+                                  ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, qc.last_error()
+    torch.cuda.synchronize()
+    tol = 1e-12 if dt == 0 else 2e-5
+    for b in range(B):
+        Er = O.energy(fwd(theta[b]), n, terms)
+        assert abs(E[b].item() - Er) <= tol
+        for kk in range(P):  # parameter shift on the oracle forward
+            tp, tm = theta[b].copy(), theta[b].copy()
+            tp[kk] += math.pi / 2
+            tm[kk] -= math.pi / 2
+            ps = 0.5 * (O.energy(fwd(tp), n, terms) - O.energy(fwd(tm), n, terms))
+            assert abs(grad[b, kk].item() - ps) <= tol
 
 
 def test_adjoint_n20_sampled_angles_param_shift(qc):
