@@ -129,6 +129,84 @@ __device__ __forceinline__ double bsum(double v, double* sh) {
   return t;  // every thread gets the same value
 }
 
+// Block sum of float pairs (h + l) on the FP32 pipe: two-sum reduction across
+// the warp, one FP64 add per warp, the warp totals added in FP64 by thread 0.
+// The result is valid in thread 0 only (the FP64 pipe of GB300 is too
+// narrow to let every thread take part).
+__device__ __forceinline__ double bsum_ff(float h, float l, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+    float s, e;
+    two_sum(h, h2, s, e);
+    e = e + (l + l2);
+    two_sum(s, e, h, l);
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)h + (double)l;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  return t;
+}
+
+// The three float-pair sums of a pass (S re, S im, Q) and the marked
+// amplitude (nonzero in one thread only) in one block reduction; results in
+// thread 0: out[0..4] = S re, S im, Q, cm re, cm im.
+__device__ __forceinline__ void bsum_pass(const float h[3], const float l[3], float cr, float ci, double* sh,
+                                          double out[5]) {
+  float H[3] = {h[0], h[1], h[2]}, L[3] = {l[0], l[1], l[2]};
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, H[v], o), l2 = __shfl_xor_sync(0xffffffffu, L[v], o);
+      float s, e;
+      two_sum(H[v], h2, s, e);
+      e = e + (L[v] + l2);
+      two_sum(s, e, H[v], L[v]);
+    }
+    cr += __shfl_xor_sync(0xffffffffu, cr, o);  // one nonzero term: exact
+    ci += __shfl_xor_sync(0xffffffffu, ci, o);
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    for (int v = 0; v < 3; ++v) sh[v * 32 + w] = (double)H[v] + (double)L[v];
+    sh[96 + w] = (double)cr;
+    sh[128 + w] = (double)ci;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int v = 0; v < 5; ++v) {
+      double t = 0.0;
+      for (int i = 0; i < nw; ++i) t += sh[v * 32 + i];
+      out[v] = t;
+    }
+}
+
+// Sum of `nv` doubles over the cluster's ranks, read in parallel by warp 0
+// (lane r reads rank r); the result is valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void cluster_gather(cg::cluster_group& cluster, const Xch& xch, int buf, int first,
+                                               double out[NV]) {
+  if (threadIdx.x >= 32) return;
+  const int G = (int)cluster.num_blocks();
+  double v[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = 0.0;
+  if ((int)threadIdx.x < G) {
+    const Xch* x = cluster.map_shared_rank(&xch, (int)threadIdx.x);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = x->v[buf][first + i];
+  }
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) out[i] = v[i];
+}
+
 __device__ __forceinline__ unsigned long long bsum_u64(unsigned long long v, unsigned long long* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();
@@ -163,18 +241,19 @@ __device__ __forceinline__ Pauli stage_errors(const TrajParams& P, int inst_id, 
   return p;
 }
 
-__global__ void __launch_bounds__(1024) k_traj(TrajParams P) {
+__global__ void __launch_bounds__(512, 2) k_traj(TrajParams P) {
   cg::cluster_group cluster = cg::this_cluster();
   const int G = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
   const int cid = blockIdx.x / G;
   __shared__ Xch xch;
-  __shared__ double shd[32];
+  __shared__ double shd[160];  // five 32-entry rows for bsum_pass
   __shared__ unsigned long long shu[32];
   __shared__ Pauli pA, pB;
   __shared__ int sh_err;
   __shared__ double wtab[QC_TRAJ_MAX_QUBITS + 1];
   __shared__ unsigned long long sh_target;
+  __shared__ float sh_sc[3];
   float2* psi = P.slots + (uint64_t)cid * P.slot_amps;
   const int tid = threadIdx.x, T = blockDim.x;
   for (;;) {
@@ -206,7 +285,7 @@ __global__ void __launch_bounds__(1024) k_traj(TrajParams P) {
       const float a0 = (float)(1.0 / sqrt(ldexp(1.0, n)));
       Sums acc;
       acc.zero();
-      double cmr = 0.0, cmi = 0.0;
+      float cmr = 0.f, cmi = 0.f;
       for (uint64_t j = lo + tid; j < hi; j += T) {
         float re = (__popcll((j ^ e0.x) & e0.z) & 1) ? -a0 : a0, im = 0.f;
         ipow(e0.a, re, im);
@@ -217,22 +296,24 @@ __global__ void __launch_bounds__(1024) k_traj(TrajParams P) {
           cmi = im;
         }
       }
-      const double S0 = bsum((double)acc.sr + (double)acc.cr, shd);
-      const double S1 = bsum((double)acc.si + (double)acc.ci, shd);
-      const double Q = bsum((double)acc.q + (double)acc.cq, shd);
-      const double c0 = bsum(cmr, shd), c1 = bsum(cmi, shd);
-      if (tid == 0) {
-        xch.v[buf][0] = S0; xch.v[buf][1] = S1; xch.v[buf][2] = Q;
-        xch.v[buf][3] = c0; xch.v[buf][4] = c1;
-      }
+      const float hh[3] = {acc.sr, acc.si, acc.q}, ll[3] = {acc.cr, acc.ci, acc.cq};
+      double red[5];
+      bsum_pass(hh, ll, cmr, cmi, shd, red);
+      if (tid == 0)
+        for (int v = 0; v < 5; ++v) xch.v[buf][v] = red[v];
     }
     __threadfence();
     cluster.sync();
+    // the per-iteration FP64 scalars live in thread 0 only (GB300's FP64 pipe
+    // is too narrow for every thread to repeat them); the others receive the
+    // three floats they need through shared memory
     double S[2] = {0, 0}, Q = 0, cm[2] = {0, 0};
-    for (int r = 0; r < G; ++r) {
-      const Xch* x = cluster.map_shared_rank(&xch, r);
-      S[0] += x->v[buf][0]; S[1] += x->v[buf][1]; Q += x->v[buf][2];
-      cm[0] += x->v[buf][3]; cm[1] += x->v[buf][4];
+    {
+      double g5[5];
+      cluster_gather<5>(cluster, xch, buf, 0, g5);
+      if (tid == 0) {
+        S[0] = g5[0]; S[1] = g5[1]; Q = g5[2]; cm[0] = g5[3]; cm[1] = g5[4];
+      }
     }
     for (int it = 0; it < I.iters; ++it) {
       buf ^= 1;
@@ -251,7 +332,6 @@ __global__ void __launch_bounds__(1024) k_traj(TrajParams P) {
       }
       __syncthreads();
       const Pauli A = pA, B = pB;
-      const double s = 1.0 / sqrt(Q);
       // sum of O psi, signed by Z^zB when B has Z factors
       double W[2] = {S[0] - 2.0 * cm[0], S[1] - 2.0 * cm[1]};
       if (B.z) {
@@ -262,40 +342,44 @@ __global__ void __launch_bounds__(1024) k_traj(TrajParams P) {
           if (__popcll(j & B.z) & 1) { v.x = -v.x; v.y = -v.y; }
           acc.add(v.x, v.y);
         }
-        const double w0 = bsum((double)acc.sr + (double)acc.cr, shd);
-        const double w1 = bsum((double)acc.si + (double)acc.ci, shd);
+        const double w0 = bsum_ff(acc.sr, acc.cr, shd);
+        const double w1 = bsum_ff(acc.si, acc.ci, shd);
         if (tid == 0) {
           xch.v[buf][5] = w0;
           xch.v[buf][6] = w1;
         }
         __threadfence();
         cluster.sync();
-        W[0] = W[1] = 0.0;
-        for (int r = 0; r < G; ++r) {
-          const Xch* x = cluster.map_shared_rank(&xch, r);
-          W[0] += x->v[buf][5];
-          W[1] += x->v[buf][6];
+        double g2[2];
+        cluster_gather<2>(cluster, xch, buf, 5, g2);
+        if (tid == 0) {
+          W[0] = g2[0];
+          W[1] = g2[1];
+          const double sg = (__popcll(m & B.z) & 1) ? -1.0 : 1.0;
+          W[0] -= 2.0 * sg * cm[0];
+          W[1] -= 2.0 * sg * cm[1];
         }
-        const double sg = (__popcll(m & B.z) & 1) ? -1.0 : 1.0;
-        W[0] -= 2.0 * sg * cm[0];
-        W[1] -= 2.0 * sg * cm[1];
         cluster.sync();  // every CTA has read the W slots before they are reused
       }
-      // m = mean of B O psi-hat = i^aB s W / N
-      double mr = W[0], mi = W[1];
-      {
+      if (tid == 0) {
+        // m = mean of B O psi-hat = i^aB s W / N; broadcast 2m, s as floats
+        const double s = 1.0 / sqrt(Q);
+        double mr = W[0], mi = W[1];
         const double r0 = mr, i0 = mi;
         if (B.a == 1) { mr = -i0; mi = r0; }
         else if (B.a == 2) { mr = -r0; mi = -i0; }
         else if (B.a == 3) { mr = i0; mi = -r0; }
+        const double scale = s / (double)N;
+        sh_sc[0] = (float)(2.0 * mr * scale);
+        sh_sc[1] = (float)(2.0 * mi * scale);
+        sh_sc[2] = (float)s;
       }
-      const double scale = s / (double)N;
-      const float t2r = (float)(2.0 * mr * scale), t2i = (float)(2.0 * mi * scale);
-      const float sf = (float)s;
+      __syncthreads();
+      const float t2r = sh_sc[0], t2i = sh_sc[1], sf = sh_sc[2];
       const uint64_t X = A.x ^ B.x;
       Sums acc;
       acc.zero();
-      double cmr = 0.0, cmi = 0.0;
+      float cmr = 0.f, cmi = 0.f;
       // out[j] from src = j ^ X
       auto out_of = [&](uint64_t j, float2 u) -> float2 {
         const uint64_t src = j ^ X;
@@ -310,11 +394,32 @@ __global__ void __launch_bounds__(1024) k_traj(TrajParams P) {
         return make_float2(re, im);
       };
       if (X == 0) {
-        for (uint64_t j = lo + tid; j < hi; j += T) {
-          const float2 o = out_of(j, psi[j]);
-          psi[j] = o;
-          acc.add(o.x, o.y);
-          if (j == m) { cmr = o.x; cmi = o.y; }
+        // 16-byte vectors of two amplitudes, two vectors in flight per thread
+        float4* p4 = reinterpret_cast<float4*>(psi);
+        const uint64_t vhi = hi / 2;
+        uint64_t v = lo / 2 + tid;
+        for (; v + T < vhi; v += 2 * T) {
+          const float4 u = p4[v], w = p4[v + T];
+          const uint64_t j = 2 * v, k2 = 2 * (v + T);
+          const float2 o0 = out_of(j, make_float2(u.x, u.y)), o1 = out_of(j + 1, make_float2(u.z, u.w));
+          const float2 o2 = out_of(k2, make_float2(w.x, w.y)), o3 = out_of(k2 + 1, make_float2(w.z, w.w));
+          p4[v] = make_float4(o0.x, o0.y, o1.x, o1.y);
+          p4[v + T] = make_float4(o2.x, o2.y, o3.x, o3.y);
+          acc.add(o0.x, o0.y);
+          acc.add(o1.x, o1.y);
+          acc.add(o2.x, o2.y);
+          acc.add(o3.x, o3.y);
+          if ((j | 1) == (m | 1)) { cmr = (j == m) ? o0.x : o1.x; cmi = (j == m) ? o0.y : o1.y; }
+          if ((k2 | 1) == (m | 1)) { cmr = (k2 == m) ? o2.x : o3.x; cmi = (k2 == m) ? o2.y : o3.y; }
+        }
+        if (v < vhi) {
+          const float4 u = p4[v];
+          const uint64_t j = 2 * v;
+          const float2 o0 = out_of(j, make_float2(u.x, u.y)), o1 = out_of(j + 1, make_float2(u.z, u.w));
+          p4[v] = make_float4(o0.x, o0.y, o1.x, o1.y);
+          acc.add(o0.x, o0.y);
+          acc.add(o1.x, o1.y);
+          if ((j | 1) == (m | 1)) { cmr = (j == m) ? o0.x : o1.x; cmi = (j == m) ? o0.y : o1.y; }
         }
       } else {
         const int hb = 63 - __clzll((long long)X);
@@ -331,21 +436,18 @@ __global__ void __launch_bounds__(1024) k_traj(TrajParams P) {
           if (jx == m) { cmr = ojx.x; cmi = ojx.y; }
         }
       }
-      const double S0 = bsum((double)acc.sr + (double)acc.cr, shd);
-      const double S1 = bsum((double)acc.si + (double)acc.ci, shd);
-      const double Qp = bsum((double)acc.q + (double)acc.cq, shd);
-      const double c0 = bsum(cmr, shd), c1 = bsum(cmi, shd);
-      if (tid == 0) {
-        xch.v[buf][0] = S0; xch.v[buf][1] = S1; xch.v[buf][2] = Qp;
-        xch.v[buf][3] = c0; xch.v[buf][4] = c1;
+      {
+        const float hh[3] = {acc.sr, acc.si, acc.q}, ll[3] = {acc.cr, acc.ci, acc.cq};
+        double red[5];
+        bsum_pass(hh, ll, cmr, cmi, shd, red);
+        if (tid == 0) for (int v = 0; v < 5; ++v) xch.v[buf][v] = red[v];
       }
       __threadfence();
       cluster.sync();
-      S[0] = S[1] = Q = cm[0] = cm[1] = 0.0;
-      for (int r = 0; r < G; ++r) {
-        const Xch* x = cluster.map_shared_rank(&xch, r);
-        S[0] += x->v[buf][0]; S[1] += x->v[buf][1]; Q += x->v[buf][2];
-        cm[0] += x->v[buf][3]; cm[1] += x->v[buf][4];
+      {
+        double g5[5];
+        cluster_gather<5>(cluster, xch, buf, 0, g5);
+        if (tid == 0) { S[0] = g5[0]; S[1] = g5[1]; Q = g5[2]; cm[0] = g5[3]; cm[1] = g5[4]; }
       }
     }
     // ---- read-out: success probabilities and one seeded measurement
@@ -555,7 +657,7 @@ QC_API qc_status qc_traj_plan_create(const qc_traj_desc* d, void* stream, int au
   }
   p->status = reinterpret_cast<int*>(p->queue + 1);
   // candidate shapes: G CTAs per instance (G <= 2^{nmin-1}), T threads
-  std::vector<int> Gs, Ts = {256, 512, 1024};
+  std::vector<int> Gs, Ts = {256, 512};
   for (int G = 1; G <= 16; G *= 2)
     if ((uint64_t)G * 2 <= (1ull << nmin) && (G >= 4 || nmax <= 14)) Gs.push_back(G);
   struct Cand {
