@@ -161,6 +161,36 @@ qc_status qc_grover_run(qc_state* s, const uint64_t* marked, int n_marked, int i
  * Runs as fused tile passes plus one in-place bit-reversal pass. */
 qc_status qc_qft(qc_state* s);
 
+/* General two-qubit operator, TwoOpA (Eq. resmat2, Eq. twoopB): for every
+ * quartet n00 (bits t1 and t2 zero), n01 = n00 + 2^t2, n10 = n00 + 2^t1,
+ * n11 = n00 + 2^t1 + 2^t2, the four amplitudes in the order
+ * (n00, n01, n10, n11) are multiplied by V: 32 host doubles, 4x4 row-major,
+ * (re, im) interleaved, V_{ij;kl} = <i j|V|k l> at row 2i+j, column 2k+l, i
+ * the value of qubit t1 and j of qubit t2.  t1 != t2; n >= 2.  complex128
+ * runs in double-float arithmetic. */
+qc_status qc_apply_2q(qc_state* s, int t1, int t2, const double V[32]);
+
+/* Shor's state of Eq. Shor2 (sec. 5.2): with register 1 the high
+ * n1 = n - n2 qubits and register 2 the low n2 qubits,
+ *   psi = 2^{-n1/2} sum_{j < 2^n1} |j>_1 |x^j mod M>_2,
+ * written directly (the paper's modular exponentiation "tacked on" to the
+ * register).  Requires 2 <= M < 2^32, M <= 2^n2, 1 <= x < M. */
+qc_status qc_shor_prepare(qc_state* s, int n2, uint64_t x, uint64_t M);
+
+/* Projective measurement of the register of qubits [lo, lo+width) with
+ * outcome `value` (ProjA, Eq. projreg2, Born rule): *prob_out (host, may be
+ * NULL) receives the outcome's probability sum |C|^2 over the matching
+ * amplitudes (FP64), the other amplitudes are set to zero and the matching
+ * ones divided by sqrt(prob).  QC_EINVAL if the probability is zero.
+ * Synchronises the stream. */
+qc_status qc_project(qc_state* s, int lo, int width, uint64_t value, double* prob_out);
+
+/* QFT of the register of qubits [lo, lo+width) (Appendix A's circuit
+ * applied to register 1 of Shor's algorithm, sec. 5.2 step 5): Hadamard /
+ * CPHASEK ladder and the swaps restoring the register's bit order, as gate
+ * passes.  On the whole state (lo = 0, width = n) it equals qc_qft. */
+qc_status qc_qft_range(qc_state* s, int lo, int width);
+
 /* ----------------------------------------------------------- reductions -- */
 
 /* sum_i |C_i|^2 accumulated in FP64 (the normalisation of sec. 2).
@@ -314,9 +344,12 @@ qc_status qc_circuit_forward(int n, qc_dtype dt, int B, const qc_gate* gates, in
  * forward pass, then walks the gates backwards applying U^dagger to psi and
  * to lambda = H psi (no intermediate states are stored); for a rotation
  * gate j with Pauli generator P: dE/dtheta_j = Im <lambda_j|P|psi_j>, with
- * FP64 accumulation.  psi_dev and lam_dev are caller-owned buffers of
- * B * 2^n amplitudes; on return psi_dev holds |0..0> up to rounding.  H is a
- * host array of Pauli terms with real coefficients. */
+ * FP64 accumulation.  psi_dev and lam_dev are caller-owned workspace of
+ * B * 2^n amplitudes each; their contents on return are unspecified.  Two
+ * rotations in a row on one qubit run as one pass, and a CNOT ring
+ * CNOT(0,1), .., CNOT(n-1,0) as one gather pass (using one more temporary
+ * buffer of B * 2^n amplitudes).  H is a host array of Pauli terms with real
+ * coefficients. */
 qc_status qc_adjoint_grad(int n, qc_dtype dt, int B, const qc_gate* gates, int n_gates,
                           const double* theta_dev, int64_t theta_stride, int n_params,
                           const qc_pauli_term* H, int n_terms,

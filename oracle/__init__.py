@@ -64,6 +64,9 @@ def lib():
             "or_philox4x32_10": (None, [_u32p, _u32p, _u32p]),
             "or_sample_from_probs": (ctypes.c_int, [_dp, ctypes.c_int, ctypes.c_uint64,
                                                     ctypes.c_int64, _u64p, _u64p]),
+            "or_shor_prepare": (None, [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64]),
+            "or_project": (ctypes.c_double, [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]),
+            "or_qft_range": (None, [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -173,6 +176,21 @@ def grover_step(psi, n, marked):
 
 def qft(psi, n):
     lib().or_qft(_state_ptr(psi), n)
+    return psi
+
+
+def shor_prepare(n, n2, x, M) -> np.ndarray:
+    psi = np.empty(1 << n, dtype=np.complex128)
+    lib().or_shor_prepare(_state_ptr(psi), n, n2, x, M)
+    return psi
+
+
+def project(psi, n, lo, w, value) -> float:
+    return float(lib().or_project(_state_ptr(psi), n, lo, w, value))
+
+
+def qft_range(psi, n, lo, w):
+    lib().or_qft_range(_state_ptr(psi), n, lo, w)
     return psi
 
 

@@ -370,3 +370,52 @@ int or_sample_from_probs(const double* p, int n, uint64_t seed, int64_t shots,
   }
   return 0;
 }
+
+/* ---- Shor's state, Eq. Shor2 (sec. 5.2): register 1 = the high n1 = n - n2
+ * bits, register 2 = the low n2 bits; psi = 2^{-n1/2} sum_j |j>|x^j mod M>,
+ * with x^j mod M built by repeated multiplication, f(j+1) = f(j) x mod M. */
+void or_shor_prepare(double* psi, int n, int n2, uint64_t x, uint64_t M) {
+  const int n1 = n - n2;
+  const int64_t N = (int64_t)1 << n;
+  memset(psi, 0, sizeof(double) * 2 * (size_t)N);
+  const double a = 1.0 / sqrt(ldexp(1.0, n1));
+  uint64_t f = 1 % M;
+  for (int64_t j = 0; j < ((int64_t)1 << n1); ++j) {
+    psi[2 * ((j << n2) | (int64_t)f)] = a;
+    f = (f * x) % M;
+  }
+}
+
+/* ---- ProjA (Eq. projreg2): keep the amplitudes whose bits [lo, lo+w)
+ * equal `value`, renormalise (Born rule); returns the outcome probability. */
+double or_project(double* psi, int n, int lo, int w, uint64_t value) {
+  const int64_t N = (int64_t)1 << n;
+  const uint64_t mask = ((uint64_t)1 << w) - 1;
+  double p = 0.0;
+  for (int64_t i = 0; i < N; ++i)
+    if ((((uint64_t)i >> lo) & mask) == value) p += psi[2 * i] * psi[2 * i] + psi[2 * i + 1] * psi[2 * i + 1];
+  const double f = p > 0.0 ? 1.0 / sqrt(p) : 0.0;
+  for (int64_t i = 0; i < N; ++i) {
+    if ((((uint64_t)i >> lo) & mask) == value) {
+      psi[2 * i] *= f;
+      psi[2 * i + 1] *= f;
+    } else {
+      psi[2 * i] = 0.0;
+      psi[2 * i + 1] = 0.0;
+    }
+  }
+  return p;
+}
+
+/* ---- The Appendix A loop on the register of qubits [lo, lo+w): the
+ * register's paper label ic = 1 .. w is bit t = lo + w - ic. */
+void or_qft_range(double* psi, int n, int lo, int w) {
+  double H[8];
+  hadamard_matrix(H);
+  for (int ic = 1; ic <= w - 1; ++ic) {
+    or_apply_1q(psi, n, lo + w - ic, H);
+    for (int k = ic + 1; k <= w; ++k) or_cphase(psi, n, lo + w - k, lo + w - ic, k + 1 - ic);
+  }
+  or_apply_1q(psi, n, lo, H);
+  for (int i = 1; i <= w / 2; ++i) or_swap(psi, n, lo + w - i, lo + i - 1);
+}

@@ -82,6 +82,10 @@ _SIGS = {
     "qc_grover_step": [_VP, _U64P, _I],
     "qc_grover_run": [_VP, _U64P, _I, _I],
     "qc_qft": [_VP],
+    "qc_apply_2q": [_VP, _I, _I, _DP],
+    "qc_shor_prepare": [_VP, _I, _U64, _U64],
+    "qc_project": [_VP, _I, _I, _U64, _DP],
+    "qc_qft_range": [_VP, _I, _I],
     "qc_norm": [_VP, _DP],
     "qc_probs": [_VP, _VP],
     "qc_expect_pauli": [_VP, _U64, _U64, _DP],
@@ -236,6 +240,30 @@ def qc_grover_run(h, marked, iters: int):
 
 def qc_qft(h):
     _check(lib().qc_qft(h))
+
+
+def qc_apply_2q(h, t1: int, t2: int, V):
+    V = np.asarray(V)
+    if V.dtype.kind == "c":
+        V = np.stack([V.real, V.imag], axis=-1)
+    a = np.ascontiguousarray(V, dtype=np.float64).reshape(-1)
+    if a.size != 32:
+        raise ValueError("a 4x4 operator needs 32 doubles")
+    _check(lib().qc_apply_2q(h, t1, t2, _dptr(a)))
+
+
+def qc_shor_prepare(h, n2: int, x: int, M: int):
+    _check(lib().qc_shor_prepare(h, n2, x, M))
+
+
+def qc_project(h, lo: int, width: int, value: int) -> float:
+    out = ctypes.c_double()
+    _check(lib().qc_project(h, lo, width, value, ctypes.byref(out)))
+    return out.value
+
+
+def qc_qft_range(h, lo: int, width: int):
+    _check(lib().qc_qft_range(h, lo, width))
 
 
 def qc_norm(h) -> float:
