@@ -152,7 +152,8 @@ __device__ __forceinline__ double bsum_ff(float h, float l, double* sh) {
 
 // The three float-pair sums of a pass (S re, S im, Q) and the marked
 // amplitude (nonzero in one thread only) in one block reduction; results in
-// thread 0: out[0..4] = S re, S im, Q, cm re, cm im.
+// thread 0: out[0..4] = S re, S im, Q, cm re, cm im.  The caller guarantees a
+// block barrier between thread 0's last read of `sh` and this call.
 __device__ __forceinline__ void bsum_pass(const float h[3], const float l[3], float cr, float ci, double* sh,
                                           double out[5]) {
   float H[3] = {h[0], h[1], h[2]}, L[3] = {l[0], l[1], l[2]};
@@ -168,7 +169,6 @@ __device__ __forceinline__ void bsum_pass(const float h[3], const float l[3], fl
     cr += __shfl_xor_sync(0xffffffffu, cr, o);  // one nonzero term: exact
     ci += __shfl_xor_sync(0xffffffffu, ci, o);
   }
-  __syncthreads();
   const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if ((threadIdx.x & 31) == 0) {
     for (int v = 0; v < 3; ++v) sh[v * 32 + w] = (double)H[v] + (double)L[v];
@@ -241,6 +241,93 @@ __device__ __forceinline__ Pauli stage_errors(const TrajParams& P, int inst_id, 
   return p;
 }
 
+// One stage's Pauli string, drawn by one warp into slot `slot`.
+__device__ __forceinline__ void draw_stage(const TrajParams& P, int inst_id, int stage, int n, int lane, Pauli* e,
+                                           int* ne, int slot) {
+  int c = 0;
+  const Pauli p = stage_errors(P, inst_id, stage, n, lane, &c);
+  if (lane == 0) {
+    e[slot] = p;
+    ne[slot] = c;
+  }
+}
+
+// Thread 0's per-iteration scalars from W = sum of B's Z-signed O psi:
+// the mean m = i^aB s W / N, broadcast as 2 m (re, im) and s = 1/sqrt(Q).
+__device__ __forceinline__ void grover_scalars(double wr, double wi, double Q, int a, uint64_t N, float* sc) {
+  const double s = 1.0 / sqrt(Q);
+  double mr = wr, mi = wi;
+  if (a == 1) { mr = -wi; mi = wr; }
+  else if (a == 2) { mr = -wr; mi = -wi; }
+  else if (a == 3) { mr = wi; mi = -wr; }
+  const double scale = s / (double)N;
+  sc[0] = (float)(2.0 * mr * scale);
+  sc[1] = (float)(2.0 * mi * scale);
+  sc[2] = (float)s;
+}
+
+// An iteration without errors (A = B = 1): out = 2 m - s psi, except at the
+// marked index, where the oracle's sign flip gives 2 m + s psi.  Amplitudes
+// move as 16-byte pairs, four pairs in flight per thread; the sums of each
+// group of eight amplitudes are formed in plain FP32 (their rounding errors
+// are independent and average out) and added into the float-pair
+// accumulators once per group.
+__device__ __forceinline__ void clean_pass(float2* psi, uint64_t lo, uint64_t hi, uint64_t m, float t2r, float t2i,
+                                           float sf, int tid, int T, Sums& acc, float& cmr, float& cmi) {
+  float4* p4 = reinterpret_cast<float4*>(psi);
+  const uint32_t vlo = (uint32_t)(lo >> 1), vhi = (uint32_t)(hi >> 1), vm = (uint32_t)(m >> 1);
+  const float nsf = -sf;
+  const bool modd = (m & 1) != 0;
+  auto one = [&](uint32_t v, const float4& u, float& bsr, float& bsi, float& bq) -> float4 {
+    float4 o;
+    o.x = fmaf(nsf, u.x, t2r);
+    o.y = fmaf(nsf, u.y, t2i);
+    o.z = fmaf(nsf, u.z, t2r);
+    o.w = fmaf(nsf, u.w, t2i);
+    if (v == vm) {
+      if (modd) {
+        o.z = fmaf(sf, u.z, t2r);
+        o.w = fmaf(sf, u.w, t2i);
+        cmr = o.z;
+        cmi = o.w;
+      } else {
+        o.x = fmaf(sf, u.x, t2r);
+        o.y = fmaf(sf, u.y, t2i);
+        cmr = o.x;
+        cmi = o.y;
+      }
+    }
+    bsr += o.x + o.z;
+    bsi += o.y + o.w;
+    bq = fmaf(o.x, o.x, bq);
+    bq = fmaf(o.y, o.y, bq);
+    bq = fmaf(o.z, o.z, bq);
+    bq = fmaf(o.w, o.w, bq);
+    return o;
+  };
+  const uint32_t uT = (uint32_t)T;
+  uint32_t v = vlo + (uint32_t)tid;
+  for (; v + 3u * uT < vhi; v += 4u * uT) {
+    const float4 u0 = p4[v], u1 = p4[v + uT], u2 = p4[v + 2u * uT], u3 = p4[v + 3u * uT];
+    float bsr = 0.f, bsi = 0.f, bq = 0.f;
+    p4[v] = one(v, u0, bsr, bsi, bq);
+    p4[v + uT] = one(v + uT, u1, bsr, bsi, bq);
+    p4[v + 2u * uT] = one(v + 2u * uT, u2, bsr, bsi, bq);
+    p4[v + 3u * uT] = one(v + 3u * uT, u3, bsr, bsi, bq);
+    ff_add(acc.sr, acc.cr, bsr);
+    ff_add(acc.si, acc.ci, bsi);
+    ff_add(acc.q, acc.cq, bq);
+  }
+  for (; v < vhi; v += uT) {
+    const float4 u0 = p4[v];
+    float bsr = 0.f, bsi = 0.f, bq = 0.f;
+    p4[v] = one(v, u0, bsr, bsi, bq);
+    ff_add(acc.sr, acc.cr, bsr);
+    ff_add(acc.si, acc.ci, bsi);
+    ff_add(acc.q, acc.cq, bq);
+  }
+}
+
 __global__ void __launch_bounds__(512, 2) k_traj(TrajParams P) {
   cg::cluster_group cluster = cg::this_cluster();
   const int G = (int)cluster.num_blocks();
@@ -250,6 +337,8 @@ __global__ void __launch_bounds__(512, 2) k_traj(TrajParams P) {
   __shared__ double shd[160];  // five 32-entry rows for bsum_pass
   __shared__ unsigned long long shu[32];
   __shared__ Pauli pA, pB;
+  __shared__ Pauli sh_e[4];  // the four stages of the next iteration
+  __shared__ int sh_ne[4];
   __shared__ int sh_err;
   __shared__ double wtab[QC_TRAJ_MAX_QUBITS + 1];
   __shared__ unsigned long long sh_target;
@@ -302,6 +391,8 @@ __global__ void __launch_bounds__(512, 2) k_traj(TrajParams P) {
       if (tid == 0)
         for (int v = 0; v < 5; ++v) xch.v[buf][v] = red[v];
     }
+    // the error draws of iteration 0 (stages 1..4, one per warp)
+    if (I.iters > 0 && tid < 128) draw_stage(P, I.id, 1 + (tid >> 5), n, tid & 31, sh_e, sh_ne, tid >> 5);
     __threadfence();
     cluster.sync();
     // the per-iteration FP64 scalars live in thread 0 only (GB300's FP64 pipe
@@ -317,24 +408,20 @@ __global__ void __launch_bounds__(512, 2) k_traj(TrajParams P) {
     }
     for (int it = 0; it < I.iters; ++it) {
       buf ^= 1;
-      const int st = 1 + 4 * it;
-      if (tid < 32) {
-        int ne = 0;
-        const Pauli e1 = stage_errors(P, I.id, st, n, tid, &ne);
-        const Pauli e2 = stage_errors(P, I.id, st + 1, n, tid, &ne);
-        const Pauli e3 = stage_errors(P, I.id, st + 2, n, tid, &ne);
-        const Pauli e4 = stage_errors(P, I.id, st + 3, n, tid, &ne);
-        if (tid == 0) {
-          pB = pmul(hconj(e2), e1);
-          pA = pmul(e4, hconj(e3));
-          sh_err += ne;
-        }
+      // three block barriers and one cluster barrier per iteration: the
+      // scalars below, the block reduction and the cluster exchange
+      if (tid == 0) {
+        const Pauli B = pmul(hconj(sh_e[1]), sh_e[0]), A = pmul(sh_e[3], hconj(sh_e[2]));
+        pB = B;
+        pA = A;
+        sh_err += sh_ne[0] + sh_ne[1] + sh_ne[2] + sh_ne[3];
+        // sum of O psi: S with the marked amplitude's sign flipped
+        if (!B.z) grover_scalars(S[0] - 2.0 * cm[0], S[1] - 2.0 * cm[1], Q, B.a, N, sh_sc);
       }
       __syncthreads();
       const Pauli A = pA, B = pB;
-      // sum of O psi, signed by Z^zB when B has Z factors
-      double W[2] = {S[0] - 2.0 * cm[0], S[1] - 2.0 * cm[1]};
       if (B.z) {
+        // sum of O psi, signed by Z^zB: one extra reading pass
         Sums acc;
         acc.zero();
         for (uint64_t j = lo + tid; j < hi; j += T) {
@@ -353,89 +440,59 @@ __global__ void __launch_bounds__(512, 2) k_traj(TrajParams P) {
         double g2[2];
         cluster_gather<2>(cluster, xch, buf, 5, g2);
         if (tid == 0) {
-          W[0] = g2[0];
-          W[1] = g2[1];
           const double sg = (__popcll(m & B.z) & 1) ? -1.0 : 1.0;
-          W[0] -= 2.0 * sg * cm[0];
-          W[1] -= 2.0 * sg * cm[1];
+          grover_scalars(g2[0] - 2.0 * sg * cm[0], g2[1] - 2.0 * sg * cm[1], Q, B.a, N, sh_sc);
         }
-        cluster.sync();  // every CTA has read the W slots before they are reused
+        // publishes sh_sc; every CTA has read the W slots before they are reused
+        cluster.sync();
       }
-      if (tid == 0) {
-        // m = mean of B O psi-hat = i^aB s W / N; broadcast 2m, s as floats
-        const double s = 1.0 / sqrt(Q);
-        double mr = W[0], mi = W[1];
-        const double r0 = mr, i0 = mi;
-        if (B.a == 1) { mr = -i0; mi = r0; }
-        else if (B.a == 2) { mr = -r0; mi = -i0; }
-        else if (B.a == 3) { mr = i0; mi = -r0; }
-        const double scale = s / (double)N;
-        sh_sc[0] = (float)(2.0 * mr * scale);
-        sh_sc[1] = (float)(2.0 * mi * scale);
-        sh_sc[2] = (float)s;
-      }
-      __syncthreads();
       const float t2r = sh_sc[0], t2i = sh_sc[1], sf = sh_sc[2];
       const uint64_t X = A.x ^ B.x;
       Sums acc;
       acc.zero();
       float cmr = 0.f, cmi = 0.f;
-      // out[j] from src = j ^ X
-      auto out_of = [&](uint64_t j, float2 u) -> float2 {
-        const uint64_t src = j ^ X;
-        float re = u.x * sf, im = u.y * sf;
-        if (src == m) { re = -re; im = -im; }                 // oracle
-        if (__popcll(src & B.z) & 1) { re = -re; im = -im; }  // B's Z part
-        ipow(B.a, re, im);
-        re = t2r - re;                                        // D
-        im = t2i - im;
-        if (__popcll((j ^ A.x) & A.z) & 1) { re = -re; im = -im; }
-        ipow(A.a, re, im);
-        return make_float2(re, im);
-      };
-      if (X == 0) {
-        // 16-byte vectors of two amplitudes, two vectors in flight per thread
-        float4* p4 = reinterpret_cast<float4*>(psi);
-        const uint64_t vhi = hi / 2;
-        uint64_t v = lo / 2 + tid;
-        for (; v + T < vhi; v += 2 * T) {
-          const float4 u = p4[v], w = p4[v + T];
-          const uint64_t j = 2 * v, k2 = 2 * (v + T);
-          const float2 o0 = out_of(j, make_float2(u.x, u.y)), o1 = out_of(j + 1, make_float2(u.z, u.w));
-          const float2 o2 = out_of(k2, make_float2(w.x, w.y)), o3 = out_of(k2 + 1, make_float2(w.z, w.w));
-          p4[v] = make_float4(o0.x, o0.y, o1.x, o1.y);
-          p4[v + T] = make_float4(o2.x, o2.y, o3.x, o3.y);
-          acc.add(o0.x, o0.y);
-          acc.add(o1.x, o1.y);
-          acc.add(o2.x, o2.y);
-          acc.add(o3.x, o3.y);
-          if ((j | 1) == (m | 1)) { cmr = (j == m) ? o0.x : o1.x; cmi = (j == m) ? o0.y : o1.y; }
-          if ((k2 | 1) == (m | 1)) { cmr = (k2 == m) ? o2.x : o3.x; cmi = (k2 == m) ? o2.y : o3.y; }
-        }
-        if (v < vhi) {
-          const float4 u = p4[v];
-          const uint64_t j = 2 * v;
-          const float2 o0 = out_of(j, make_float2(u.x, u.y)), o1 = out_of(j + 1, make_float2(u.z, u.w));
-          p4[v] = make_float4(o0.x, o0.y, o1.x, o1.y);
-          acc.add(o0.x, o0.y);
-          acc.add(o1.x, o1.y);
-          if ((j | 1) == (m | 1)) { cmr = (j == m) ? o0.x : o1.x; cmi = (j == m) ? o0.y : o1.y; }
-        }
+      if (((A.x | A.z | B.x | B.z) == 0) && ((A.a | B.a) == 0)) {
+        clean_pass(psi, lo, hi, m, t2r, t2i, sf, tid, T, acc, cmr, cmi);
       } else {
-        const int hb = 63 - __clzll((long long)X);
-        const uint64_t plo = lo / 2, phi = hi / 2;  // pair indices owned by this CTA
-        for (uint64_t p = plo + tid; p < phi; p += T) {
-          const uint64_t j = insert0(p, hb), jx = j ^ X;
-          const float2 u = psi[j], v = psi[jx];
-          const float2 oj = out_of(j, v), ojx = out_of(jx, u);
-          psi[j] = oj;
-          psi[jx] = ojx;
-          acc.add(oj.x, oj.y);
-          acc.add(ojx.x, ojx.y);
-          if (j == m) { cmr = oj.x; cmi = oj.y; }
-          if (jx == m) { cmr = ojx.x; cmi = ojx.y; }
+        // out[j] from src = j ^ X
+        auto out_of = [&](uint64_t j, float2 u) -> float2 {
+          const uint64_t src = j ^ X;
+          float re = u.x * sf, im = u.y * sf;
+          if (src == m) { re = -re; im = -im; }                 // oracle
+          if (__popcll(src & B.z) & 1) { re = -re; im = -im; }  // B's Z part
+          ipow(B.a, re, im);
+          re = t2r - re;                                        // D
+          im = t2i - im;
+          if (__popcll((j ^ A.x) & A.z) & 1) { re = -re; im = -im; }
+          ipow(A.a, re, im);
+          return make_float2(re, im);
+        };
+        if (X == 0) {
+          for (uint64_t j = lo + tid; j < hi; j += T) {
+            const float2 o = out_of(j, psi[j]);
+            psi[j] = o;
+            acc.add(o.x, o.y);
+            if (j == m) { cmr = o.x; cmi = o.y; }
+          }
+        } else {
+          const int hb = 63 - __clzll((long long)X);
+          const uint64_t plo = lo / 2, phi = hi / 2;  // pair indices owned by this CTA
+          for (uint64_t p = plo + tid; p < phi; p += T) {
+            const uint64_t j = insert0(p, hb), jx = j ^ X;
+            const float2 u = psi[j], v = psi[jx];
+            const float2 oj = out_of(j, v), ojx = out_of(jx, u);
+            psi[j] = oj;
+            psi[jx] = ojx;
+            acc.add(oj.x, oj.y);
+            acc.add(ojx.x, ojx.y);
+            if (j == m) { cmr = oj.x; cmi = oj.y; }
+            if (jx == m) { cmr = ojx.x; cmi = ojx.y; }
+          }
         }
       }
+      // the next iteration's error draws (thread 0 read sh_e before the
+      // barrier above), published by the reduction's barrier
+      if (it + 1 < I.iters && tid < 128) draw_stage(P, I.id, 5 + 4 * it + (tid >> 5), n, tid & 31, sh_e, sh_ne, tid >> 5);
       {
         const float hh[3] = {acc.sr, acc.si, acc.q}, ll[3] = {acc.cr, acc.ci, acc.cq};
         double red[5];

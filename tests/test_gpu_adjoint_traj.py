@@ -245,3 +245,18 @@ def test_traj_replay_vs_oracle(qc, p):
         if int(oc[i]) != O.trajectory_measure(prob, n, tb.seed, i, tb.thr_readout):
             mism += 1
     assert mism <= 1  # complex64 vs complex128 weights may split a CDF boundary
+
+
+@pytest.mark.parametrize("autotune", [0, 1])
+def test_traj_replay_wide_states(qc, autotune):
+    # 15..17 qubits: every CTA of a cluster streams several 16-byte vectors
+    # per thread, and most iterations draw no error (the error-free pass)
+    tb = W.trajectory_batch(6, 15, 17, seed=23, p_gate=2e-3, p_readout=0.01)
+    ps, pr, oc, ne, info = run_traj(qc, tb, autotune=autotune)
+    for i in range(len(tb.nq)):
+        n, m, k = int(tb.nq[i]), int(tb.marked[i]), int(tb.iters[i])
+        psi, errs = O.trajectory_run(n, m, k, tb.seed, i, tb.thr_gate)
+        assert ne[i] == errs
+        prob = O.probs(psi, n)
+        assert abs(ps[i] - prob[m] / prob.sum()) <= 1e-5
+        assert abs(pr[i] - O.readout_success(prob, n, m, tb.p_readout) / prob.sum()) <= 1e-5
