@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=30, help="qubits of the main workload")
+    ap.add_argument("--dtype", default="c128", choices=["c128", "c64"], help="state type of the main workload")
     ap.add_argument("--iters", type=int, default=100, help="Grover iterations per step")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -154,7 +155,7 @@ def read_traffic(profile_name, src_hash):
         if ":" in ln:
             k, v = ln.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_sha") != src_hash:
+    if vals.get("kernel_source_sha", "").split(" ")[0] != src_hash:
         return None
     try:
         return float(vals["traffic_bytes_per_launch_full_size"])
@@ -190,9 +191,10 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     n, iters = args.n, args.iters
     N = 1 << n
-    S = N * 16
+    amp = 16 if args.dtype == "c128" else 8
+    S = N * amp
     marked = W.marked_indices(W.rng(2026), n, 8)
-    st = qc.State(n, qc.QC_C128)
+    st = qc.State(n, qc.QC_C128 if args.dtype == "c128" else qc.QC_C64)
     H = np.array([[1, 1], [1, -1]], dtype=np.complex128) / math.sqrt(2.0)
     ops_per_step = 1 + iters + 1 + 3 * n
 
@@ -275,7 +277,7 @@ def run_ours(args, ws, rank, local):
         "grover_step (prep+pass+fix)": {"ms": grover_ms, "alg_bytes": 2 * S, "GB/s": gb(2 * S, grover_ms),
                                         "launches_per_step": iters * 3},
         "hall_uniform_fill": {"ms": comp["hall_uniform"], "alg_bytes": S, "GB/s": gb(S, comp["hall_uniform"])},
-        "qft": {"ms": comp["qft"], "alg_bytes": qft_bytes(n, 16), "GB/s": gb(qft_bytes(n, 16), comp["qft"])},
+        "qft": {"ms": comp["qft"], "alg_bytes": qft_bytes(n, amp), "GB/s": gb(qft_bytes(n, amp), comp["qft"])},
     }
     sweep_table = {}
     for g in ("h", "cnot", "cphase"):
@@ -285,20 +287,23 @@ def run_ours(args, ws, rank, local):
                           "frac_of_measured_min": round(min(gb(bytes_gate[g], m) for m in ms) / hbm, 3),
                           "frac_of_measured_max": round(max(gb(bytes_gate[g], m) for m in ms) / hbm, 3)}
     # dominant kernel: the fused Grover pass (100 launches per step)
-    src_hash = kernel_source_hash(["grover.cu", "common.cuh"])
-    traffic = read_traffic("grover_pass_n30_c128.txt", src_hash)
+    src_hash = kernel_source_hash(["grover.cu", "common.cuh", "ff.cuh"])
+    traffic = read_traffic("grover_pass_n30_c128.txt", src_hash) if args.dtype == "c128" and n == 30 else None
     achieved = gb(2 * S, grover_ms)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": traffic,
-                "kernel": "k_grover_pass_c128 (one fused oracle+diffusion read/write pass)",
+                "kernel": "k_grover_pass_%s (one fused oracle+diffusion read/write pass)" % args.dtype,
                 "alg_bytes_per_launch": 2 * S, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
-        "config": {"workload": "grover%d_qft_sweep_c128" % n, "qubits": n, "state_bytes": S,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128 (f64 storage; f64 and double-float arithmetic)" if args.dtype == "c128" else "c64 (f32; f64 reductions)",
+        "data": "synthetic",
+        "config": {"workload": "grover%d_qft_sweep_%s" % (n, args.dtype), "qubits": n, "state_bytes": S,
                    "grover_iterations": iters, "marked": 8, "sweep": "H, CNOT(t+1 mod n, t), CPHASE k=1 for t=0..n-1",
-                   "operators_per_step": ops_per_step, "l2": "inputs larger than L2 (16 GiB state)",
+                   "operators_per_step": ops_per_step,
+                   "l2": "inputs larger than L2 (%.1f GiB state)" % (S / 2 ** 30) if S > 2 ** 27 else "state fits in L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches),
         "kernels": kernels, "sweep": sweep_table, "component_ms_per_step": comp,
@@ -331,9 +336,11 @@ def run_e2e(args, st, step_fn, ops_per_step, N):
     import numpy as np
     import torch
     n = args.n
-    host_in = torch.zeros(N, dtype=torch.complex128, pin_memory=True)
+    cdt = st.tensor.dtype
+    amp = st.tensor.element_size()
+    host_in = torch.zeros(N, dtype=cdt, pin_memory=True)
     host_in[0] = 1.0
-    host_out = torch.empty(N, dtype=torch.complex128, pin_memory=True)
+    host_out = torch.empty(N, dtype=cdt, pin_memory=True)
     host_shots = torch.empty(1000, dtype=torch.int64, pin_memory=True)
     import paper_0902_0699_gb300 as qc
 
@@ -352,8 +359,8 @@ def run_e2e(args, st, step_fn, ops_per_step, N):
     el = (time.perf_counter() - t0) * 1e3
     tmax, wsum = aggregate(el, float(ops_per_step) * N * args.steps)
     del host_in, host_out
-    return {"value": wsum / (tmax / 1e3), "unit": UNIT, "h2d_bytes_per_step": N * 16 + 8 * 8,
-            "d2h_bytes_per_step": N * 16 + 8 * 1000, "ms_per_step": tmax / args.steps,
+    return {"value": wsum / (tmax / 1e3), "unit": UNIT, "h2d_bytes_per_step": N * amp + 8 * 8,
+            "d2h_bytes_per_step": N * amp + 8 * 1000, "ms_per_step": tmax / args.steps,
             "note": "host state in pinned memory -> device, full step, final state and samples -> host"}
 
 
