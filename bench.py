@@ -478,13 +478,14 @@ def extra_c2():
     return res
 
 
-def extra_c4():
+def extra_c4(n_inst=4096, n_lo=12, n_hi=20, seed=4096, autotune=1):
+    """Noisy Grover trajectories: n_inst instances with n ~ U{n_lo..n_hi}."""
     import ctypes
     import numpy as np
     import torch
     import paper_0902_0699_gb300 as qc
     import workloads as W
-    tb = W.trajectory_batch(4096, 12, 20, seed=4096)
+    tb = W.trajectory_batch(n_inst, n_lo, n_hi, seed=seed)
     n_inst = len(tb.nq)
     nq = np.ascontiguousarray(tb.nq, dtype=np.int32)
     mk = np.ascontiguousarray(tb.marked, dtype=np.uint64)
@@ -496,7 +497,7 @@ def extra_c4():
     plan = ctypes.c_void_p()
     s = torch.cuda.current_stream().cuda_stream
     t0 = time.perf_counter()
-    rc = qc.lib().qc_traj_plan_create(ctypes.byref(d), ctypes.c_void_p(s), 1, ctypes.byref(plan))
+    rc = qc.lib().qc_traj_plan_create(ctypes.byref(d), ctypes.c_void_p(s), autotune, ctypes.byref(plan))
     torch.cuda.synchronize()
     t_plan = time.perf_counter() - t0
     if rc:
@@ -531,7 +532,6 @@ def extra_c5():
     import ctypes
     import numpy as np
     import torch
-    import oracle  # noqa: F401  (gate list helper lives with the workloads)
     import paper_0902_0699_gb300 as qc
     import workloads as W
     n, layers = 20, 50
@@ -650,7 +650,9 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     if args.only:
-        fn = {"c64": extra_c64, "c1": extra_c1, "c2": extra_c2, "c4": extra_c4, "c5": extra_c5}[args.only]
+        fn = {"c64": extra_c64, "c1": extra_c1, "c2": extra_c2, "c4": extra_c4, "c5": extra_c5,
+              # a small trajectory batch (96 instances, 16..18 qubits) for profiling
+              "c4s": lambda: extra_c4(96, 16, 18, seed=7, autotune=0)}[args.only]
         print(json.dumps({args.only: fn()}), flush=True)
         return 0
     out, st, step_fn, ops, N = run_ours(args, ws, rank, local)

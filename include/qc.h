@@ -217,8 +217,13 @@ qc_status qc_renormalize(qc_state* s, double* norm_out_host);
  *   (Salmon et al., SC'11) with counter (s_lo, s_hi, 0, 0) and key
  *   (seed_lo, seed_hi), r = x0 * 2^32 + x1, target = floor(r * total / 2^64),
  *   outcome = smallest i with W_i > target.
- * Requires sum p_i <= 2 (QC_EINVAL otherwise) and shots >= 0.  Uses a
- * temporary device buffer of 8 * 2^n bytes (QC_ENOMEM if it does not fit). */
+ * Requires every p_i in [0, 2] and 0 < total <= 2^63 (so sum p_i <= 2;
+ * QC_EINVAL otherwise) and shots >= 0.  With shots <= 2^n / 2048 each shot
+ * rescans the one block of 2048 amplitudes that holds its target, and the
+ * temporary device buffer is 8 * (2^n / 2048 + 2) bytes; with more shots
+ * the full W is written, 8 * (2^n + 2^n / 2048 + 2) bytes (QC_ENOMEM if it
+ * does not fit).  Both give the outcomes above.  Synchronises the stream
+ * once (to read the total back). */
 qc_status qc_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_t* out_dev);
 
 /* Seeded measurement for callers that cannot allocate device memory.  The

@@ -251,23 +251,55 @@ qc_status reduce_expect(const qc_state* s, uint64_t x, uint64_t z, double* out_h
 // w_i = trunc(p_i * 2^62); W = inclusive prefix sum (exact integers, so the
 // parallel order does not matter); shot s: target = floor(r * W_{N-1} /
 // 2^64), outcome = smallest i with W_i > target.
+//
+// Only the per-block weight sums (one per SMP_BLOCK amplitudes) are scanned
+// over the whole state.  With few shots, each shot finds its block by
+// bisection over the block offsets and rescans that block's weights; with
+// many shots the full CDF is written once and bisected per shot.
 #define SMP_PER 8
 #define SMP_T 256
 #define SMP_BLOCK (SMP_PER * SMP_T)
+#define SMP_BAD_P 1ull     // some p_i outside [0, 2] or NaN
+#define SMP_OVERFLOW 2ull  // a weight sum above 2^64 - 1
 
-template <typename R>
-__device__ __forceinline__ uint64_t weight_of(typename CT<R>::V2 v) {
-  const double p = prob_of<R>(v);
-  return __double2ull_rz(p * 4611686018427387904.0);
+// a + b, saturated at 2^64 - 1 (associative, so any summation order
+// saturates exactly when the true sum does not fit)
+__device__ __forceinline__ uint64_t sat_add(uint64_t a, uint64_t b) {
+  const uint64_t s = a + b;
+  return s < a ? ~0ull : s;
 }
 
+// trunc(p * 2^62) for 0 <= p <= 2 from the IEEE-754 fields, with integer
+// operations only: p = m * 2^(e - 1075) with the 53-bit significand m, so
+// p * 2^62 = m * 2^(e - 1013).  Sets *bad (and returns 0) for p outside
+// [0, 2] or NaN, i.e. for a bit pattern above that of 2.0 (unsigned).
+__device__ __forceinline__ uint64_t weight_of_p(double p, bool* bad) {
+  const uint64_t b = (uint64_t)__double_as_longlong(p);
+  if (b > 0x4000000000000000ull) {
+    *bad = true;
+    return 0;
+  }
+  const int e = (int)(b >> 52);
+  const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
+  const int sh = e - 1013;
+  if (sh >= 0) return m << sh;  // sh <= 11: m << sh <= 2^63
+  return sh <= -64 ? 0ull : m >> (-sh);
+}
+
+template <typename R>
+__device__ __forceinline__ uint64_t weight_of(typename CT<R>::V2 v, bool* bad) {
+  return weight_of_p(prob_of<R>(v), bad);
+}
+
+// Exclusive block scan with saturating sums; *total (if given) receives the
+// block total.  Exact whenever the block total fits in 64 bits.
 __device__ __forceinline__ uint64_t block_excl_scan_u64(uint64_t v, uint64_t* total) {
   __shared__ uint64_t ws[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint64_t x = v;
   for (int o = 1; o < 32; o <<= 1) {
     const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
+    if (lane >= o) x = sat_add(x, y);
   }
   if (lane == 31) ws[w] = x;
   __syncthreads();
@@ -276,7 +308,7 @@ __device__ __forceinline__ uint64_t block_excl_scan_u64(uint64_t v, uint64_t* to
     uint64_t t = lane < nw ? ws[lane] : 0ull;
     for (int o = 1; o < 32; o <<= 1) {
       const uint64_t y = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += y;
+      if (lane >= o) t = sat_add(t, y);
     }
     ws[lane] = t;  // inclusive over warps
   }
@@ -288,66 +320,91 @@ __device__ __forceinline__ uint64_t block_excl_scan_u64(uint64_t v, uint64_t* to
   return r;
 }
 
+// Weights of the SMP_PER consecutive elements thread `t` owns in block b.
+template <typename R>
+__device__ __forceinline__ uint64_t thread_weights(const typename CT<R>::V2* __restrict__ s, uint64_t N, uint64_t b,
+                                                   int t, uint64_t w[SMP_PER], bool* bad) {
+  const uint64_t base = b * SMP_BLOCK + (uint64_t)t * SMP_PER;
+  uint64_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < SMP_PER; ++k) {
+    const uint64_t i = base + k;
+    w[k] = i < N ? weight_of<R>(s[i], bad) : 0ull;
+    sum = sat_add(sum, w[k]);
+  }
+  return sum;
+}
+
+// Per-block weight sums; status bits for unusable probabilities.
 template <typename R>
 __global__ void __launch_bounds__(SMP_T) k_wsum(const typename CT<R>::V2* __restrict__ s, uint64_t N,
-                                                uint64_t* __restrict__ bsum) {
+                                                uint64_t* __restrict__ bsum, uint64_t* __restrict__ status) {
+  // coalesced: the sum does not depend on which thread adds which weight
   const uint64_t base = (uint64_t)blockIdx.x * SMP_BLOCK;
+  bool bad = false;
   uint64_t t = 0;
+#pragma unroll
   for (int k = 0; k < SMP_PER; ++k) {
     const uint64_t i = base + (uint64_t)k * SMP_T + threadIdx.x;
-    if (i < N) t += weight_of<R>(s[i]);
+    if (i < N) t = sat_add(t, weight_of<R>(s[i], &bad));
   }
   uint64_t tot = 0;
   block_excl_scan_u64(t, &tot);
   if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr((unsigned long long*)status, SMP_BAD_P);
 }
 
-// Exclusive scan of the block sums, one block.
-__global__ void __launch_bounds__(1024) k_scan_bsum(uint64_t* __restrict__ bsum, uint64_t nb) {
+// Exclusive scan of the block sums in place (one block); tail[0] receives
+// the total and status gets SMP_OVERFLOW if it does not fit in 64 bits.
+__global__ void __launch_bounds__(1024) k_scan_bsum(uint64_t* __restrict__ bsum, uint64_t nb,
+                                                    uint64_t* __restrict__ tail, uint64_t* __restrict__ status) {
   const uint64_t per = (nb + blockDim.x - 1) / blockDim.x;
   const uint64_t lo = (uint64_t)threadIdx.x * per;
   uint64_t t = 0;
-  for (uint64_t i = lo; i < lo + per && i < nb; ++i) t += bsum[i];
-  uint64_t off = block_excl_scan_u64(t, nullptr);
+  for (uint64_t i = lo; i < lo + per && i < nb; ++i) t = sat_add(t, bsum[i]);
+  uint64_t total = 0;
+  uint64_t off = block_excl_scan_u64(t, &total);
   for (uint64_t i = lo; i < lo + per && i < nb; ++i) {
     const uint64_t v = bsum[i];
     bsum[i] = off;
     off += v;
+  }
+  if (threadIdx.x == 0) {
+    if (tail) tail[0] = total;
+    if (total == ~0ull) atomicOr((unsigned long long*)status, SMP_OVERFLOW);
   }
 }
 
 template <typename R>
 __global__ void __launch_bounds__(SMP_T) k_wcdf(const typename CT<R>::V2* __restrict__ s, uint64_t N,
                                                 const uint64_t* __restrict__ boff, uint64_t* __restrict__ cdf) {
-  // thread owns SMP_PER consecutive elements
-  const uint64_t base = (uint64_t)blockIdx.x * SMP_BLOCK + (uint64_t)threadIdx.x * SMP_PER;
   uint64_t w[SMP_PER];
-  uint64_t t = 0;
-#pragma unroll
-  for (int k = 0; k < SMP_PER; ++k) {
-    const uint64_t i = base + k;
-    w[k] = i < N ? weight_of<R>(s[i]) : 0ull;
-    t += w[k];
-  }
+  bool bad = false;
+  const uint64_t t = thread_weights<R>(s, N, blockIdx.x, threadIdx.x, w, &bad);
   uint64_t run = boff[blockIdx.x] + block_excl_scan_u64(t, nullptr);
+  const uint64_t base = (uint64_t)blockIdx.x * SMP_BLOCK + (uint64_t)threadIdx.x * SMP_PER;
 #pragma unroll
   for (int k = 0; k < SMP_PER; ++k) {
-    const uint64_t i = base + k;
     run += w[k];
-    if (i < N) cdf[i] = run;
+    if (base + k < N) cdf[base + k] = run;
   }
 }
 
+__device__ __forceinline__ uint64_t shot_target(int64_t sh, uint64_t seed, uint64_t total) {
+  uint32_t x[4];
+  philox4x32_10((uint32_t)(uint64_t)sh, (uint32_t)((uint64_t)sh >> 32), 0u, 0u, (uint32_t)seed,
+                (uint32_t)(seed >> 32), x);
+  const uint64_t r = ((uint64_t)x[0] << 32) | x[1];
+  return __umul64hi(r, total);
+}
+
+// Many shots: bisection of the full CDF.
 __global__ void k_sample(const uint64_t* __restrict__ cdf, uint64_t N, uint64_t seed, int64_t shots,
                          uint64_t* __restrict__ out) {
   const uint64_t total = cdf[N - 1];
   for (int64_t sh = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sh < shots;
        sh += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t x[4];
-    philox4x32_10((uint32_t)(uint64_t)sh, (uint32_t)((uint64_t)sh >> 32), 0u, 0u, (uint32_t)seed,
-                  (uint32_t)(seed >> 32), x);
-    const uint64_t r = ((uint64_t)x[0] << 32) | x[1];
-    const uint64_t target = __umul64hi(r, total);
+    const uint64_t target = shot_target(sh, seed, total);
     uint64_t lo = 0, hi = N - 1;  // answer in [lo, hi]; cdf[N-1] = total > target
     while (lo < hi) {
       const uint64_t mid = lo + ((hi - lo) >> 1);
@@ -358,35 +415,93 @@ __global__ void k_sample(const uint64_t* __restrict__ cdf, uint64_t N, uint64_t 
   }
 }
 
-qc_status launch_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_t* out) {
-  double nrm = 0.0;
-  qc_status st = reduce_norm(s, &nrm);
-  if (st) return st;
-  if (!(nrm <= 2.0) || !(nrm > 0.0)) {
-    set_error("sampling needs 0 < sum |C|^2 <= 2 (got %g)", nrm);
-    return QC_EINVAL;
+// Few shots: one CTA per shot finds the block holding the target (the last
+// block whose exclusive offset is <= target) and rescans its weights.
+template <typename R>
+__global__ void __launch_bounds__(SMP_T) k_sample_local(const typename CT<R>::V2* __restrict__ s, uint64_t N,
+                                                        const uint64_t* __restrict__ boff, uint64_t nb,
+                                                        const uint64_t* __restrict__ tail, uint64_t seed,
+                                                        int64_t shots, uint64_t* __restrict__ out) {
+  const uint64_t total = tail[0];
+  for (int64_t sh = blockIdx.x; sh < shots; sh += gridDim.x) {
+    const uint64_t target = shot_target(sh, seed, total);
+    uint64_t lo = 0, hi = nb - 1;  // boff[0] = 0 <= target
+    while (lo < hi) {
+      const uint64_t mid = hi - ((hi - lo) >> 1);
+      if (boff[mid] <= target) lo = mid;
+      else hi = mid - 1;
+    }
+    uint64_t w[SMP_PER];
+    bool bad = false;
+    const uint64_t t = thread_weights<R>(s, N, lo, threadIdx.x, w, &bad);
+    uint64_t run = boff[lo] + block_excl_scan_u64(t, nullptr);
+    const uint64_t base = lo * SMP_BLOCK + (uint64_t)threadIdx.x * SMP_PER;
+    if (run <= target && target < run + t) {
+#pragma unroll
+      for (int k = 0; k < SMP_PER; ++k) {
+        const uint64_t prev = run;
+        run += w[k];
+        if (prev <= target && target < run) out[sh] = base + k;
+      }
+    }
   }
+}
+
+qc_status launch_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_t* out) {
   const uint64_t N = 1ull << s->n;
   const uint64_t nb = (N + SMP_BLOCK - 1) / SMP_BLOCK;
+  const bool local = (uint64_t)shots <= nb;
+  // [cdf (many shots only)] [block offsets nb] [total] [status]
+  const uint64_t words = (local ? 0 : N) + nb + 2;
   uint64_t* buf = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&buf, (N + nb) * sizeof(uint64_t), s->stream);
+  cudaError_t e = cudaMallocAsync((void**)&buf, words * sizeof(uint64_t), s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "sampler buffer");
   uint64_t* cdf = buf;
-  uint64_t* bsum = buf + N;
-  if (s->dt == QC_C128) {
-    const double2* d = reinterpret_cast<const double2*>(s->data);
-    k_wsum<double><<<(unsigned)nb, SMP_T, 0, s->stream>>>(d, N, bsum);
-    k_scan_bsum<<<1, 1024, 0, s->stream>>>(bsum, nb);
-    k_wcdf<double><<<(unsigned)nb, SMP_T, 0, s->stream>>>(d, N, bsum, cdf);
-  } else {
-    const float2* d = reinterpret_cast<const float2*>(s->data);
-    k_wsum<float><<<(unsigned)nb, SMP_T, 0, s->stream>>>(d, N, bsum);
-    k_scan_bsum<<<1, 1024, 0, s->stream>>>(bsum, nb);
-    k_wcdf<float><<<(unsigned)nb, SMP_T, 0, s->stream>>>(d, N, bsum, cdf);
+  uint64_t* bsum = buf + (local ? 0 : N);
+  uint64_t* tail = bsum + nb;
+  uint64_t* status = tail + 1;
+  e = cudaMemsetAsync(status, 0, sizeof(uint64_t), s->stream);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(buf, s->stream);
+    return cuda_fail(e, "sampler status reset");
   }
-  const unsigned g = (unsigned)std::min<int64_t>((shots + 255) / 256, (int64_t)sm_count() * 8);
-  k_sample<<<g, 256, 0, s->stream>>>(cdf, N, seed, shots, out);
-  st = check_launch("sample", 4);
+  if (s->dt == QC_C128)
+    k_wsum<double><<<(unsigned)nb, SMP_T, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), N, bsum, status);
+  else
+    k_wsum<float><<<(unsigned)nb, SMP_T, 0, s->stream>>>(reinterpret_cast<const float2*>(s->data), N, bsum, status);
+  k_scan_bsum<<<1, 1024, 0, s->stream>>>(bsum, nb, tail, status);
+  qc_status st = check_launch("sample weights", 2);
+  uint64_t h[2] = {0, 0};
+  if (!st) {
+    e = cudaMemcpyAsync(h, tail, sizeof h, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "sampler total readback");
+  }
+  if (!st && (h[1] || h[0] == 0 || h[0] > (1ull << 63))) {
+    set_error("sampling needs every |C_i|^2 in [0, 2] and 0 < sum trunc(|C_i|^2 2^62) <= 2^63 "
+              "(status %llu, total %llu)", (unsigned long long)h[1], (unsigned long long)h[0]);
+    st = QC_EINVAL;
+  }
+  if (!st) {
+    if (local) {
+      const unsigned g = (unsigned)std::min<int64_t>(shots, (int64_t)sm_count() * 8);
+      if (s->dt == QC_C128)
+        k_sample_local<double><<<g, SMP_T, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), N, bsum, nb,
+                                                           tail, seed, shots, out);
+      else
+        k_sample_local<float><<<g, SMP_T, 0, s->stream>>>(reinterpret_cast<const float2*>(s->data), N, bsum, nb,
+                                                          tail, seed, shots, out);
+      st = check_launch("sample", 1);
+    } else {
+      if (s->dt == QC_C128)
+        k_wcdf<double><<<(unsigned)nb, SMP_T, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), N, bsum, cdf);
+      else
+        k_wcdf<float><<<(unsigned)nb, SMP_T, 0, s->stream>>>(reinterpret_cast<const float2*>(s->data), N, bsum, cdf);
+      const unsigned g = (unsigned)std::min<int64_t>((shots + 255) / 256, (int64_t)sm_count() * 8);
+      k_sample<<<g, 256, 0, s->stream>>>(cdf, N, seed, shots, out);
+      st = check_launch("sample", 2);
+    }
+  }
   cudaFreeAsync(buf, s->stream);
   return st;
 }
@@ -404,18 +519,8 @@ static __device__ __align__(256) uint64_t g_noalloc_scratch[NA_CDF + NA_BSUM + 3
 // stand-in for the symbol, so the address is looked up once per device).
 static uint64_t* g_noalloc_ptr[64] = {nullptr};
 
-// Status bits: 1 = some p_i outside [0, 2] (or NaN), 2 = total weight zero or
-// above 2^63.
-template <typename R>
-__global__ void k_noalloc_check(const typename CT<R>::V2* __restrict__ s, uint64_t N, uint64_t* __restrict__ status) {
-  bool bad = false;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
-    const double p = prob_of<R>(s[i]);
-    bad |= !(p >= 0.0 && p <= 2.0);
-  }
-  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr((unsigned long long*)status, 1ull);
-}
-
+// Status bits: 1 = some p_i outside [0, 2] (or NaN, from k_wsum), 2 = total
+// weight zero or above 2^63.
 __global__ void k_noalloc_total(const uint64_t* __restrict__ cdf, uint64_t N, uint64_t* __restrict__ status) {
   const uint64_t total = cdf[N - 1];
   if (total == 0 || total > (1ull << 63)) atomicOr((unsigned long long*)status, 2ull);
@@ -463,22 +568,19 @@ QC_API qc_status qc_sample_noalloc(const void* psi_dev, int n, qc_dtype dt, uint
   const uint64_t nb = (N + SMP_BLOCK - 1) / SMP_BLOCK;
   e = cudaMemsetAsync(status, 0, sizeof(uint64_t), st);  // the previous call's status is stale
   if (e != cudaSuccess) return cuda_fail(e, "qc_sample_noalloc: status reset");
-  const unsigned gc = (unsigned)std::min<uint64_t>((N + 255) / 256, (uint64_t)sm_count() * 4);
   if (dt == QC_C128) {
     const double2* d = reinterpret_cast<const double2*>(psi_dev);
-    k_noalloc_check<double><<<gc, 256, 0, st>>>(d, N, status);
-    k_wsum<double><<<(unsigned)nb, SMP_T, 0, st>>>(d, N, bsum);
-    k_scan_bsum<<<1, 1024, 0, st>>>(bsum, nb);
+    k_wsum<double><<<(unsigned)nb, SMP_T, 0, st>>>(d, N, bsum, status);
+    k_scan_bsum<<<1, 1024, 0, st>>>(bsum, nb, nullptr, status);
     k_wcdf<double><<<(unsigned)nb, SMP_T, 0, st>>>(d, N, bsum, cdf);
   } else {
     const float2* d = reinterpret_cast<const float2*>(psi_dev);
-    k_noalloc_check<float><<<gc, 256, 0, st>>>(d, N, status);
-    k_wsum<float><<<(unsigned)nb, SMP_T, 0, st>>>(d, N, bsum);
-    k_scan_bsum<<<1, 1024, 0, st>>>(bsum, nb);
+    k_wsum<float><<<(unsigned)nb, SMP_T, 0, st>>>(d, N, bsum, status);
+    k_scan_bsum<<<1, 1024, 0, st>>>(bsum, nb, nullptr, status);
     k_wcdf<float><<<(unsigned)nb, SMP_T, 0, st>>>(d, N, bsum, cdf);
   }
   k_noalloc_total<<<1, 1, 0, st>>>(cdf, N, status);
-  qc_status rs = check_launch("qc_sample_noalloc: cdf", 5);
+  qc_status rs = check_launch("qc_sample_noalloc: cdf", 4);
   if (rs) return rs;
   uint64_t hstat = 0;
   e = cudaMemcpyAsync(&hstat, status, sizeof hstat, cudaMemcpyDeviceToHost, st);

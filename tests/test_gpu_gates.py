@@ -214,6 +214,44 @@ def test_sample_bit_exact(qc, dt, n):
         assert np.array_equal(got, ref)
 
 
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n,shots", [(12, 1), (12, 2), (12, 3), (16, 32), (16, 33), (20, 500)])
+def test_sample_block_local_and_cdf_paths(qc, dt, n, shots):
+    # shots <= 2^n / 2048 rescans one 2048-amplitude block per shot; more
+    # shots write the full CDF: both must give the definition's outcomes
+    s, v = mk(qc, n, dt, seed=n + 5 * shots)
+    p = s.probs().cpu().numpy()
+    for seed in (3, 2 ** 33 + 1):
+        got = s.sample(seed, shots).cpu().numpy().astype(np.uint64)
+        assert np.array_equal(got, O.sample_from_probs(p, seed, shots))
+
+
+@pytest.mark.parametrize("shots", [4, 64])
+def test_sample_sparse_state(qc, shots):
+    # most 2048-amplitude blocks carry zero weight: the block search must
+    # skip runs of equal offsets
+    n = 17
+    vec = np.zeros(1 << n, dtype=complex)
+    for i, a in ((5, 0.3), (40000, 0.5j), (40001, 0.1), (131071, 0.8 - 0.1j)):
+        vec[i] = a
+    vec /= np.linalg.norm(vec)
+    s, _ = mk(qc, n, 0, vec=vec)
+    p = s.probs().cpu().numpy()
+    got = s.sample(77, shots).cpu().numpy().astype(np.uint64)
+    assert np.array_equal(got, O.sample_from_probs(p, 77, shots))
+    assert set(got.tolist()) <= {5, 40000, 40001, 131071}
+
+
+def test_sample_rejects_unusable_probabilities(qc):
+    n = 13
+    for vec in (np.zeros(1 << n, dtype=complex), np.full(1 << n, 1.5 + 0j), np.full(1 << n, 0.9 + 0j)):
+        s, _ = mk(qc, n, 0, vec=vec)
+        for shots in (1, 100):
+            with pytest.raises(qc.QCError) as e:
+                s.sample(1, shots)
+            assert e.value.status == qc.QC_EINVAL
+
+
 def test_renormalize(qc):
     n = 9
     s, v = mk(qc, n, 0, vec=W.random_state(W.rng(2), n) * 1.7)
