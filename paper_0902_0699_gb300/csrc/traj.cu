@@ -22,6 +22,13 @@
 //   out[j] = A-phase(j) * (2 m - B-phase * s * (O psi)[j ^ xA ^ xB]),
 // where m is the mean of B O psi-hat and s = 1/sqrt(Q) renormalises the
 // state every iteration (complex64 arithmetic, FP64 reductions).
+//
+// At the error rates of interest most iterations draw no error, and such an
+// iteration moves every unmarked amplitude by one common affine map (see
+// Track below).  The draws of 256 iterations are made up front, in
+// parallel; error-free iterations then only update FP64 scalars in thread
+// 0, and the state is read and written only by iterations with errors (and
+// once at the end), which apply the pending map on the fly.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -90,13 +97,16 @@ __device__ __forceinline__ void ipow(int a, float& re, float& im) {
   else if (a == 3) { re = i; im = -r; }
 }
 
+// Partial sums exchanged between the CTAs of a cluster, as float pairs
+// (hi, lo), double-buffered: S re, S im, Q, cm re, cm im, W re, W im, aux.
 struct Xch {
   int inst;
   int pad;
-  double v[2][8];  // double-buffered partials: S re, S im, Q, cm re, cm im, aux0, aux1, aux2
+  float2 v[2][8];
   unsigned long long w[2];
 };
 
+// One float-pair accumulation step s + c += p (Knuth two-sum, error kept).
 __device__ __forceinline__ void ff_add(float& s, float& c, float p) {
   const float t = s + p;
   const float bp = t - s;
@@ -104,36 +114,8 @@ __device__ __forceinline__ void ff_add(float& s, float& c, float p) {
   s = t;
 }
 
-struct Sums {  // per-thread float-pair accumulators
-  float sr, cr, si, ci, q, cq;
-  __device__ void zero() { sr = cr = si = ci = q = cq = 0.f; }
-  __device__ void add(float re, float im) {
-    ff_add(sr, cr, re);
-    ff_add(si, ci, im);
-    const float p = re * re;
-    ff_add(q, cq, p);
-    cq += fmaf(re, re, -p);
-    const float p2 = im * im;
-    ff_add(q, cq, p2);
-    cq += fmaf(im, im, -p2);
-  }
-};
-
-__device__ __forceinline__ double bsum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double t = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-  return t;  // every thread gets the same value
-}
-
-// Block sum of float pairs (h + l) on the FP32 pipe: two-sum reduction across
-// the warp, one FP64 add per warp, the warp totals added in FP64 by thread 0.
-// The result is valid in thread 0 only (the FP64 pipe of GB300 is too
-// narrow to let every thread take part).
-__device__ __forceinline__ double bsum_ff(float h, float l, double* sh) {
+// Float-pair sum across a warp (every lane gets the total).
+__device__ __forceinline__ void warp_ff_sum(float& h, float& l) {
   for (int o = 16; o > 0; o >>= 1) {
     const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
     float s, e;
@@ -141,70 +123,56 @@ __device__ __forceinline__ double bsum_ff(float h, float l, double* sh) {
     e = e + (l + l2);
     two_sum(s, e, h, l);
   }
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)h + (double)l;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-  return t;
 }
 
-// The three float-pair sums of a pass (S re, S im, Q) and the marked
-// amplitude (nonzero in one thread only) in one block reduction; results in
-// thread 0: out[0..4] = S re, S im, Q, cm re, cm im.  The caller guarantees a
-// block barrier between thread 0's last read of `sh` and this call.
-__device__ __forceinline__ void bsum_pass(const float h[3], const float l[3], float cr, float ci, double* sh,
-                                          double out[5]) {
-  float H[3] = {h[0], h[1], h[2]}, L[3] = {l[0], l[1], l[2]};
-  for (int o = 16; o > 0; o >>= 1) {
+// Block sums of NV float pairs, all on the FP32 pipe (a single thread's FP64
+// chain is slow on GB300): warp sums, then warp 0 sums the warp totals.  The
+// results are valid in thread 0.  The caller guarantees a block barrier
+// between thread 0's last read of `sh` (NV * 32 entries) and this call.
+template <int NV>
+__device__ __forceinline__ void block_ff_sum(float h[NV], float l[NV], float2* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-    for (int v = 0; v < 3; ++v) {
-      const float h2 = __shfl_xor_sync(0xffffffffu, H[v], o), l2 = __shfl_xor_sync(0xffffffffu, L[v], o);
-      float s, e;
-      two_sum(H[v], h2, s, e);
-      e = e + (L[v] + l2);
-      two_sum(s, e, H[v], L[v]);
-    }
-    cr += __shfl_xor_sync(0xffffffffu, cr, o);  // one nonzero term: exact
-    ci += __shfl_xor_sync(0xffffffffu, ci, o);
-  }
-  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    for (int v = 0; v < 3; ++v) sh[v * 32 + w] = (double)H[v] + (double)L[v];
-    sh[96 + w] = (double)cr;
-    sh[128 + w] = (double)ci;
+  for (int v = 0; v < NV; ++v) {
+    warp_ff_sum(h[v], l[v]);
+    if (lane == 0) sh[v * 32 + w] = make_float2(h[v], l[v]);
   }
   __syncthreads();
-  if (threadIdx.x == 0)
-    for (int v = 0; v < 5; ++v) {
-      double t = 0.0;
-      for (int i = 0; i < nw; ++i) t += sh[v * 32 + i];
-      out[v] = t;
+  if (w == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const float2 x = lane < nw ? sh[v * 32 + lane] : make_float2(0.f, 0.f);
+      h[v] = x.x;
+      l[v] = x.y;
+      warp_ff_sum(h[v], l[v]);
     }
+  }
 }
 
-// Sum of `nv` doubles over the cluster's ranks, read in parallel by warp 0
-// (lane r reads rank r); the result is valid in thread 0.
+// Sum over the cluster's ranks of NV exchanged float pairs, read in parallel
+// by warp 0 (lane r reads rank r); the result is valid in thread 0.
 template <int NV>
 __device__ __forceinline__ void cluster_gather(cg::cluster_group& cluster, const Xch& xch, int buf, int first,
-                                               double out[NV]) {
+                                               ff out[NV]) {
   if (threadIdx.x >= 32) return;
   const int G = (int)cluster.num_blocks();
-  double v[NV];
+  float h[NV], l[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) v[i] = 0.0;
+  for (int i = 0; i < NV; ++i) h[i] = l[i] = 0.f;
   if ((int)threadIdx.x < G) {
     const Xch* x = cluster.map_shared_rank(&xch, (int)threadIdx.x);
 #pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] = x->v[buf][first + i];
+    for (int i = 0; i < NV; ++i) {
+      const float2 y = x->v[buf][first + i];
+      h[i] = y.x;
+      l[i] = y.y;
+    }
   }
-  for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int i = 0; i < NV; ++i) out[i] = v[i];
+  for (int i = 0; i < NV; ++i) {
+    warp_ff_sum(h[i], l[i]);
+    out[i] = ff_make(h[i], l[i]);
+  }
 }
 
 __device__ __forceinline__ unsigned long long bsum_u64(unsigned long long v, unsigned long long* sh) {
@@ -241,109 +209,239 @@ __device__ __forceinline__ Pauli stage_errors(const TrajParams& P, int inst_id, 
   return p;
 }
 
-// One stage's Pauli string, drawn by one warp into slot `slot`.
-__device__ __forceinline__ void draw_stage(const TrajParams& P, int inst_id, int stage, int n, int lane, Pauli* e,
-                                           int* ne, int slot) {
-  int c = 0;
-  const Pauli p = stage_errors(P, inst_id, stage, n, lane, &c);
-  if (lane == 0) {
-    e[slot] = p;
-    ne[slot] = c;
-  }
-}
-
 // Thread 0's per-iteration scalars from W = sum of B's Z-signed O psi:
-// the mean m = i^aB s W / N, broadcast as 2 m (re, im) and s = 1/sqrt(Q).
-__device__ __forceinline__ void grover_scalars(double wr, double wi, double Q, int a, uint64_t N, float* sc) {
-  const double s = 1.0 / sqrt(Q);
-  double mr = wr, mi = wi;
-  if (a == 1) { mr = -wi; mi = wr; }
-  else if (a == 2) { mr = -wr; mi = -wi; }
-  else if (a == 3) { mr = wi; mi = -wr; }
-  const double scale = s / (double)N;
-  sc[0] = (float)(2.0 * mr * scale);
-  sc[1] = (float)(2.0 * mi * scale);
-  sc[2] = (float)s;
+// the mean m = i^aB s W / N, broadcast as 2 m (re, im) and s = 1/sqrt(Q),
+// in FP32 (the kernel's arithmetic precision; the same s scales both terms).
+__device__ __forceinline__ void grover_scalars(ff wr, ff wi, ff Q, int a, int n, float* sc) {
+  const float s = 1.f / sqrtf(Q.hi + Q.lo);
+  float mr = wr.hi + wr.lo, mi = wi.hi + wi.lo;
+  const float r0 = mr, i0 = mi;
+  if (a == 1) { mr = -i0; mi = r0; }
+  else if (a == 2) { mr = -r0; mi = -i0; }
+  else if (a == 3) { mr = i0; mi = -r0; }
+  const float scale = ldexpf(s, 1 - n);  // 2 s / N
+  sc[0] = mr * scale;
+  sc[1] = mi * scale;
+  sc[2] = s;
 }
 
-// An iteration without errors (A = B = 1): out = 2 m - s psi, except at the
-// marked index, where the oracle's sign flip gives 2 m + s psi.  Amplitudes
-// move as 16-byte pairs, four pairs in flight per thread; the sums of each
-// group of eight amplitudes are formed in plain FP32 (their rounding errors
-// are independent and average out) and added into the float-pair
-// accumulators once per group.
-__device__ __forceinline__ void clean_pass(float2* psi, uint64_t lo, uint64_t hi, uint64_t m, float t2r, float t2i,
-                                           float sf, int tid, int T, Sums& acc, float& cmr, float& cmi) {
-  float4* p4 = reinterpret_cast<float4*>(psi);
-  const uint32_t vlo = (uint32_t)(lo >> 1), vhi = (uint32_t)(hi >> 1), vm = (uint32_t)(m >> 1);
-  const float nsf = -sf;
-  const bool modd = (m & 1) != 0;
-  auto one = [&](uint32_t v, const float4& u, float& bsr, float& bsi, float& bq) -> float4 {
-    float4 o;
-    o.x = fmaf(nsf, u.x, t2r);
-    o.y = fmaf(nsf, u.y, t2i);
-    o.z = fmaf(nsf, u.z, t2r);
-    o.w = fmaf(nsf, u.w, t2i);
-    if (v == vm) {
-      if (modd) {
-        o.z = fmaf(sf, u.z, t2r);
-        o.w = fmaf(sf, u.w, t2i);
-        cmr = o.z;
-        cmi = o.w;
-      } else {
-        o.x = fmaf(sf, u.x, t2r);
-        o.y = fmaf(sf, u.y, t2i);
-        cmr = o.x;
-        cmi = o.y;
-      }
+// Runs of error-free iterations.  Without errors (A = B = 1) an iteration is
+// the unitary map
+//   psi_j -> g - psi_j (j != m),   c -> g + c,   g = 2 W / N,  W = S - 2 c,
+// one common affine map for every unmarked amplitude; the new sum is S' = W
+// and the squared norm Q is unchanged.  So such an iteration needs no pass
+// over the state: thread 0 updates (S, c) and composes the map
+//   virtual psi_j = a + b stored_j   (j != m; b = +-1; the marked one is c)
+// in double-float.  The next iteration that draws an error (or the end of the run)
+// applies the map while it reads the state, and renormalises.
+struct Track {
+  // double-float: a single thread's FP64 chain is slow on GB300, and these
+  // updates run once per iteration
+  ff S[2], c[2], a[2], Q;
+  float b;
+  bool mapped;  // the map is not the identity
+  __device__ void anchor(const ff g5[5]) {  // after a pass with reductions
+    S[0] = g5[0];
+    S[1] = g5[1];
+    Q = g5[2];
+    c[0] = g5[3];
+    c[1] = g5[4];
+    a[0] = a[1] = ff_make(0.f, 0.f);
+    b = 1.f;
+    mapped = false;
+  }
+  // k = 2/N, a power of two, so scaling by it is exact
+  __device__ void clean_step(float k) {
+    for (int i = 0; i < 2; ++i) {
+      const ff w = W(i);
+      const ff g = ff_make(k * w.hi, k * w.lo);
+      a[i] = ff_sub(g, a[i]);
+      c[i] = ff_add(g, c[i]);
+      S[i] = w;
     }
-    bsr += o.x + o.z;
-    bsi += o.y + o.w;
-    bq = fmaf(o.x, o.x, bq);
-    bq = fmaf(o.y, o.y, bq);
-    bq = fmaf(o.z, o.z, bq);
-    bq = fmaf(o.w, o.w, bq);
-    return o;
+    b = -b;
+    mapped = true;
+  }
+  // W = S - 2 c, the sum of O psi
+  __device__ ff W(int i) const { return ff_sub(S[i], ff_make(2.f * c[i].hi, 2.f * c[i].lo)); }
+  // the pending map and the marked amplitude, as floats
+  __device__ void to_args(float& ar, float& ai, float& bb, float& cr, float& ci) const {
+    ar = a[0].hi + a[0].lo;
+    ai = a[1].hi + a[1].lo;
+    bb = b;
+    cr = c[0].hi + c[0].lo;
+    ci = c[1].hi + c[1].lo;
+  }
+};
+
+// Per-thread sums of a pass: float pairs for S (re, im) and Q, fed by
+// groups of a few outputs summed in plain FP32 (their rounding errors are
+// independent and average out).
+struct Acc {
+  float sr, cr, si, ci, q, cq, gr, gi, gq;
+  __device__ void zero() { sr = cr = si = ci = q = cq = gr = gi = gq = 0.f; }
+  __device__ void add(float2 o) {
+    gr += o.x;
+    gi += o.y;
+    gq = fmaf(o.x, o.x, fmaf(o.y, o.y, gq));
+  }
+  __device__ void flush() {
+    ff_add(sr, cr, gr);
+    ff_add(si, ci, gi);
+    ff_add(q, cq, gq);
+    gr = gi = gq = 0.f;
+  }
+};
+
+// The uniform data of one pass, from shared memory.
+struct PassArgs {
+  float ar, ai, b, cr, ci;  // pending map and the virtual marked amplitude
+  float t2r, t2i, sf;       // 2 m and s of a noisy iteration
+  uint32_t m, X, ax, az, bz;
+  int aa, ba;
+};
+
+__device__ __forceinline__ float2 virt(uint32_t j, float2 u, const PassArgs& q) {
+  if (j == q.m) return make_float2(q.cr, q.ci);
+  return make_float2(fmaf(q.b, u.x, q.ar), fmaf(q.b, u.y, q.ai));
+}
+
+// out[j] of a noisy iteration from the virtual amplitude u at src = j ^ X
+__device__ __forceinline__ float2 noisy_out(uint32_t j, float2 u, const PassArgs& q) {
+  const uint32_t src = j ^ q.X;
+  float re = u.x * q.sf, im = u.y * q.sf;
+  if ((src == q.m) != (bool)(__popc(src & q.bz) & 1)) {  // oracle, B's Z part
+    re = -re;
+    im = -im;
+  }
+  ipow(q.ba, re, im);
+  re = q.t2r - re;  // D
+  im = q.t2i - im;
+  if (__popc((j ^ q.ax) & q.az) & 1) {
+    re = -re;
+    im = -im;
+  }
+  ipow(q.aa, re, im);
+  return make_float2(re, im);
+}
+
+// A pass that maps every 16-byte vector v (amplitudes 2v, 2v+1) of [lo, hi)
+// to f(v, stored vector); sums of the outputs and the output at m.  Four
+// vectors are loaded before any is stored, to keep loads in flight.
+template <class F>
+__device__ __forceinline__ void vec_pass(float4* p4, uint32_t lo, uint32_t hi, uint32_t m, int tid, int T, F f,
+                                         Acc& acc, float& cmr, float& cmi) {
+  const uint32_t vm = m >> 1, vhi = hi >> 1, uT = (uint32_t)T;
+  auto one = [&](uint32_t v, const float4& u) {
+    const float4 o = f(v, u);
+    p4[v] = o;
+    acc.add(make_float2(o.x, o.y));
+    acc.add(make_float2(o.z, o.w));
+    if (v == vm) {
+      cmr = (m & 1) ? o.z : o.x;
+      cmi = (m & 1) ? o.w : o.y;
+    }
   };
-  const uint32_t uT = (uint32_t)T;
-  uint32_t v = vlo + (uint32_t)tid;
+  uint32_t v = (lo >> 1) + (uint32_t)tid;
   for (; v + 3u * uT < vhi; v += 4u * uT) {
     const float4 u0 = p4[v], u1 = p4[v + uT], u2 = p4[v + 2u * uT], u3 = p4[v + 3u * uT];
-    float bsr = 0.f, bsi = 0.f, bq = 0.f;
-    p4[v] = one(v, u0, bsr, bsi, bq);
-    p4[v + uT] = one(v + uT, u1, bsr, bsi, bq);
-    p4[v + 2u * uT] = one(v + 2u * uT, u2, bsr, bsi, bq);
-    p4[v + 3u * uT] = one(v + 3u * uT, u3, bsr, bsi, bq);
-    ff_add(acc.sr, acc.cr, bsr);
-    ff_add(acc.si, acc.ci, bsi);
-    ff_add(acc.q, acc.cq, bq);
+    one(v, u0);
+    one(v + uT, u1);
+    one(v + 2u * uT, u2);
+    one(v + 3u * uT, u3);
+    acc.flush();
   }
   for (; v < vhi; v += uT) {
-    const float4 u0 = p4[v];
-    float bsr = 0.f, bsi = 0.f, bq = 0.f;
-    p4[v] = one(v, u0, bsr, bsi, bq);
-    ff_add(acc.sr, acc.cr, bsr);
-    ff_add(acc.si, acc.ci, bsi);
-    ff_add(acc.q, acc.cq, bq);
+    one(v, p4[v]);
+    acc.flush();
   }
 }
 
-__global__ void __launch_bounds__(512, 2) k_traj(TrajParams P) {
+// A noisy iteration whose amplitudes move between vectors (X >> 1 != 0):
+// vector pairs (v, v ^ (X >> 1)), each visited once.
+__device__ __forceinline__ void pair_pass(float4* p4, uint32_t lo, uint32_t hi, int tid, int T, const PassArgs& q,
+                                          Acc& acc, float& cmr, float& cmi) {
+  const uint32_t Xv = q.X >> 1, vm = q.m >> 1;
+  const int hb = 31 - __clz(Xv);
+  const bool sw = q.X & 1u;
+  auto two = [&](uint32_t v, uint32_t vx, const float4& u, const float4& w) {
+    const float2 a0 = virt(2 * v, make_float2(u.x, u.y), q), a1 = virt(2 * v + 1, make_float2(u.z, u.w), q);
+    const float2 b0 = virt(2 * vx, make_float2(w.x, w.y), q), b1 = virt(2 * vx + 1, make_float2(w.z, w.w), q);
+    const float2 o0 = noisy_out(2 * v, sw ? b1 : b0, q), o1 = noisy_out(2 * v + 1, sw ? b0 : b1, q);
+    const float2 o2 = noisy_out(2 * vx, sw ? a1 : a0, q), o3 = noisy_out(2 * vx + 1, sw ? a0 : a1, q);
+    p4[v] = make_float4(o0.x, o0.y, o1.x, o1.y);
+    p4[vx] = make_float4(o2.x, o2.y, o3.x, o3.y);
+    acc.add(o0);
+    acc.add(o1);
+    acc.add(o2);
+    acc.add(o3);
+    acc.flush();
+    if (v == vm) {
+      cmr = (q.m & 1) ? o1.x : o0.x;
+      cmi = (q.m & 1) ? o1.y : o0.y;
+    }
+    if (vx == vm) {
+      cmr = (q.m & 1) ? o3.x : o2.x;
+      cmi = (q.m & 1) ? o3.y : o2.y;
+    }
+  };
+  auto vec_of = [&](uint32_t p) { return ((p >> hb) << (hb + 1)) | (p & ((1u << hb) - 1u)); };
+  const uint32_t phi = hi >> 2, uT = (uint32_t)T;
+  uint32_t p = (lo >> 2) + (uint32_t)tid;
+  for (; p + uT < phi; p += 2u * uT) {  // two vector pairs in flight
+    const uint32_t v0 = vec_of(p), v1 = vec_of(p + uT);
+    const float4 u0 = p4[v0], w0 = p4[v0 ^ Xv], u1 = p4[v1], w1 = p4[v1 ^ Xv];
+    two(v0, v0 ^ Xv, u0, w0);
+    two(v1, v1 ^ Xv, u1, w1);
+  }
+  if (p < phi) {
+    const uint32_t v0 = vec_of(p);
+    two(v0, v0 ^ Xv, p4[v0], p4[v0 ^ Xv]);
+  }
+}
+
+// trunc(x^2 2^62) from the fields of a float (integer operations, exact):
+// x = mm 2^(e - 150), so x^2 2^62 = mm^2 2^(2e - 238); |x| < 2.
+__device__ __forceinline__ unsigned long long sqw(float x) {
+  const uint32_t bits = __float_as_uint(x) & 0x7fffffffu;
+  const int e = (int)(bits >> 23);
+  if (e == 0) return 0ull;  // zero or subnormal: below one unit
+  const unsigned long long mm = (bits & 0x7fffffu) | 0x800000u;
+  const unsigned long long sq = mm * mm;
+  const int sh = 2 * e - 238;
+  if (sh >= 0) return sq << (sh < 16 ? sh : 16);
+  return sh <= -64 ? 0ull : sq >> (-sh);
+}
+
+// Read-out weight of amplitude v: trunc(re^2 2^62) + trunc(im^2 2^62).
+__device__ __forceinline__ unsigned long long ro_weight(float2 v) { return sqw(v.x) + sqw(v.y); }
+
+// Iterations per table of error draws (shared memory: 12 KiB).
+#define TCH 256
+
+// MINB = resident CTAs per SM the register budget is sized for (the plan's
+// autotuner picks): 2 caps registers at 64 (some spills), 1 leaves them free.
+template <int MINB>
+__global__ void __launch_bounds__(512, MINB) k_traj(TrajParams P) {
   cg::cluster_group cluster = cg::this_cluster();
   const int G = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
   const int cid = blockIdx.x / G;
   __shared__ Xch xch;
-  __shared__ double shd[160];  // five 32-entry rows for bsum_pass
+  __shared__ float2 shf[5 * 32];  // block_ff_sum rows
   __shared__ unsigned long long shu[32];
   __shared__ Pauli pA, pB;
-  __shared__ Pauli sh_e[4];  // the four stages of the next iteration
-  __shared__ int sh_ne[4];
   __shared__ int sh_err;
-  __shared__ double wtab[QC_TRAJ_MAX_QUBITS + 1];
+  __shared__ int sh_flag;
+  __shared__ float wtab[QC_TRAJ_MAX_QUBITS + 1];
   __shared__ unsigned long long sh_target;
-  __shared__ float sh_sc[3];
+  __shared__ PassArgs sh_q;
+  // error draws of TCH iterations: X and Z masks and Y count per stage
+  __shared__ uint32_t ex[TCH][4], ez[TCH][4];
+  __shared__ int ey[TCH][4];
+  __shared__ uint32_t dirty[TCH / 32];
   float2* psi = P.slots + (uint64_t)cid * P.slot_amps;
+  float4* p4 = reinterpret_cast<float4*>(psi);
   const int tid = threadIdx.x, T = blockDim.x;
   for (;;) {
     if (rank == 0 && tid == 0) xch.inst = (int)atomicAdd(P.queue, 1u);
@@ -353,12 +451,26 @@ __global__ void __launch_bounds__(512, 2) k_traj(TrajParams P) {
     if (k >= P.n_inst) break;
     const TrajInst I = P.inst[k];
     const int n = I.n;
-    const uint64_t N = 1ull << n;
-    const uint64_t per = N / (uint64_t)G, lo = (uint64_t)rank * per, hi = lo + per;
-    const uint64_t m = I.marked;
+    const uint32_t N = 1u << n;
+    const uint32_t per = N / (uint32_t)G, lo = (uint32_t)rank * per, hi = lo + per;  // per >= 2
+    const uint32_t m = (uint32_t)I.marked;
     if (tid == 0) sh_err = 0;
     __syncthreads();
     int buf = 0;
+    // one block reduction of a pass's sums, exchanged over the cluster; the
+    // totals re-anchor thread 0's scalars
+    Track tr;
+    auto reduce_anchor = [&](Acc& acc, float cmr, float cmi) {
+      float h[5] = {acc.sr, acc.si, acc.q, cmr, cmi}, l[5] = {acc.cr, acc.ci, acc.cq, 0.f, 0.f};
+      block_ff_sum<5>(h, l, shf);
+      if (tid == 0)
+        for (int v = 0; v < 5; ++v) xch.v[buf][v] = make_float2(h[v], l[v]);
+      __threadfence();
+      cluster.sync();
+      ff g5[5];
+      cluster_gather<5>(cluster, xch, buf, 0, g5);
+      if (tid == 0) tr.anchor(g5);
+    };
     // ---- stage 0: E0 HALL |0..0> = E0 |s>: psi[j] = i^a (-1)^{|(j^x)&z|} 2^{-n/2}
     if (tid < 32) {
       int ne = 0;
@@ -371,160 +483,209 @@ __global__ void __launch_bounds__(512, 2) k_traj(TrajParams P) {
     __syncthreads();
     {
       const Pauli e0 = pA;
+      const uint32_t x0 = (uint32_t)e0.x, z0 = (uint32_t)e0.z;
+      const int a0p = e0.a;
       const float a0 = (float)(1.0 / sqrt(ldexp(1.0, n)));
-      Sums acc;
+      Acc acc;
       acc.zero();
       float cmr = 0.f, cmi = 0.f;
-      for (uint64_t j = lo + tid; j < hi; j += T) {
-        float re = (__popcll((j ^ e0.x) & e0.z) & 1) ? -a0 : a0, im = 0.f;
-        ipow(e0.a, re, im);
-        psi[j] = make_float2(re, im);
-        acc.add(re, im);
-        if (j == m) {
-          cmr = re;
-          cmi = im;
-        }
-      }
-      const float hh[3] = {acc.sr, acc.si, acc.q}, ll[3] = {acc.cr, acc.ci, acc.cq};
-      double red[5];
-      bsum_pass(hh, ll, cmr, cmi, shd, red);
-      if (tid == 0)
-        for (int v = 0; v < 5; ++v) xch.v[buf][v] = red[v];
+      auto amp = [&](uint32_t j) {
+        float re = (__popc((j ^ x0) & z0) & 1) ? -a0 : a0, im = 0.f;
+        ipow(a0p, re, im);
+        return make_float2(re, im);
+      };
+      vec_pass(p4, lo, hi, m, tid, T,
+               [&](uint32_t v, const float4&) {
+                 const float2 o0 = amp(2 * v), o1 = amp(2 * v + 1);
+                 return make_float4(o0.x, o0.y, o1.x, o1.y);
+               },
+               acc, cmr, cmi);
+      reduce_anchor(acc, cmr, cmi);
     }
-    // the error draws of iteration 0 (stages 1..4, one per warp)
-    if (I.iters > 0 && tid < 128) draw_stage(P, I.id, 1 + (tid >> 5), n, tid & 31, sh_e, sh_ne, tid >> 5);
-    __threadfence();
-    cluster.sync();
-    // the per-iteration FP64 scalars live in thread 0 only (GB300's FP64 pipe
-    // is too narrow for every thread to repeat them); the others receive the
-    // three floats they need through shared memory
-    double S[2] = {0, 0}, Q = 0, cm[2] = {0, 0};
-    {
-      double g5[5];
-      cluster_gather<5>(cluster, xch, buf, 0, g5);
-      if (tid == 0) {
-        S[0] = g5[0]; S[1] = g5[1]; Q = g5[2]; cm[0] = g5[3]; cm[1] = g5[4];
-      }
-    }
-    for (int it = 0; it < I.iters; ++it) {
-      buf ^= 1;
-      // three block barriers and one cluster barrier per iteration: the
-      // scalars below, the block reduction and the cluster exchange
-      if (tid == 0) {
-        const Pauli B = pmul(hconj(sh_e[1]), sh_e[0]), A = pmul(sh_e[3], hconj(sh_e[2]));
-        pB = B;
-        pA = A;
-        sh_err += sh_ne[0] + sh_ne[1] + sh_ne[2] + sh_ne[3];
-        // sum of O psi: S with the marked amplitude's sign flipped
-        if (!B.z) grover_scalars(S[0] - 2.0 * cm[0], S[1] - 2.0 * cm[1], Q, B.a, N, sh_sc);
+    const float two_over_n = ldexpf(1.f, 1 - n);
+    for (int base = 0; base < I.iters; base += TCH) {
+      const int cnt = min(TCH, I.iters - base);
+      // ---- the error draws of iterations base .. base+cnt-1, all at once
+      for (int i = tid; i < TCH * 4; i += T) {
+        (&ex[0][0])[i] = 0u;
+        (&ez[0][0])[i] = 0u;
+        (&ey[0][0])[i] = 0;
       }
       __syncthreads();
-      const Pauli A = pA, B = pB;
-      if (B.z) {
-        // sum of O psi, signed by Z^zB: one extra reading pass
-        Sums acc;
-        acc.zero();
-        for (uint64_t j = lo + tid; j < hi; j += T) {
-          float2 v = psi[j];
-          if (__popcll(j & B.z) & 1) { v.x = -v.x; v.y = -v.y; }
-          acc.add(v.x, v.y);
+      if (P.thr_gate) {
+        const int per_it = 4 * n, F = cnt * per_it;
+        int hits = 0;
+        for (int f = tid; f < F; f += T) {
+          const int li = f / per_it, r = f - li * per_it, sg = r / n, q = r - sg * n;
+          uint32_t x[4];
+          philox4x32_10((uint32_t)I.id, (uint32_t)(1 + 4 * (base + li) + sg), (uint32_t)q, TAG_NOISE,
+                        (uint32_t)P.seed, (uint32_t)(P.seed >> 32), x);
+          if (x[0] < P.thr_gate) {
+            const int t = (int)(((uint64_t)x[1] * 3ull) >> 32);  // 0 X, 1 Y, 2 Z
+            if (t <= 1) atomicOr(&ex[li][sg], 1u << q);
+            if (t >= 1) atomicOr(&ez[li][sg], 1u << q);
+            if (t == 1) atomicAdd(&ey[li][sg], 1);
+            ++hits;
+          }
         }
-        const double w0 = bsum_ff(acc.sr, acc.cr, shd);
-        const double w1 = bsum_ff(acc.si, acc.ci, shd);
-        if (tid == 0) {
-          xch.v[buf][5] = w0;
-          xch.v[buf][6] = w1;
-        }
-        __threadfence();
-        cluster.sync();
-        double g2[2];
-        cluster_gather<2>(cluster, xch, buf, 5, g2);
-        if (tid == 0) {
-          const double sg = (__popcll(m & B.z) & 1) ? -1.0 : 1.0;
-          grover_scalars(g2[0] - 2.0 * sg * cm[0], g2[1] - 2.0 * sg * cm[1], Q, B.a, N, sh_sc);
-        }
-        // publishes sh_sc; every CTA has read the W slots before they are reused
-        cluster.sync();
+        if (hits) atomicAdd(&sh_err, hits);
       }
-      const float t2r = sh_sc[0], t2i = sh_sc[1], sf = sh_sc[2];
-      const uint64_t X = A.x ^ B.x;
-      Sums acc;
+      __syncthreads();
+      if (tid < TCH) {
+        const bool any = (ex[tid][0] | ex[tid][1] | ex[tid][2] | ex[tid][3] | ez[tid][0] | ez[tid][1] | ez[tid][2] |
+                          ez[tid][3]) != 0u;
+        const unsigned bal = __ballot_sync(0xffffffffu, any);
+        if ((tid & 31) == 0) dirty[tid >> 5] = bal;
+      }
+      __syncthreads();
+      for (int li = 0; li < cnt; ++li) {
+        if (!((dirty[li >> 5] >> (li & 31)) & 1u)) {
+          if (tid == 0) tr.clean_step(two_over_n);  // no pass, no barrier
+          continue;
+        }
+        // ---- an iteration with errors: one pass over the state
+        buf ^= 1;
+        if (tid == 0) {
+          Pauli e[4];
+          for (int sg = 0; sg < 4; ++sg) e[sg] = Pauli{ex[li][sg], ez[li][sg], ey[li][sg] & 3};
+          const Pauli B = pmul(hconj(e[1]), e[0]), A = pmul(e[3], hconj(e[2]));
+          pB = B;
+          PassArgs q;
+          tr.to_args(q.ar, q.ai, q.b, q.cr, q.ci);
+          q.m = m;
+          q.X = (uint32_t)(A.x ^ B.x);
+          q.ax = (uint32_t)A.x;
+          q.az = (uint32_t)A.z;
+          q.bz = (uint32_t)B.z;
+          q.aa = A.a;
+          q.ba = B.a;
+          if (!B.z) {  // sum of O psi: S with the marked amplitude's sign flipped
+            float sc[3];
+            grover_scalars(tr.W(0), tr.W(1), tr.Q, B.a, n, sc);
+            q.t2r = sc[0];
+            q.t2i = sc[1];
+            q.sf = sc[2];
+          }
+          sh_q = q;
+        }
+        __syncthreads();
+        if (pB.z) {
+          // sum of O psi, signed by Z^zB: one extra reading pass
+          const PassArgs q = sh_q;
+          float hr = 0.f, lr = 0.f, hi_ = 0.f, li_ = 0.f;
+          auto signed_sum = [&](uint32_t v, const float4& u, float& sr, float& si) {
+            const float2 a0 = virt(2 * v, make_float2(u.x, u.y), q), a1 = virt(2 * v + 1, make_float2(u.z, u.w), q);
+            const bool s0 = __popc((2 * v) & q.bz) & 1, s1 = s0 != (bool)(q.bz & 1u);
+            sr += (s0 ? -a0.x : a0.x) + (s1 ? -a1.x : a1.x);
+            si += (s0 ? -a0.y : a0.y) + (s1 ? -a1.y : a1.y);
+          };
+          const uint32_t vhi = hi >> 1, uT = (uint32_t)T;
+          uint32_t v = (lo >> 1) + (uint32_t)tid;
+          for (; v + 3u * uT < vhi; v += 4u * uT) {
+            const float4 u0 = p4[v], u1 = p4[v + uT], u2 = p4[v + 2u * uT], u3 = p4[v + 3u * uT];
+            float sr = 0.f, si = 0.f;
+            signed_sum(v, u0, sr, si);
+            signed_sum(v + uT, u1, sr, si);
+            signed_sum(v + 2u * uT, u2, sr, si);
+            signed_sum(v + 3u * uT, u3, sr, si);
+            ff_add(hr, lr, sr);
+            ff_add(hi_, li_, si);
+          }
+          for (; v < vhi; v += uT) {
+            float sr = 0.f, si = 0.f;
+            signed_sum(v, p4[v], sr, si);
+            ff_add(hr, lr, sr);
+            ff_add(hi_, li_, si);
+          }
+          float h2[2] = {hr, hi_}, l2[2] = {lr, li_};
+          block_ff_sum<2>(h2, l2, shf);
+          if (tid == 0) {
+            xch.v[buf][5] = make_float2(h2[0], l2[0]);
+            xch.v[buf][6] = make_float2(h2[1], l2[1]);
+          }
+          __threadfence();
+          cluster.sync();
+          ff g2[2];
+          cluster_gather<2>(cluster, xch, buf, 5, g2);
+          if (tid == 0) {
+            // W = (signed sum of psi) - 2 sign(m) c
+            const bool neg = __popc(m & q.bz) & 1;
+            ff w[2];
+            for (int i = 0; i < 2; ++i) {
+              const ff c2 = ff_make(2.f * tr.c[i].hi, 2.f * tr.c[i].lo);
+              w[i] = neg ? ff_add(g2[i], c2) : ff_sub(g2[i], c2);
+            }
+            float sc[3];
+            grover_scalars(w[0], w[1], tr.Q, q.ba, n, sc);
+            sh_q.t2r = sc[0];
+            sh_q.t2i = sc[1];
+            sh_q.sf = sc[2];
+          }
+          // publishes sh_q; every CTA has read the W slots before they are reused
+          cluster.sync();
+        }
+        const PassArgs q = sh_q;
+        Acc acc;
+        acc.zero();
+        float cmr = 0.f, cmi = 0.f;
+        if ((q.X >> 1) == 0) {
+          const bool sw = q.X & 1u;
+          vec_pass(p4, lo, hi, m, tid, T,
+                   [&](uint32_t v, const float4& u) {
+                     const float2 a0 = virt(2 * v, make_float2(u.x, u.y), q);
+                     const float2 a1 = virt(2 * v + 1, make_float2(u.z, u.w), q);
+                     const float2 o0 = noisy_out(2 * v, sw ? a1 : a0, q), o1 = noisy_out(2 * v + 1, sw ? a0 : a1, q);
+                     return make_float4(o0.x, o0.y, o1.x, o1.y);
+                   },
+                   acc, cmr, cmi);
+        } else {
+          pair_pass(p4, lo, hi, tid, T, q, acc, cmr, cmi);
+        }
+        reduce_anchor(acc, cmr, cmi);
+      }
+      __syncthreads();  // the tables are read before the next chunk clears them
+    }
+    // ---- a pending map is applied once, with the sums of the result
+    if (tid == 0) {
+      sh_flag = tr.mapped;
+      PassArgs q;
+      tr.to_args(q.ar, q.ai, q.b, q.cr, q.ci);
+      q.m = m;
+      sh_q = q;
+    }
+    __syncthreads();
+    if (sh_flag) {
+      buf ^= 1;
+      const PassArgs q = sh_q;
+      Acc acc;
       acc.zero();
       float cmr = 0.f, cmi = 0.f;
-      if (((A.x | A.z | B.x | B.z) == 0) && ((A.a | B.a) == 0)) {
-        clean_pass(psi, lo, hi, m, t2r, t2i, sf, tid, T, acc, cmr, cmi);
-      } else {
-        // out[j] from src = j ^ X
-        auto out_of = [&](uint64_t j, float2 u) -> float2 {
-          const uint64_t src = j ^ X;
-          float re = u.x * sf, im = u.y * sf;
-          if (src == m) { re = -re; im = -im; }                 // oracle
-          if (__popcll(src & B.z) & 1) { re = -re; im = -im; }  // B's Z part
-          ipow(B.a, re, im);
-          re = t2r - re;                                        // D
-          im = t2i - im;
-          if (__popcll((j ^ A.x) & A.z) & 1) { re = -re; im = -im; }
-          ipow(A.a, re, im);
-          return make_float2(re, im);
-        };
-        if (X == 0) {
-          for (uint64_t j = lo + tid; j < hi; j += T) {
-            const float2 o = out_of(j, psi[j]);
-            psi[j] = o;
-            acc.add(o.x, o.y);
-            if (j == m) { cmr = o.x; cmi = o.y; }
-          }
-        } else {
-          const int hb = 63 - __clzll((long long)X);
-          const uint64_t plo = lo / 2, phi = hi / 2;  // pair indices owned by this CTA
-          for (uint64_t p = plo + tid; p < phi; p += T) {
-            const uint64_t j = insert0(p, hb), jx = j ^ X;
-            const float2 u = psi[j], v = psi[jx];
-            const float2 oj = out_of(j, v), ojx = out_of(jx, u);
-            psi[j] = oj;
-            psi[jx] = ojx;
-            acc.add(oj.x, oj.y);
-            acc.add(ojx.x, ojx.y);
-            if (j == m) { cmr = oj.x; cmi = oj.y; }
-            if (jx == m) { cmr = ojx.x; cmi = ojx.y; }
-          }
-        }
-      }
-      // the next iteration's error draws (thread 0 read sh_e before the
-      // barrier above), published by the reduction's barrier
-      if (it + 1 < I.iters && tid < 128) draw_stage(P, I.id, 5 + 4 * it + (tid >> 5), n, tid & 31, sh_e, sh_ne, tid >> 5);
-      {
-        const float hh[3] = {acc.sr, acc.si, acc.q}, ll[3] = {acc.cr, acc.ci, acc.cq};
-        double red[5];
-        bsum_pass(hh, ll, cmr, cmi, shd, red);
-        if (tid == 0) for (int v = 0; v < 5; ++v) xch.v[buf][v] = red[v];
-      }
-      __threadfence();
-      cluster.sync();
-      {
-        double g5[5];
-        cluster_gather<5>(cluster, xch, buf, 0, g5);
-        if (tid == 0) { S[0] = g5[0]; S[1] = g5[1]; Q = g5[2]; cm[0] = g5[3]; cm[1] = g5[4]; }
-      }
+      vec_pass(p4, lo, hi, m, tid, T,
+               [&](uint32_t v, const float4& u) {
+                 const float2 o0 = virt(2 * v, make_float2(u.x, u.y), q), o1 = virt(2 * v + 1, make_float2(u.z, u.w), q);
+                 return make_float4(o0.x, o0.y, o1.x, o1.y);
+               },
+               acc, cmr, cmi);
+      reduce_anchor(acc, cmr, cmi);
     }
     // ---- read-out: success probabilities and one seeded measurement
     buf ^= 1;
-    if (tid <= n) {
-      wtab[tid] = pow(P.p_ro, (double)tid) * pow(1.0 - P.p_ro, (double)(n - tid));
-    }
+    if (tid <= n) wtab[tid] = (float)(pow(P.p_ro, (double)tid) * pow(1.0 - P.p_ro, (double)(n - tid)));
     __syncthreads();
-    double ro = 0.0;
+    float roh = 0.f, rol = 0.f;
     unsigned long long wt = 0;
-    for (uint64_t j = lo + tid; j < hi; j += T) {
-      const float2 v = psi[j];
-      const double pj = __dadd_rn(__dmul_rn((double)v.x, (double)v.x), __dmul_rn((double)v.y, (double)v.y));
-      ro = fma(pj, wtab[__popcll(j ^ m)], ro);
-      wt += __double2ull_rz(pj * 4611686018427387904.0);
+    for (uint32_t v = (lo >> 1) + tid; v < (hi >> 1); v += T) {
+      const float4 u = p4[v];
+      const float2 v0 = make_float2(u.x, u.y), v1 = make_float2(u.z, u.w);
+      const float p0 = fmaf(v0.x, v0.x, v0.y * v0.y), p1 = fmaf(v1.x, v1.x, v1.y * v1.y);
+      ff_add(roh, rol, fmaf(p0, wtab[__popc((2 * v) ^ m)], p1 * wtab[__popc((2 * v + 1) ^ m)]));
+      wt += ro_weight(v0) + ro_weight(v1);
     }
-    const double rop = bsum(ro, shd);
+    float rh[1] = {roh}, rl[1] = {rol};
+    block_ff_sum<1>(rh, rl, shf);
     const unsigned long long wtot = bsum_u64(wt, shu);
     if (tid == 0) {
-      xch.v[buf][5] = rop;
+      xch.v[buf][5] = make_float2(rh[0], rl[0]);
       xch.w[buf] = wtot;
     }
     __threadfence();
@@ -533,7 +694,7 @@ __global__ void __launch_bounds__(512, 2) k_traj(TrajParams P) {
     unsigned long long off = 0, total = 0;
     for (int r = 0; r < G; ++r) {
       const Xch* x = cluster.map_shared_rank(&xch, r);
-      rosum += x->v[buf][5];
+      if (tid == 0) rosum += (double)x->v[buf][5].x + (double)x->v[buf][5].y;  // once per instance
       if (r < rank) off += x->w[buf];
       total += x->w[buf];
     }
@@ -543,14 +704,10 @@ __global__ void __launch_bounds__(512, 2) k_traj(TrajParams P) {
     // the CTA whose weight range holds the target finds the outcome
     if (total > 0 && target >= off && target < off + wtot) {
       // contiguous chunk per thread, block-level exclusive scan of chunk sums
-      const uint64_t chunk = (per + T - 1) / T;
-      const uint64_t c_lo = lo + (uint64_t)tid * chunk, c_hi = min(hi, c_lo + chunk);
+      const uint32_t chunk = (per + T - 1) / T;
+      const uint32_t c_lo = min(hi, lo + (uint32_t)tid * chunk), c_hi = min(hi, c_lo + chunk);
       unsigned long long mine = 0;
-      for (uint64_t j = c_lo; j < c_hi; ++j) {
-        const float2 v = psi[j];
-        const double pj = __dadd_rn(__dmul_rn((double)v.x, (double)v.x), __dmul_rn((double)v.y, (double)v.y));
-        mine += __double2ull_rz(pj * 4611686018427387904.0);
-      }
+      for (uint32_t j = c_lo; j < c_hi; ++j) mine += ro_weight(psi[j]);
       // inclusive scan over threads (simple two-level through shared memory)
       unsigned long long x = mine;
       const int lane = tid & 31, wid = tid >> 5;
@@ -566,11 +723,9 @@ __global__ void __launch_bounds__(512, 2) k_traj(TrajParams P) {
       const unsigned long long incl = off + wo + x, excl = incl - mine;
       if (target >= excl && target < incl) {
         unsigned long long run = excl;
-        uint64_t j = c_lo;
+        uint32_t j = c_lo;
         for (; j < c_hi; ++j) {
-          const float2 v = psi[j];
-          const double pj = __dadd_rn(__dmul_rn((double)v.x, (double)v.x), __dmul_rn((double)v.y, (double)v.y));
-          run += __double2ull_rz(pj * 4611686018427387904.0);
+          run += ro_weight(psi[j]);
           if (run > target) break;
         }
         sh_target = j;
@@ -593,7 +748,8 @@ __global__ void __launch_bounds__(512, 2) k_traj(TrajParams P) {
       }
     }
     if (rank == 0 && tid == 0) {
-      P.p_success[I.id] = (cm[0] * cm[0] + cm[1] * cm[1]) / Q;
+      const double c0 = ff_to_d(tr.c[0]), c1 = ff_to_d(tr.c[1]), Q = ff_to_d(tr.Q);
+      P.p_success[I.id] = (c0 * c0 + c1 * c1) / Q;
       P.p_readout[I.id] = rosum / Q;
       P.n_errors[I.id] = (uint32_t)sh_err;
     }
@@ -619,13 +775,16 @@ struct qc_traj_plan {
   int* status;
   uint64_t slot_amps;
   TrajParams params;
-  int G, T, grid;
+  int G, T, grid, minb;
   cudaGraphExec_t gexec;
   qc_traj_out last_out;
   bool have_graph;
 };
 
-static qc_status traj_launch(qc_traj_plan* p, int G, int T, int grid, const TrajParams& prm) {
+typedef void (*TrajKernel)(TrajParams);
+static TrajKernel traj_kernel(int minb) { return minb == 1 ? k_traj<1> : k_traj<2>; }
+
+static qc_status traj_launch(qc_traj_plan* p, int G, int T, int grid, int minb, const TrajParams& prm) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(T);
@@ -638,14 +797,14 @@ static qc_status traj_launch(qc_traj_plan* p, int G, int T, int grid, const Traj
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_traj, prm);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, traj_kernel(minb), prm);
   if (e != cudaSuccess) return cuda_fail(e, "trajectory launch");
   return QC_OK;
 }
 
 // Largest number of co-resident clusters for (G, T); 0 if not launchable.
-static int traj_max_clusters(int G, int T) {
-  cudaFuncSetAttribute(k_traj, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+static int traj_max_clusters(int G, int T, int minb) {
+  cudaFuncSetAttribute(traj_kernel(minb), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(G * 64);
   cfg.blockDim = dim3(T);
@@ -657,7 +816,7 @@ static int traj_max_clusters(int G, int T) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int nc = 0;
-  if (cudaOccupancyMaxActiveClusters(&nc, k_traj, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&nc, traj_kernel(minb), &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -718,13 +877,15 @@ QC_API qc_status qc_traj_plan_create(const qc_traj_desc* d, void* stream, int au
   for (int G = 1; G <= 16; G *= 2)
     if ((uint64_t)G * 2 <= (1ull << nmin) && (G >= 4 || nmax <= 14)) Gs.push_back(G);
   struct Cand {
-    int G, T, grid;
+    int G, T, grid, minb;
   };
   std::vector<Cand> cands;
   for (int G : Gs)
     for (int T : Ts) {
-      const int nc = traj_max_clusters(G, T);
-      if (nc > 0) cands.push_back({G, T, nc * G});
+      for (int minb = 1; minb <= 2; ++minb) {
+        const int nc = traj_max_clusters(G, T, minb);
+        if (nc > 0) cands.push_back({G, T, nc * G, minb});
+      }
     }
   if (cands.empty()) {
     cudaFree(p->d_inst);
@@ -798,7 +959,7 @@ QC_API qc_status qc_traj_plan_create(const qc_traj_desc* d, void* stream, int au
       for (int rep = 0; rep < 2; ++rep) {  // first run warms up, both are timed
         cudaMemsetAsync(p->queue, 0, sizeof(unsigned), p->stream);
         cudaEventRecord(e0, p->stream);
-        if (traj_launch(p, c.G, c.T, c.grid, sp)) break;
+        if (traj_launch(p, c.G, c.T, c.grid, c.minb, sp)) break;
         cudaEventRecord(e1, p->stream);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -820,6 +981,7 @@ QC_API qc_status qc_traj_plan_create(const qc_traj_desc* d, void* stream, int au
   p->G = best.G;
   p->T = best.T;
   p->grid = best.grid;
+  p->minb = best.minb;
   // later work on the caller's stream sees the uploaded descriptors
   e = cudaEventRecord(p->ev_out, p->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(p->user, p->ev_out, 0);
@@ -853,7 +1015,7 @@ QC_API qc_status qc_traj_plan_run(qc_traj_plan* p, const qc_traj_out* o) {
     cudaError_t e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "graph capture");
     cudaMemsetAsync(p->queue, 0, sizeof(unsigned) + sizeof(int), p->stream);
-    qc_status st = traj_launch(p, p->G, p->T, p->grid, prm);
+    qc_status st = traj_launch(p, p->G, p->T, p->grid, p->minb, prm);
     e = cudaStreamEndCapture(p->stream, &g);
     if (st) return st;
     if (e != cudaSuccess) return cuda_fail(e, "graph capture end");
