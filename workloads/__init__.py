@@ -143,3 +143,44 @@ def ansatz_hamiltonian(n: int) -> list[tuple[int, int, float]]:
     terms = [(0, 0b11, 1.0)]
     terms += [(1 << i, 0, 0.1) for i in range(n)]
     return terms
+
+
+@dataclass
+class MultiverseNoise:
+    """One intrusion per noisy universe (sec. 6.3 "Noise scenarios"):
+    universe 0 runs without noise; universe b >= 1 gets a Wigner rotation
+    D^{1/2}(alpha, beta, 0) on qubit qhit (kind 1) or D^{3/2}(alpha, beta, 0)
+    on the pair (qhit, qhit2) (kind 2) before iteration eloc (eloc = iters
+    puts it after the last one).  P holds the universes' weights."""
+    kind: np.ndarray    # (B,) int: 0 none, 1 one-qubit, 2 two-qubit
+    qhit: np.ndarray    # (B,) int
+    qhit2: np.ndarray   # (B,) int (kind 2 only)
+    eloc: np.ndarray    # (B,) int in [0, iters]
+    alpha: np.ndarray   # (B,) float in [0, 2 pi)
+    beta: np.ndarray    # (B,) float in [0, pi]
+    P: np.ndarray       # (B,) float, sum 1
+
+
+def multiverse_noise(B: int, n: int, iters: int, seed: int, two_qubit_every: int = 4,
+                     P: np.ndarray | None = None) -> MultiverseNoise:
+    """Seeded intrusion list: every `two_qubit_every`-th noisy universe
+    gets the two-qubit D^{3/2}, the others the one-qubit D^{1/2}; the
+    universes are equally weighted unless P is given."""
+    g = rng(seed)
+    kind = np.zeros(B, dtype=np.int32)
+    qhit = np.zeros(B, dtype=np.int32)
+    qhit2 = np.zeros(B, dtype=np.int32)
+    eloc = np.zeros(B, dtype=np.int32)
+    alpha = np.zeros(B)
+    beta = np.zeros(B)
+    for b in range(1, B):
+        kind[b] = 2 if (two_qubit_every and n >= 2 and b % two_qubit_every == 0) else 1
+        qhit[b] = int(g.integers(0, n))
+        if kind[b] == 2:
+            q2 = int(g.integers(0, n - 1))
+            qhit2[b] = q2 + (q2 >= qhit[b])
+        eloc[b] = int(g.integers(0, iters + 1))
+        alpha[b] = g.random() * 2.0 * math.pi
+        beta[b] = g.random() * math.pi
+    w = np.full(B, 1.0 / B) if P is None else np.asarray(P, dtype=float)
+    return MultiverseNoise(kind=kind, qhit=qhit, qhit2=qhit2, eloc=eloc, alpha=alpha, beta=beta, P=w)
