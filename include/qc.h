@@ -361,6 +361,44 @@ qc_status qc_adjoint_grad(int n, qc_dtype dt, int B, const qc_gate* gates, int n
                           void* psi_dev, void* lam_dev, double* energy_dev, double* grad_dev,
                           void* stream);
 
+/* -------------------------------- noise intrusions and density matrix -- */
+/* The paper's noise scenario and ensemble average (sec. 6.1-6.3): a batch of
+ * B states ("multiverses", each run with its own unitary intrusions) stored
+ * one after another, state a at amplitudes [a 2^n, (a+1) 2^n) of psi_dev
+ * (device, dtype dt), with weights P_host[a] >= 0 (host). */
+#define QC_DM_MAX_QUBITS 15
+#define QC_SPECTRUM_MAX_UNIVERSES 64
+
+/* Wigner rotation D^j(alpha, beta, gamma) for j = twoj/2 in {1/2, 3/2}
+ * (the paper's D2 and D4 noise operators; it takes gamma = 0):
+ *   D_{m'm} = e^{-i m' alpha} d^j_{m'm}(beta) e^{-i m gamma},
+ * rows and columns ordered m = j, j-1, .., -j, written row-major as
+ * interleaved (re, im) doubles to D_out (host; 8 doubles for j = 1/2, 32
+ * for j = 3/2), ready for qc_apply_1q / qc_apply_2q (m = +1/2 is qubit
+ * value 0; the j = 3/2 states m = 3/2 .. -3/2 take the quartet positions
+ * 0 .. 3).  Host arithmetic only.  QC_EINVAL for other j or non-finite
+ * angles. */
+qc_status qc_wigner_d(int twoj, double alpha, double beta, double gamma, double* D_out);
+
+/* The ensemble density matrix (sec. 6.1):
+ *   rho[n][n'] = sum_a P_a C_a(n) C_a(n')^*,
+ * written row-major to rho_dev (device, 4^n amplitudes of dtype dt, owned by
+ * the caller).  1 <= n <= QC_DM_MAX_QUBITS, B >= 1.  Stream-ordered; the
+ * inner products run in double-float. */
+qc_status qc_density_matrix(const void* psi_dev, int n, qc_dtype dt, int B, const double* P_host,
+                            void* rho_dev, void* stream);
+
+/* Eigenvalues of the same rho without forming it: its nonzero eigenvalues
+ * are those of the B x B Gram matrix G_ab = sqrt(P_a P_b) <psi_a|psi_b>
+ * (one streaming pass over the batch), diagonalised by a one-CTA Jacobi
+ * solver in FP64.  evals_host (B doubles) receives them in descending
+ * order (the other 2^n - B eigenvalues of rho are zero); stats_host[0..2] =
+ * Tr rho, Tr rho^2 and the entropy -sum l ln l over l > 1e-14 (natural
+ * logarithm).  1 <= B <= QC_SPECTRUM_MAX_UNIVERSES, 1 <= n <= 34.
+ * Synchronises the stream.  QC_ECUDA if the solver does not converge. */
+qc_status qc_mixed_spectrum(const void* psi_dev, int n, qc_dtype dt, int B, const double* P_host,
+                            double* evals_host, double* stats_host, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -99,6 +99,9 @@ _SIGS = {
     "qc_circuit_forward": [_I, _I, _I, ctypes.POINTER(Gate), _I, _VP, _I64, _VP, _VP],
     "qc_adjoint_grad": [_I, _I, _I, ctypes.POINTER(Gate), _I, _VP, _I64, _I,
                         ctypes.POINTER(PauliTerm), _I, _VP, _VP, _VP, _VP, _VP],
+    "qc_wigner_d": [_I, ctypes.c_double, ctypes.c_double, ctypes.c_double, _DP],
+    "qc_density_matrix": [_VP, _I, _I, _I, _DP, _VP, _VP],
+    "qc_mixed_spectrum": [_VP, _I, _I, _I, _DP, _DP, _DP, _VP],
 }
 
 _lib = None
@@ -264,6 +267,37 @@ def qc_project(h, lo: int, width: int, value: int) -> float:
 
 def qc_qft_range(h, lo: int, width: int):
     _check(lib().qc_qft_range(h, lo, width))
+
+
+def qc_wigner_d(twoj: int, alpha: float, beta: float, gamma: float = 0.0) -> np.ndarray:
+    """D^{twoj/2}(alpha, beta, gamma) as a complex (twoj+1) x (twoj+1) matrix."""
+    dim = twoj + 1
+    out = np.zeros(2 * dim * dim)
+    _check(lib().qc_wigner_d(twoj, alpha, beta, gamma, _dptr(out)))
+    return (out[0::2] + 1j * out[1::2]).reshape(dim, dim)
+
+
+def _weights(P, B):
+    w = np.ascontiguousarray(P, dtype=np.float64)
+    if w.size != B:
+        raise ValueError("need one weight per state")
+    return w
+
+
+def qc_density_matrix(psi_ptr: int, n: int, dt: int, B: int, P, rho_ptr: int, stream: int = 0):
+    w = _weights(P, B)
+    _check(lib().qc_density_matrix(ctypes.c_void_p(psi_ptr), n, dt, B, _dptr(w), ctypes.c_void_p(rho_ptr),
+                                   ctypes.c_void_p(stream)))
+
+
+def qc_mixed_spectrum(psi_ptr: int, n: int, dt: int, B: int, P, stream: int = 0):
+    """(eigenvalues descending, (trace, purity, entropy))."""
+    w = _weights(P, B)
+    ev = np.zeros(B)
+    st = np.zeros(3)
+    _check(lib().qc_mixed_spectrum(ctypes.c_void_p(psi_ptr), n, dt, B, _dptr(w), _dptr(ev), _dptr(st),
+                                   ctypes.c_void_p(stream)))
+    return ev, tuple(st)
 
 
 def qc_norm(h) -> float:

@@ -35,3 +35,16 @@ def test_library_exports_every_declared_symbol():
 def test_binding_loads_without_gpu():
     import paper_0902_0699_gb300 as qc
     assert "sm_103a" in qc.version()
+
+
+def test_wigner_operators_host_logic():
+    # qc_wigner_d is host arithmetic in the library (no device call): its
+    # closed forms for j = 1/2 and 3/2 against the oracle's sum formula
+    import numpy as np
+    import oracle.density as D
+    import paper_0902_0699_gb300 as qc
+    for twoj in (1, 3):
+        for (a, b, g) in [(0.3, 1.2, 0.0), (5.1, 2.9, 0.7), (0.0, 0.0, 0.0), (1.0, np.pi, -2.0)]:
+            U = qc.qc_wigner_d(twoj, a, b, g)
+            assert np.max(np.abs(U - D.wigner_D(twoj, a, b, g))) <= 1e-15
+            assert np.max(np.abs(U @ U.conj().T - np.eye(twoj + 1))) <= 1e-15
