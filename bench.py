@@ -583,6 +583,62 @@ def extra_c5():
     return res
 
 
+def extra_f3(n=14, B=64):
+    """The paper's multiverse noise and density matrix (sec. 6.1-6.3): B
+    Grover runs of n qubits, each noisy universe with one Wigner intrusion
+    (D^{1/2} or D^{3/2}) at a random stage, then rho explicitly and its
+    spectrum through the Gram matrix (complex128)."""
+    import numpy as np
+    import torch
+    import paper_0902_0699_gb300 as qc
+    import workloads as W
+    k = W.grover_iterations(n)
+    m = int(W.marked_indices(W.rng(140), n, 1)[0])
+    mv = W.multiverse_noise(B, n, k, seed=14)
+    t = torch.empty((B, 1 << n), dtype=torch.complex128, device="cuda")
+    ops = {b: {} for b in range(B)}
+    for b in range(B):
+        if mv.kind[b]:
+            twoj = 1 if mv.kind[b] == 1 else 3
+            ops[b] = qc.qc_wigner_d(twoj, mv.alpha[b], mv.beta[b], 0.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for b in range(B):
+        s = qc.State(n, qc.QC_C128, tensor=t[b])
+        s.uniform()
+        for it in range(k + 1):
+            if mv.kind[b] and it == mv.eloc[b]:
+                if mv.kind[b] == 1:
+                    s.apply_1q(int(mv.qhit[b]), ops[b])
+                else:
+                    qc.qc_apply_2q(s.h, int(mv.qhit[b]), int(mv.qhit2[b]), ops[b])
+            if it < k:
+                s.grover_step([m])
+        s.close()
+    torch.cuda.synchronize()
+    t_runs = time.perf_counter() - t0
+    N = 1 << n
+    rho = torch.empty(N * N, dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    qc.qc_density_matrix(t.data_ptr(), n, qc.QC_C128, B, mv.P, rho.data_ptr(), stream)
+    a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    qc.qc_density_matrix(t.data_ptr(), n, qc.QC_C128, B, mv.P, rho.data_ptr(), stream)
+    b_.record()
+    torch.cuda.synchronize()
+    t_rho = a.elapsed_time(b_)
+    p_m = float(rho[m * N + m].real.item())
+    qc.qc_mixed_spectrum(t.data_ptr(), n, qc.QC_C128, B, mv.P)
+    t0 = time.perf_counter()
+    ev, (tr, pur, ent) = qc.qc_mixed_spectrum(t.data_ptr(), n, qc.QC_C128, B, mv.P)
+    t_spec = time.perf_counter() - t0
+    del rho
+    return {"qubits": n, "universes": B, "grover_iterations": k, "runs_ms": t_runs * 1e3,
+            "rho_ms (complex128, 4^n entries)": t_rho, "rho_GB/s_written": N * N * 16 / (t_rho * 1e6),
+            "spectrum_ms (Gram + Jacobi, synchronous)": t_spec * 1e3, "trace": tr, "purity": pur,
+            "entropy": ent, "p_success_rho_mm": p_m, "largest_eigenvalue": float(ev[0])}
+
+
 # ------------------------------------------------------------ CPU oracle ----
 
 def cpu_oracle_sample(n=22, iters=2):
@@ -654,7 +710,7 @@ def main():
     if args.only:
         fn = {"c64": extra_c64, "c1": extra_c1, "c2": extra_c2, "c4": extra_c4, "c5": extra_c5,
               # a small trajectory batch (96 instances, 16..18 qubits) for profiling
-              "c4s": lambda: extra_c4(96, 16, 18, seed=7, autotune=0)}[args.only]
+              "c4s": lambda: extra_c4(96, 16, 18, seed=7, autotune=0), "f3": extra_f3}[args.only]
         print(json.dumps({args.only: fn()}), flush=True)
         return 0
     out, st, step_fn, ops, N = run_ours(args, ws, rank, local)
@@ -673,7 +729,8 @@ def main():
     if rank == 0 and not args.no_extras:
         extras = {}
         for name, fn in (("c64_n32", extra_c64), ("grover_n10", extra_c1), ("random_n24", extra_c2),
-                         ("trajectories_4096", extra_c4), ("adjoint_n20", extra_c5)):
+                         ("trajectories_4096", extra_c4), ("adjoint_n20", extra_c5),
+                         ("multiverse_density_n14", extra_f3)):
             try:
                 extras[name] = fn()
             except Exception as e:
