@@ -120,6 +120,32 @@ def apply_2q(psi, n, t1, t2, V):
     return psi
 
 
+def dense_offsets(qubits) -> np.ndarray:
+    """offs[l] = sum_b bit b of l placed at qubit qubits[b] (qubits[0] is
+    the least significant bit of the local index l)."""
+    k = len(qubits)
+    offs = np.zeros(1 << k, dtype=np.int64)
+    for l in range(1 << k):
+        for b, q in enumerate(qubits):
+            if (l >> b) & 1:
+                offs[l] |= 1 << q
+    return offs
+
+
+def apply_dense(psi, n, qubits, U):
+    """A dense 2^k x 2^k operator on k qubits (the paper's OneOpA and TwoOpA,
+    sec. 3-4, extended to k qubits): for every assignment g of the other
+    n - k qubits, the 2^k amplitudes C[g | offs[l]] are replaced by
+    sum_l' U[l][l'] C[g | offs[l']]."""
+    U = np.asarray(U, dtype=complex)
+    offs = dense_offsets(qubits)
+    mask = int(offs[-1])
+    base = np.array([i for i in range(1 << n) if i & mask == 0], dtype=np.int64)
+    idx = base[:, None] + offs[None, :]
+    psi[idx] = psi[idx] @ U.T
+    return psi
+
+
 def apply_ctrl(psi, n, c, t, U):
     lib().or_apply_ctrl(_state_ptr(psi), n, c, t, _d(_mat(U)))
     return psi
