@@ -170,6 +170,17 @@ qc_status qc_qft(qc_state* s);
  * runs in double-float arithmetic. */
 qc_status qc_apply_2q(qc_state* s, int t1, int t2, const double V[32]);
 
+/* Dense k-qubit block: OneOpA / TwoOpA (Eqs. resmat1, resmat2) extended to
+ * a 2^k x 2^k operator U on k distinct qubits, 1 <= k <= 6.  Local index l
+ * has bit b on qubit qubits[b] (host array); for every assignment g of the
+ * other qubits, C[g|offs(l)] <- sum_l' U[l][l'] C[g|offs(l')].  U: host,
+ * 2 * 4^k doubles, row-major, (re, im) interleaved.  k = 2 with qubits
+ * {t2, t1} is qc_apply_2q(t1, t2).  complex64 with k = 5 runs on the
+ * tensor cores (TF32 operands split hi + lo, FP32 accumulation; synchronises
+ * the stream to read a status word, QC_ETIMEOUT if a device wait gave up);
+ * other cases on CUDA cores (complex128 in double-float). */
+qc_status qc_apply_dense(qc_state* s, int k, const int* qubits, const double* U);
+
 /* Shor's state of Eq. Shor2 (sec. 5.2): with register 1 the high
  * n1 = n - n2 qubits and register 2 the low n2 qubits,
  *   psi = 2^{-n1/2} sum_{j < 2^n1} |j>_1 |x^j mod M>_2,

@@ -100,6 +100,7 @@ _SIGS = {
     "qc_adjoint_grad": [_I, _I, _I, ctypes.POINTER(Gate), _I, _VP, _I64, _I,
                         ctypes.POINTER(PauliTerm), _I, _VP, _VP, _VP, _VP, _VP],
     "qc_wigner_d": [_I, ctypes.c_double, ctypes.c_double, ctypes.c_double, _DP],
+    "qc_apply_dense": [_VP, _I, ctypes.POINTER(_I), _DP],
     "qc_density_matrix": [_VP, _I, _I, _I, _DP, _VP, _VP],
     "qc_mixed_spectrum": [_VP, _I, _I, _I, _DP, _DP, _DP, _VP],
 }
@@ -253,6 +254,18 @@ def qc_apply_2q(h, t1: int, t2: int, V):
     if a.size != 32:
         raise ValueError("a 4x4 operator needs 32 doubles")
     _check(lib().qc_apply_2q(h, t1, t2, _dptr(a)))
+
+
+def qc_apply_dense(h, qubits, U):
+    """A dense 2^k x 2^k operator on k qubits (local bit b on qubits[b])."""
+    q = np.ascontiguousarray(qubits, dtype=np.int32)
+    U = np.asarray(U)
+    if U.dtype.kind == "c":
+        U = np.stack([U.real, U.imag], axis=-1)
+    a = np.ascontiguousarray(U, dtype=np.float64).reshape(-1)
+    if a.size != 2 * (1 << (2 * q.size)):
+        raise ValueError("a 2^k x 2^k operator needs 2 * 4^k doubles")
+    _check(lib().qc_apply_dense(h, int(q.size), q.ctypes.data_as(ctypes.POINTER(_I)), _dptr(a)))
 
 
 def qc_shor_prepare(h, n2: int, x: int, M: int):

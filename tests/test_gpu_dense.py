@@ -1,0 +1,81 @@
+"""GPU parity of the dense k-qubit block against the oracle, through the C
+ABI: the CUDA-core kernel for k = 1..6 (both dtypes), the tensor-core
+kernel (complex64, k = 5) on contiguous and scattered qubits, full and
+partial 128-group tiles, and agreement with TwoOpA."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qc():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_0902_0699_gb300 as q
+    q.lib()
+    return q
+
+
+def unitary(g, d):
+    A = g.standard_normal((d, d)) + 1j * g.standard_normal((d, d))
+    Q, _ = np.linalg.qr(A)
+    return Q
+
+
+def run(qc, n, dt, qubits, U, seed):
+    s = qc.State(n, dt)
+    v = W.random_state(W.rng(seed), n)
+    s.load(v)
+    x = v.astype(np.complex64).astype(np.complex128) if dt == 1 else v.copy()
+    qc.qc_apply_dense(s.h, qubits, U)
+    got = s.numpy()
+    ref = O.apply_dense(x, n, list(qubits), U)
+    return np.max(np.abs(got - ref))
+
+
+@pytest.mark.parametrize("n,qubits", [(12, [0, 1, 2, 3, 4]), (14, [0, 1, 2, 3, 4]), (13, [7, 2, 11, 0, 5]),
+                                      (9, [4, 0, 8, 2, 6]), (5, [0, 1, 2, 3, 4]), (16, [15, 3, 9, 1, 12])])
+def test_tensor_core_block_c64(qc, n, qubits):
+    U = unitary(W.rng(n + sum(qubits)), 32)
+    assert run(qc, n, 1, qubits, U, seed=n) <= 1e-5
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
+def test_cuda_core_block(qc, dt, k):
+    if dt == 1 and k == 5:
+        pytest.skip("complex64 k = 5 runs on the tensor cores (tested above)")
+    n = 11
+    g = W.rng(100 + k)
+    qubits = [int(x) for x in g.permutation(n)[:k]]
+    U = unitary(g, 1 << k)
+    tol = 1e-12 if dt == 0 else 1e-5
+    assert run(qc, n, dt, qubits, U, seed=k) <= tol
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_k2_equals_twoopa(qc, dt):
+    n = 8
+    V = unitary(W.rng(5), 4)
+    a = qc.State(n, dt)
+    b = qc.State(n, dt)
+    v = W.random_state(W.rng(6), n)
+    a.load(v)
+    b.load(v)
+    qc.qc_apply_dense(a.h, [1, 6], V)
+    qc.qc_apply_2q(b.h, 6, 1, V)
+    assert np.max(np.abs(a.numpy() - b.numpy())) <= (1e-13 if dt == 0 else 2e-6)
+
+
+def test_dense_invalid(qc):
+    s = qc.State(6, 0)
+    with pytest.raises(qc.QCError):
+        qc.qc_apply_dense(s.h, [1, 1], np.eye(4, dtype=complex))
+    with pytest.raises(qc.QCError):
+        qc.qc_apply_dense(s.h, [6], np.eye(2, dtype=complex))
+    with pytest.raises(qc.QCError):
+        qc.qc_apply_dense(s.h, [0, 1, 2, 3, 4, 5, 0], np.eye(128, dtype=complex))  # k = 7 > 6
