@@ -146,6 +146,18 @@ def apply_dense(psi, n, qubits, U):
     return psi
 
 
+def hamiltonian_step(psi, n, dt, terms):
+    """One first-order step of Hamiltonian evolution (sec. 7, hbar = 1):
+    psi <- [1 - i dt (H1 + H2)] psi, with H a sum of one- and two-body terms
+    (qubits, h): h is the 2x2 or 4x4 Hermitian matrix on those qubits
+    (local bit b on qubits[b]).  Each term's action h psi is taken on the
+    state before the step."""
+    src = psi.copy()
+    for qubits, h in terms:
+        psi += -1j * dt * apply_dense(src.copy(), n, list(qubits), h)
+    return psi
+
+
 def apply_ctrl(psi, n, c, t, U):
     lib().or_apply_ctrl(_state_ptr(psi), n, c, t, _d(_mat(U)))
     return psi
