@@ -181,6 +181,23 @@ qc_status qc_apply_2q(qc_state* s, int t1, int t2, const double V[32]);
  * other cases on CUDA cores (complex128 in double-float). */
 qc_status qc_apply_dense(qc_state* s, int k, const int* qubits, const double* U);
 
+/* One term of a Hamiltonian: a one- (k = 1) or two-body (k = 2) operator h
+ * on qubits[0..k-1] (local bit b on qubits[b], as for qc_apply_dense),
+ * row-major 2^k x 2^k, (re, im) interleaved (the first 2 * 4^k doubles of
+ * h are used). */
+typedef struct {
+  int32_t k;
+  int32_t qubits[2];
+  double h[32];
+} qc_hterm;
+
+/* One first-order step of Hamiltonian evolution (sec. 7, hbar = 1):
+ *   psi <- [1 - i dt (H1 + H2)] psi,  H = sum of the n_terms terms,
+ * each term acting on the state as it was before the step (a temporary
+ * device snapshot of 2^n amplitudes).  h is expected Hermitian; the step is
+ * computed as written for any h.  One accumulating pass per term. */
+qc_status qc_hamiltonian_step(qc_state* s, double dt, const qc_hterm* terms, int n_terms);
+
 /* Shor's state of Eq. Shor2 (sec. 5.2): with register 1 the high
  * n1 = n - n2 qubits and register 2 the low n2 qubits,
  *   psi = 2^{-n1/2} sum_{j < 2^n1} |j>_1 |x^j mod M>_2,

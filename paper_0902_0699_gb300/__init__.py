@@ -101,6 +101,7 @@ _SIGS = {
                         ctypes.POINTER(PauliTerm), _I, _VP, _VP, _VP, _VP, _VP],
     "qc_wigner_d": [_I, ctypes.c_double, ctypes.c_double, ctypes.c_double, _DP],
     "qc_apply_dense": [_VP, _I, ctypes.POINTER(_I), _DP],
+    "qc_hamiltonian_step": [_VP, ctypes.c_double, _VP, _I],
     "qc_density_matrix": [_VP, _I, _I, _I, _DP, _VP, _VP],
     "qc_mixed_spectrum": [_VP, _I, _I, _I, _DP, _DP, _DP, _VP],
 }
@@ -266,6 +267,24 @@ def qc_apply_dense(h, qubits, U):
     if a.size != 2 * (1 << (2 * q.size)):
         raise ValueError("a 2^k x 2^k operator needs 2 * 4^k doubles")
     _check(lib().qc_apply_dense(h, int(q.size), q.ctypes.data_as(ctypes.POINTER(_I)), _dptr(a)))
+
+
+class HTerm(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("qubits", ctypes.c_int32 * 2), ("h", ctypes.c_double * 32)]
+
+
+def qc_hamiltonian_step(h, dt: float, terms):
+    """psi <- [1 - i dt sum h_t] psi; terms: list of (qubits, 2x2 or 4x4 matrix)."""
+    arr = (HTerm * max(1, len(terms)))()
+    for i, (qs, m) in enumerate(terms):
+        m = np.asarray(m, dtype=complex)
+        arr[i].k = len(qs)
+        for b, q in enumerate(qs):
+            arr[i].qubits[b] = int(q)
+        flat = np.stack([m.real, m.imag], axis=-1).reshape(-1)
+        for e, x in enumerate(flat):
+            arr[i].h[e] = float(x)
+    _check(lib().qc_hamiltonian_step(h, dt, ctypes.cast(arr, ctypes.c_void_p), len(terms)))
 
 
 def qc_shor_prepare(h, n2: int, x: int, M: int):

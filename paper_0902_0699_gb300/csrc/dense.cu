@@ -459,3 +459,107 @@ QC_API qc_status qc_apply_dense(qc_state* s, int k, const int* qubits, const dou
   s->sum_valid = false;
   return st;
 }
+
+// ------------------------------------------------- Hamiltonian step ------
+// psi <- [1 - i dt (H1 + H2)] psi (sec. 7; hbar = 1): every one- or
+// two-body term adds (-i dt h) applied to a snapshot of the state taken
+// before the step -- one accumulating pass per term, the paper's repeated
+// OneOpA / TwoOpA.
+namespace qc {
+
+struct HMat {
+  double v[32];  // -i dt h, row-major dim x dim, (re, im)
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_hterm(typename DenseT<R>::V* __restrict__ dst,
+                                               const typename DenseT<R>::V* __restrict__ src, uint64_t ngroups,
+                                               DenseMap M, HMat A) {
+  typedef DenseT<R> D;
+  typedef typename D::S S;
+  const int dim = 1 << M.k;  // 2 or 4
+  S a[16];
+  for (int e = 0; e < dim * dim; ++e) a[e] = D::from_d(A.v[2 * e], A.v[2 * e + 1]);
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += G) {
+    const uint64_t base = group_base(g, M);
+    S x[4];
+    for (int l = 0; l < dim; ++l) x[l] = D::load(src, base | M.offs[l]);
+    for (int l = 0; l < dim; ++l) {
+      S acc = D::load(dst, base | M.offs[l]);
+      for (int lp = 0; lp < dim; ++lp) D::mac(acc, a[l * dim + lp], x[lp]);
+      D::store(dst, base | M.offs[l], acc);
+    }
+  }
+}
+
+}  // namespace qc
+
+QC_API qc_status qc_hamiltonian_step(qc_state* s, double dt, const qc_hterm* terms, int n_terms) {
+  clear_error();
+  qc_status st = check_state(s);
+  if (st) return st;
+  if (n_terms < 0 || (n_terms > 0 && !terms) || !std::isfinite(dt)) {
+    set_error("qc_hamiltonian_step: bad term list or dt");
+    return QC_EINVAL;
+  }
+  std::vector<DenseMap> maps(n_terms);
+  std::vector<HMat> mats(n_terms);
+  for (int t = 0; t < n_terms; ++t) {
+    const qc_hterm& T = terms[t];
+    if ((T.k != 1 && T.k != 2) || T.k > s->n) {
+      set_error("qc_hamiltonian_step: term %d has k = %d (1 or 2 qubits)", t, T.k);
+      return QC_EINVAL;
+    }
+    DenseMap& M = maps[t];
+    M = DenseMap{};
+    M.k = T.k;
+    for (int b = 0; b < T.k; ++b) {
+      if (T.qubits[b] < 0 || T.qubits[b] >= s->n || (b == 1 && T.qubits[1] == T.qubits[0])) {
+        set_error("qc_hamiltonian_step: term %d qubit %d out of range or repeated", t, T.qubits[b]);
+        return QC_EINVAL;
+      }
+      M.pos[b] = T.qubits[b];
+    }
+    std::sort(M.pos, M.pos + T.k);
+    const int dim = 1 << T.k;
+    for (int l = 0; l < dim; ++l) {
+      uint64_t o = 0;
+      for (int b = 0; b < T.k; ++b)
+        if ((l >> b) & 1) o |= 1ull << T.qubits[b];
+      M.offs[l] = o;
+    }
+    for (int e = 0; e < dim * dim; ++e) {
+      const double hr = T.h[2 * e], hi = T.h[2 * e + 1];
+      if (!std::isfinite(hr) || !std::isfinite(hi)) {
+        set_error("qc_hamiltonian_step: term %d has a non-finite entry", t);
+        return QC_EINVAL;
+      }
+      mats[t].v[2 * e] = dt * hi;       // (-i dt)(hr + i hi) = dt hi - i dt hr
+      mats[t].v[2 * e + 1] = -dt * hr;
+    }
+  }
+  if (n_terms == 0) return QC_OK;
+  const uint64_t N = 1ull << s->n;
+  const size_t bytes = (s->dt == QC_C128 ? 16 : 8) * (size_t)N;
+  void* snap = nullptr;
+  cudaError_t e = cudaMallocAsync(&snap, bytes, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(snap, s->data, bytes, cudaMemcpyDeviceToDevice, s->stream);
+  if (e != cudaSuccess) {
+    if (snap) cudaFreeAsync(snap, s->stream);
+    return cuda_fail(e, "Hamiltonian step snapshot");
+  }
+  for (int t = 0; t < n_terms; ++t) {
+    const uint64_t ng = N >> maps[t].k;
+    if (s->dt == QC_C128)
+      k_hterm<double><<<resident_grid(k_hterm<double>, 256, (int64_t)ng, 256), 256, 0, s->stream>>>(
+          reinterpret_cast<double2*>(s->data), reinterpret_cast<const double2*>(snap), ng, maps[t], mats[t]);
+    else
+      k_hterm<float><<<resident_grid(k_hterm<float>, 256, (int64_t)ng, 256), 256, 0, s->stream>>>(
+          reinterpret_cast<float2*>(s->data), reinterpret_cast<const float2*>(snap), ng, maps[t], mats[t]);
+  }
+  st = check_launch("Hamiltonian step", n_terms);
+  cudaFreeAsync(snap, s->stream);
+  s->sum_valid = false;
+  return st;
+}
