@@ -639,6 +639,47 @@ def extra_f3(n=14, B=64):
             "entropy": ent, "p_success_rho_mm": p_m, "largest_eigenvalue": float(ev[0])}
 
 
+def extra_dense(n=30, reps=5):
+    """The dense k-qubit block on the tensor cores: a random 32 x 32 unitary
+    on 5 qubits of an n-qubit complex64 state (tcgen05, 3xTF32), on the
+    lowest five qubits and on five scattered ones.  Bound: HBM (2S per
+    launch); the tensor work is 3 x 256 flops per amplitude."""
+    import json as _json
+    import numpy as np
+    import torch
+    import paper_0902_0699_gb300 as qc
+    g = np.random.default_rng(5)
+    A = g.standard_normal((32, 32)) + 1j * g.standard_normal((32, 32))
+    U, _ = np.linalg.qr(A)
+    peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    tf32 = peaks.get("bf16_tflops", 1900.0) * 1.1 / 2.25  # nominal TF32 / bf16 ratio
+    res = {}
+    s = qc.State(n, qc.QC_C64)
+    s.uniform()
+    for name, qs in (("qubits_0_4", [0, 1, 2, 3, 4]), ("qubits_5_9", [5, 6, 7, 8, 9]),
+                     ("scattered", [n - 5, 3, n - 13, 9, n - 1])):
+        qc.qc_apply_dense(s.h, qs, U)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            qc.qc_apply_dense(s.h, qs, U)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        S = (1 << n) * 8
+        gbs = 2 * S / ms / 1e6
+        tflops = 3 * 256 * (1 << n) / ms / 1e9
+        res[name] = {"qubits": qs, "ms": ms, "GB/s": gbs, "frac_of_measured_hbm": gbs / hbm,
+                     "tensor_TFLOP/s (3xTF32 executed)": tflops, "frac_of_tf32_peak": tflops / tf32}
+    s.close()
+    res["note"] = ("per launch: %d-qubit complex64, one tile of 128 groups per MMA round (tcgen05 kind::tf32, "
+                   "M128 N64 K64 x 3 terms); tf32 peak = measured bf16 x 1.1/2.25 = %.0f TFLOP/s" % (n, tf32))
+    return res
+
+
 # ------------------------------------------------------------ CPU oracle ----
 
 def cpu_oracle_sample(n=22, iters=2):
@@ -710,7 +751,8 @@ def main():
     if args.only:
         fn = {"c64": extra_c64, "c1": extra_c1, "c2": extra_c2, "c4": extra_c4, "c5": extra_c5,
               # a small trajectory batch (96 instances, 16..18 qubits) for profiling
-              "c4s": lambda: extra_c4(96, 16, 18, seed=7, autotune=0), "f3": extra_f3}[args.only]
+              "c4s": lambda: extra_c4(96, 16, 18, seed=7, autotune=0), "f3": extra_f3,
+              "dense": extra_dense, "dense26": lambda: extra_dense(26, 2)}[args.only]
         print(json.dumps({args.only: fn()}), flush=True)
         return 0
     out, st, step_fn, ops, N = run_ours(args, ws, rank, local)
@@ -730,7 +772,7 @@ def main():
         extras = {}
         for name, fn in (("c64_n32", extra_c64), ("grover_n10", extra_c1), ("random_n24", extra_c2),
                          ("trajectories_4096", extra_c4), ("adjoint_n20", extra_c5),
-                         ("multiverse_density_n14", extra_f3)):
+                         ("multiverse_density_n14", extra_f3), ("dense_block_k5_n30_c64", extra_dense)):
             try:
                 extras[name] = fn()
             except Exception as e:
