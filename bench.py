@@ -198,29 +198,30 @@ def run_ours(args, ws, rank, local):
     H = np.array([[1, 1], [1, -1]], dtype=np.complex128) / math.sqrt(2.0)
     ops_per_step = 1 + iters + 1 + 3 * n
 
-    def step(ev: Events | None, sweep_ev=None):
+    def step(ev: Events | None, sweep_ev=None, state=None):
+        st_ = state if state is not None else st
         if ev: ev.mark("start")
-        st.uniform()
+        st_.uniform()
         if ev: ev.mark("hall_uniform")
         for _ in range(iters):
-            st.grover_step(marked)
+            st_.grover_step(marked)
         if ev: ev.mark("grover")
-        st.qft()
+        st_.qft()
         if ev: ev.mark("qft")
-        st.probs()
-        shots = st.sample(12345, 1000)
+        st_.probs()
+        shots = st_.sample(12345, 1000)
         if ev: ev.mark("probs_sample")
         for t in range(n):
             if sweep_ev is not None: sweep_ev[("h", t)][0].record()
-            st.apply_1q(t, H)
+            st_.apply_1q(t, H)
             if sweep_ev is not None:
                 sweep_ev[("h", t)][1].record()
                 sweep_ev[("cnot", t)][0].record()
-            st.cnot((t + 1) % n, t)
+            st_.cnot((t + 1) % n, t)
             if sweep_ev is not None:
                 sweep_ev[("cnot", t)][1].record()
                 sweep_ev[("cphase", t)][0].record()
-            st.cphase((t + 1) % n, t, 1)
+            st_.cphase((t + 1) % n, t, 1)
             if sweep_ev is not None: sweep_ev[("cphase", t)][1].record()
         if ev: ev.mark("sweep")
         return shots
@@ -331,10 +332,14 @@ def read_peaks():
 
 def run_e2e(args, st, step_fn, ops_per_step, N):
     """Same workload through the public API with the state in pinned host
-    memory: every step copies the input state host->device, runs the step and
-    copies the final state and the samples back."""
+    memory: every step copies its input state host->device, runs the step
+    and copies its final state and samples back.  Two device states are
+    used in turn, so step i+1's upload and step i-1's download (on their
+    own streams) overlap step i's compute, as a production pipeline would;
+    the timed region still holds every step's copies."""
     import numpy as np
     import torch
+    import paper_0902_0699_gb300 as qc
     n = args.n
     cdt = st.tensor.dtype
     amp = st.tensor.element_size()
@@ -342,26 +347,55 @@ def run_e2e(args, st, step_fn, ops_per_step, N):
     host_in[0] = 1.0
     host_out = torch.empty(N, dtype=cdt, pin_memory=True)
     host_shots = torch.empty(1000, dtype=torch.int64, pin_memory=True)
-    import paper_0902_0699_gb300 as qc
+    comp = torch.cuda.current_stream()
+    st2 = qc.State(n, st.dt)
+    states = [st, st2]
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_done = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_free = [torch.cuda.Event(), torch.cuda.Event()]
+    issued_free = [False, False]
 
-    def e2e_step():
-        st.tensor.copy_(host_in, non_blocking=True)
-        qc.qc_state_invalidate(st.h)
-        shots = step_fn(None)
-        host_out.copy_(st.tensor, non_blocking=True)
-        host_shots.copy_(shots, non_blocking=True)
-    e2e_step()
+    def upload(b):
+        with torch.cuda.stream(s_in):
+            if issued_free[b]:
+                s_in.wait_event(ev_free[b])  # the previous download of this buffer is done
+            states[b].tensor.copy_(host_in, non_blocking=True)
+            ev_in[b].record(s_in)
+
+    def run(b):
+        comp.wait_event(ev_in[b])
+        qc.qc_state_invalidate(states[b].h)
+        shots = step_fn(None, None, states[b])
+        ev_done[b].record(comp)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev_done[b])
+            host_out.copy_(states[b].tensor, non_blocking=True)
+            host_shots.copy_(shots, non_blocking=True)
+            ev_free[b].record(s_out)
+        issued_free[b] = True
+
+    def pipeline(k):
+        upload(0)
+        if k > 1:
+            upload(1)
+        for i in range(k):
+            run(i % 2)
+            if i + 2 < k:
+                upload(i % 2)
+    pipeline(2)  # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
+    pipeline(args.steps)
     torch.cuda.synchronize()
     el = (time.perf_counter() - t0) * 1e3
     tmax, wsum = aggregate(el, float(ops_per_step) * N * args.steps)
+    st2.close()
     del host_in, host_out
     return {"value": wsum / (tmax / 1e3), "unit": UNIT, "h2d_bytes_per_step": N * amp + 8 * 8,
             "d2h_bytes_per_step": N * amp + 8 * 1000, "ms_per_step": tmax / args.steps,
-            "note": "host state in pinned memory -> device, full step, final state and samples -> host"}
+            "note": "host state in pinned memory -> device, full step, final state and samples -> host; "
+                    "two device states in turn, uploads and downloads on their own streams overlap compute"}
 
 
 # ---------------------------------------------------------------- extras ----
