@@ -508,6 +508,35 @@ def extra_c2():
         ms = a.elapsed_time(b)
         gates = layers * n + sum(len(circ.cnot_pairs(l)) for l in range(layers)) + n * (n + 1) // 2 + n // 2
         res[name] = {"ms": ms, "gates": gates, "gate_level_amp_updates_per_s": gates * (1 << n) / (ms * 1e-3)}
+        # the same circuit grouped into dense blocks (gate fusion); complex64
+        # blocks of 5 qubits run on the tensor cores
+        ops = []
+        for l in range(layers):
+            for q in range(n):
+                ops.append((1, q, 0, 0, circ.U[l, q]))
+            for (c, t) in circ.cnot_pairs(l):
+                ops.append((2, c, t, 0, None))
+        kmax, pad = (5, True) if dt == qc.QC_C64 else (3, False)
+        t0 = time.perf_counter()
+        plan = qc.FusedPlan(n, ops, kmax=kmax, pad=pad)
+        t_plan = (time.perf_counter() - t0) * 1e3
+
+        def run_fused():
+            st.reset(0)
+            plan.run(st.h)
+            st.qft()
+        run_fused()
+        torch.cuda.synchronize()
+        a.record()
+        run_fused()
+        b.record()
+        torch.cuda.synchronize()
+        msf = a.elapsed_time(b)
+        nb, _ = plan.info()
+        plan.close()
+        res[name + "_fused"] = {"ms": msf, "blocks": nb, "block_qubits": kmax, "plan_ms_host_once": t_plan,
+                               "gates": gates, "gate_level_amp_updates_per_s": gates * (1 << n) / (msf * 1e-3),
+                               "speedup_vs_gate_by_gate": ms / msf}
         st.close()
     return res
 

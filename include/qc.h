@@ -181,6 +181,46 @@ qc_status qc_apply_2q(qc_state* s, int t1, int t2, const double V[32]);
  * other cases on CUDA cores (complex128 in double-float). */
 qc_status qc_apply_dense(qc_state* s, int k, const int* qubits, const double* U);
 
+/* ------------------------------------------------------- gate fusion -- */
+/* A circuit operator for gate fusion: kind QC_OP_1Q applies m (a U(2),
+ * row-major (re, im)) to q0; QC_OP_CNOT flips q1 where q0 is 1; QC_OP_CPHASE
+ * multiplies the amplitudes with q0 = q1 = 1 by e^{2 pi i / 2^k}; QC_OP_SWAP
+ * exchanges q0 and q1; QC_OP_CTRL applies m to q1 where q0 is 1. */
+#define QC_OP_1Q 1
+#define QC_OP_CNOT 2
+#define QC_OP_CPHASE 3
+#define QC_OP_SWAP 4
+#define QC_OP_CTRL 5
+typedef struct {
+  int32_t kind;
+  int32_t q0, q1;
+  int32_t k;
+  double m[8];
+} qc_op;
+
+typedef struct qc_fused_plan qc_fused_plan;
+
+/* Groups a circuit of n_ops operators (host array, applied in order) on n
+ * qubits into dense blocks of at most kmax (2..6) qubits: the fused
+ * multi-gate pass of sec. 3 (independent pair updates) generalised to
+ * two-qubit operators.  A block takes every later operator whose qubits fit
+ * and that no left-out operator precedes on a shared qubit, so the blocks
+ * compose to the circuit exactly.  pad != 0 pads blocks to kmax qubits
+ * (complex64 5-qubit blocks run on the tensor cores).  The block operators
+ * are composed on the host in FP64. */
+qc_status qc_fused_plan_create(int n, const qc_op* ops, int n_ops, int kmax, int pad, qc_fused_plan** out);
+
+/* Number of blocks and the block size limit. */
+qc_status qc_fused_plan_info(const qc_fused_plan* p, int* n_blocks, int* kmax);
+
+/* Applies the blocks to s (one pass each, qc_apply_dense's kernels).  The
+ * packed operators are uploaded on the first run for each dtype (a
+ * synchronous copy); a run with tensor-core blocks synchronises the stream
+ * once to read its status word (QC_ETIMEOUT if a device wait gave up). */
+qc_status qc_fused_plan_run(qc_state* s, qc_fused_plan* p);
+
+qc_status qc_fused_plan_free(qc_fused_plan* p);
+
 /* One term of a Hamiltonian: a one- (k = 1) or two-body (k = 2) operator h
  * on qubits[0..k-1] (local bit b on qubits[b], as for qc_apply_dense),
  * row-major 2^k x 2^k, (re, im) interleaved (the first 2 * 4^k doubles of

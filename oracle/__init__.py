@@ -146,6 +146,27 @@ def apply_dense(psi, n, qubits, U):
     return psi
 
 
+def apply_ops(psi, n, ops):
+    """A circuit applied literally, one operator after another (OneOpA,
+    CNOT, CPHASEK, SWAP and controlled-U of sec. 3-4 and App. A): ops are
+    (kind, q0, q1, k, U) with kind 1 = U on q0, 2 = CNOT(q0 -> q1),
+    3 = CPHASEK(q0, q1, k), 4 = SWAP(q0, q1), 5 = U on q1 controlled by q0."""
+    for kind, q0, q1, k, U in ops:
+        if kind == 1:
+            apply_1q(psi, n, q0, U)
+        elif kind == 2:
+            cnot(psi, n, q0, q1)
+        elif kind == 3:
+            cphase(psi, n, q0, q1, k)
+        elif kind == 4:
+            swap(psi, n, q0, q1)
+        elif kind == 5:
+            apply_ctrl(psi, n, q0, q1, U)
+        else:
+            raise ValueError("unknown operator kind %d" % kind)
+    return psi
+
+
 def hamiltonian_step(psi, n, dt, terms):
     """One first-order step of Hamiltonian evolution (sec. 7, hbar = 1):
     psi <- [1 - i dt (H1 + H2)] psi, with H a sum of one- and two-body terms

@@ -102,6 +102,10 @@ _SIGS = {
     "qc_wigner_d": [_I, ctypes.c_double, ctypes.c_double, ctypes.c_double, _DP],
     "qc_apply_dense": [_VP, _I, ctypes.POINTER(_I), _DP],
     "qc_hamiltonian_step": [_VP, ctypes.c_double, _VP, _I],
+    "qc_fused_plan_create": [_I, _VP, _I, _I, _I, ctypes.POINTER(_VP)],
+    "qc_fused_plan_info": [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "qc_fused_plan_run": [_VP, _VP],
+    "qc_fused_plan_free": [_VP],
     "qc_density_matrix": [_VP, _I, _I, _I, _DP, _VP, _VP],
     "qc_mixed_spectrum": [_VP, _I, _I, _I, _DP, _DP, _DP, _VP],
 }
@@ -267,6 +271,55 @@ def qc_apply_dense(h, qubits, U):
     if a.size != 2 * (1 << (2 * q.size)):
         raise ValueError("a 2^k x 2^k operator needs 2 * 4^k doubles")
     _check(lib().qc_apply_dense(h, int(q.size), q.ctypes.data_as(ctypes.POINTER(_I)), _dptr(a)))
+
+
+QC_OP_1Q, QC_OP_CNOT, QC_OP_CPHASE, QC_OP_SWAP, QC_OP_CTRL = 1, 2, 3, 4, 5
+
+
+class QCOp(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("q0", ctypes.c_int32), ("q1", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("m", ctypes.c_double * 8)]
+
+
+class FusedPlan:
+    """A circuit grouped into dense blocks (qc_fused_plan_*).  ops: list of
+    (kind, q0, q1, k, U) with U a 2x2 matrix or None."""
+
+    def __init__(self, n: int, ops, kmax: int = 5, pad: bool = True):
+        arr = (QCOp * max(1, len(ops)))()
+        for i, (kind, q0, q1, k, U) in enumerate(ops):
+            arr[i].kind, arr[i].q0, arr[i].q1, arr[i].k = int(kind), int(q0), int(q1), int(k)
+            if U is not None:
+                u = np.asarray(U)
+                if u.shape == (2, 2):  # a matrix (real or complex), not interleaved doubles
+                    u = u.astype(complex)
+                if u.dtype.kind == "c":
+                    u = np.stack([u.real, u.imag], axis=-1)
+                flat = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+                for e in range(8):
+                    arr[i].m[e] = float(flat[e])
+        self.h = ctypes.c_void_p()
+        _check(lib().qc_fused_plan_create(n, ctypes.cast(arr, ctypes.c_void_p), len(ops), kmax, int(pad),
+                                          ctypes.byref(self.h)))
+
+    def info(self):
+        nb, km = _I(), _I()
+        _check(lib().qc_fused_plan_info(self.h, ctypes.byref(nb), ctypes.byref(km)))
+        return nb.value, km.value
+
+    def run(self, state_h):
+        _check(lib().qc_fused_plan_run(state_h, self.h))
+
+    def close(self):
+        if self.h:
+            lib().qc_fused_plan_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class HTerm(ctypes.Structure):

@@ -328,4 +328,18 @@ qc_status reduce_expect(const qc_state* s, uint64_t x, uint64_t z, double* out_h
 qc_status launch_scale(qc_state* s, double f);
 qc_status launch_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_t* out);
 
+// Dense k-qubit blocks (dense.cu): the qubit map of a block, the packed
+// device form of its operator, and an asynchronous launch.
+#define DENSE_MAX_K 6
+struct DenseMap {
+  int k;
+  int pos[DENSE_MAX_K];             // target qubits, ascending (for inserting zeros)
+  uint64_t offs[1 << DENSE_MAX_K];  // offs[l]: bit b of l placed on qubit qubits[b]
+};
+qc_status dense_map(int n, int k, const int* qubits, DenseMap* M);
+bool dense_uses_tc(qc_dtype dt, int k);
+size_t dense_op_bytes(qc_dtype dt, int k);
+void dense_pack(qc_dtype dt, int k, const double* U, void* host_out);
+qc_status dense_launch(qc_state* s, const DenseMap& M, const void* dev_op, int* status);
+
 }  // namespace qc

@@ -23,14 +23,6 @@
 
 namespace qc {
 
-#define DENSE_MAX_K 6
-
-// sorted target positions and the offset table, in constant-size arrays
-struct DenseMap {
-  int k;
-  int pos[DENSE_MAX_K];        // target qubits, ascending (for inserting zeros)
-  uint64_t offs[1 << DENSE_MAX_K];
-};
 
 __device__ __forceinline__ uint64_t group_base(uint64_t g, const DenseMap& M) {
   for (int b = 0; b < M.k; ++b) g = insert0(g, M.pos[b]);
@@ -331,132 +323,164 @@ __global__ void __launch_bounds__(TC_M) k_dense_tc(float2* __restrict__ psi, uin
 using namespace qc;
 
 // -------------------------------------------------------------- host ----
+namespace qc {
+
 static uint32_t tf32_hi_bits(float x) {
   uint32_t b;
   memcpy(&b, &x, 4);
   return (b + 0x1000u) & 0xFFFFE000u;
 }
 
+qc_status dense_map(int n, int k, const int* qubits, DenseMap* M) {
+  if (k < 1 || k > DENSE_MAX_K || k > n || !qubits) {
+    set_error("dense block: k = %d must be in 1..%d and <= n = %d", k, DENSE_MAX_K, n);
+    return QC_EINVAL;
+  }
+  *M = DenseMap{};
+  M->k = k;
+  uint64_t seen = 0;
+  for (int b = 0; b < k; ++b) {
+    if (qubits[b] < 0 || qubits[b] >= n || ((seen >> qubits[b]) & 1)) {
+      set_error("dense block: qubit %d out of range or repeated", qubits[b]);
+      return QC_EINVAL;
+    }
+    seen |= 1ull << qubits[b];
+    M->pos[b] = qubits[b];
+  }
+  std::sort(M->pos, M->pos + k);
+  for (int l = 0; l < (1 << k); ++l) {
+    uint64_t o = 0;
+    for (int b = 0; b < k; ++b)
+      if ((l >> b) & 1) o |= 1ull << qubits[b];
+    M->offs[l] = o;
+  }
+  return QC_OK;
+}
+
+bool dense_uses_tc(qc_dtype dt, int k) { return dt == QC_C64 && k == 5; }
+
+size_t dense_op_bytes(qc_dtype dt, int k) {
+  return dense_uses_tc(dt, k) ? 2 * sizeof(float) * TC_N * TC_K : sizeof(double) * 2 * (size_t)(1 << k) * (1 << k);
+}
+
+// The device form of U: W^T split into TF32 hi and lo for the tensor cores
+// (W^T[n][kk], n the output real 2j or 2j+1, kk the input real 2l or
+// 2l+1), else U itself.
+void dense_pack(qc_dtype dt, int k, const double* U, void* host_out) {
+  const int dim = 1 << k;
+  if (!dense_uses_tc(dt, k)) {
+    memcpy(host_out, U, sizeof(double) * 2 * dim * dim);
+    return;
+  }
+  float* hi = reinterpret_cast<float*>(host_out);
+  float* lo = hi + TC_N * TC_K;
+  for (int j = 0; j < dim; ++j)
+    for (int l = 0; l < dim; ++l) {
+      const double ur = U[2 * (j * dim + l)], ui = U[2 * (j * dim + l) + 1];
+      const float vals[4] = {(float)ur, (float)-ui, (float)ui, (float)ur};  // (2j,2l) (2j,2l+1) (2j+1,2l) (2j+1,2l+1)
+      const int rr[4] = {2 * j, 2 * j, 2 * j + 1, 2 * j + 1}, cc[4] = {2 * l, 2 * l + 1, 2 * l, 2 * l + 1};
+      for (int q = 0; q < 4; ++q) {
+        const float x = vals[q];
+        const uint32_t hb = tf32_hi_bits(x);
+        float h;
+        memcpy(&h, &hb, 4);
+        hi[rr[q] * TC_K + cc[q]] = h;
+        lo[rr[q] * TC_K + cc[q]] = x - h;
+      }
+    }
+}
+
+// Launches one block on the state's stream (no allocation, no sync);
+// dev_op holds dense_pack's output; status (tensor cores) is a device word
+// that a timed-out wait sets to 1.
+qc_status dense_launch(qc_state* s, const DenseMap& M, const void* dev_op, int* status) {
+  const int k = M.k, dim = 1 << k;
+  const uint64_t ngroups = 1ull << (s->n - k);
+  if (dense_uses_tc(s->dt, k)) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+      attr = true;
+    }
+    const uint64_t ntiles = (ngroups + TC_M - 1) / TC_M;
+    const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)sm_count() * 2);
+    k_dense_tc<<<grid, TC_M, TC_SMEM, s->stream>>>(reinterpret_cast<float2*>(s->data), ngroups,
+                                                     reinterpret_cast<const float*>(dev_op),
+                                                     reinterpret_cast<const float*>(dev_op) + TC_N * TC_K, M, status);
+  } else if (s->dt == QC_C64) {
+    const size_t smem = sizeof(float2) * ((size_t)dim * dim + (size_t)DENSE_GROUPS * dim);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_dense<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(float2) * (64 * 64 + DENSE_GROUPS * 64)));
+      attr = true;
+    }
+    const unsigned grid =
+        (unsigned)std::min<uint64_t>((ngroups + DENSE_GROUPS - 1) / DENSE_GROUPS, (uint64_t)sm_count() * 4);
+    k_dense<float><<<grid, 256, smem, s->stream>>>(reinterpret_cast<float2*>(s->data), ngroups,
+                                                    reinterpret_cast<const double*>(dev_op), M);
+  } else {
+    const size_t smem = sizeof(ffc) * ((size_t)dim * dim + (size_t)DENSE_GROUPS * dim);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_dense<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(ffc) * (64 * 64 + DENSE_GROUPS * 64)));
+      attr = true;
+    }
+    const unsigned grid =
+        (unsigned)std::min<uint64_t>((ngroups + DENSE_GROUPS - 1) / DENSE_GROUPS, (uint64_t)sm_count() * 4);
+    k_dense<double><<<grid, 256, smem, s->stream>>>(reinterpret_cast<double2*>(s->data), ngroups,
+                                                     reinterpret_cast<const double*>(dev_op), M);
+  }
+  s->sum_valid = false;
+  return QC_OK;
+}
+
+}  // namespace qc
+
 QC_API qc_status qc_apply_dense(qc_state* s, int k, const int* qubits, const double* U) {
   clear_error();
   qc_status st = check_state(s);
   if (st) return st;
-  if (k < 1 || k > DENSE_MAX_K || k > s->n || !qubits || !U) {
-    set_error("qc_apply_dense: k = %d must be in 1..%d and <= n = %d, pointers non-NULL", k, DENSE_MAX_K, s->n);
+  if (!U) {
+    set_error("qc_apply_dense: U is NULL");
     return QC_EINVAL;
   }
-  DenseMap M = {};
-  M.k = k;
-  uint64_t seen = 0;
-  for (int b = 0; b < k; ++b) {
-    if (qubits[b] < 0 || qubits[b] >= s->n || ((seen >> qubits[b]) & 1)) {
-      set_error("qc_apply_dense: qubit %d out of range or repeated", qubits[b]);
-      return QC_EINVAL;
-    }
-    seen |= 1ull << qubits[b];
-    M.pos[b] = qubits[b];
-  }
+  DenseMap M;
+  st = dense_map(s->n, k, qubits, &M);
+  if (st) return st;
   const int dim = 1 << k;
   for (int e = 0; e < 2 * dim * dim; ++e)
     if (!std::isfinite(U[e])) {
       set_error("qc_apply_dense: non-finite operator entry");
       return QC_EINVAL;
     }
-  std::sort(M.pos, M.pos + k);
-  for (int l = 0; l < dim; ++l) {
-    uint64_t o = 0;
-    for (int b = 0; b < k; ++b)
-      if ((l >> b) & 1) o |= 1ull << qubits[b];
-    M.offs[l] = o;
-  }
-  const uint64_t ngroups = 1ull << (s->n - k);
-  const bool tc = s->dt == QC_C64 && k == 5;
-  // device copy of the operator (the CUDA-core kernels) or of W^T split (tensor cores)
-  const size_t ubytes = tc ? 2 * sizeof(float) * TC_N * TC_K : sizeof(double) * 2 * dim * dim;
+  const size_t ob = dense_op_bytes(s->dt, k);
+  std::vector<unsigned char> host(ob);
+  dense_pack(s->dt, k, U, host.data());
   void* dbuf = nullptr;
-  cudaError_t e = cudaMallocAsync(&dbuf, ubytes + 16, s->stream);
+  cudaError_t e = cudaMallocAsync(&dbuf, ob + 16, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "dense operator buffer");
-  if (tc) {
-    std::vector<float> wt(2 * TC_N * TC_K);
-    float* hi = wt.data();
-    float* lo = hi + TC_N * TC_K;
-    // W^T[n][kk]: n = output real (2j or 2j+1), kk = input real (2l or 2l+1)
-    for (int j = 0; j < dim; ++j)
-      for (int l = 0; l < dim; ++l) {
-        const double ur = U[2 * (j * dim + l)], ui = U[2 * (j * dim + l) + 1];
-        const float vals[4] = {(float)ur, (float)-ui, (float)ui, (float)ur};  // (2j,2l) (2j,2l+1) (2j+1,2l) (2j+1,2l+1)
-        const int rr[4] = {2 * j, 2 * j, 2 * j + 1, 2 * j + 1}, cc[4] = {2 * l, 2 * l + 1, 2 * l, 2 * l + 1};
-        for (int q = 0; q < 4; ++q) {
-          const float x = vals[q];
-          uint32_t hb = tf32_hi_bits(x);
-          float h;
-          memcpy(&h, &hb, 4);
-          hi[rr[q] * TC_K + cc[q]] = h;
-          lo[rr[q] * TC_K + cc[q]] = x - h;
-        }
-      }
-    e = cudaMemcpyAsync(dbuf, wt.data(), ubytes, cudaMemcpyHostToDevice, s->stream);
-    int* status = reinterpret_cast<int*>(reinterpret_cast<char*>(dbuf) + ubytes);
-    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), s->stream);
-    if (e == cudaSuccess) {
-      static bool attr = false;
-      if (!attr) {
-        cudaFuncSetAttribute(k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-        attr = true;
-      }
-      const uint64_t ntiles = (ngroups + TC_M - 1) / TC_M;
-      const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)sm_count() * 2);
-      k_dense_tc<<<grid, TC_M, TC_SMEM, s->stream>>>(reinterpret_cast<float2*>(s->data), ngroups,
-                                                       reinterpret_cast<const float*>(dbuf),
-                                                       reinterpret_cast<const float*>(dbuf) + TC_N * TC_K, M, status);
-      st = check_launch("dense block (tensor cores)", 1);
-      int hstat = 0;
-      if (!st) {
-        e = cudaMemcpyAsync(&hstat, status, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-        if (e != cudaSuccess) st = cuda_fail(e, "dense block status");
-        else if (hstat) {
-          set_error("dense block: an mbarrier wait timed out");
-          st = QC_ETIMEOUT;
-        }
-      }
-    } else {
-      st = cuda_fail(e, "dense operator upload");
+  int* status = reinterpret_cast<int*>(reinterpret_cast<char*>(dbuf) + ob);
+  e = cudaMemcpyAsync(dbuf, host.data(), ob, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), s->stream);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(dbuf, s->stream);
+    return cuda_fail(e, "dense operator upload");
+  }
+  dense_launch(s, M, dbuf, status);
+  st = check_launch(dense_uses_tc(s->dt, k) ? "dense block (tensor cores)" : "dense block", 1);
+  if (!st && dense_uses_tc(s->dt, k)) {
+    int hstat = 0;
+    e = cudaMemcpyAsync(&hstat, status, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "dense block status");
+    else if (hstat) {
+      set_error("dense block: an mbarrier wait timed out");
+      st = QC_ETIMEOUT;
     }
-  } else {
-    e = cudaMemcpyAsync(dbuf, U, ubytes, cudaMemcpyHostToDevice, s->stream);
-    if (e != cudaSuccess) {
-      cudaFreeAsync(dbuf, s->stream);
-      return cuda_fail(e, "dense operator upload");
-    }
-    const int G = DENSE_GROUPS;
-    if (s->dt == QC_C64) {
-      const size_t smem = sizeof(float2) * ((size_t)dim * dim + (size_t)G * dim);
-      static bool attr = false;
-      if (!attr) {
-        cudaFuncSetAttribute(k_dense<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(float2) * (64 * 64 + G * 64)));
-        attr = true;
-      }
-      const unsigned grid = (unsigned)std::min<uint64_t>((ngroups + G - 1) / G, (uint64_t)sm_count() * 4);
-      k_dense<float><<<grid, 256, smem, s->stream>>>(reinterpret_cast<float2*>(s->data), ngroups,
-                                                      reinterpret_cast<const double*>(dbuf), M);
-    } else {
-      const size_t smem = sizeof(ffc) * ((size_t)dim * dim + (size_t)G * dim);
-      static bool attr = false;
-      if (!attr) {
-        cudaFuncSetAttribute(k_dense<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(ffc) * (64 * 64 + G * 64)));
-        attr = true;
-      }
-      const unsigned grid = (unsigned)std::min<uint64_t>((ngroups + G - 1) / G, (uint64_t)sm_count() * 4);
-      k_dense<double><<<grid, 256, smem, s->stream>>>(reinterpret_cast<double2*>(s->data), ngroups,
-                                                       reinterpret_cast<const double*>(dbuf), M);
-    }
-    st = check_launch("dense block", 1);
   }
   cudaFreeAsync(dbuf, s->stream);
-  s->sum_valid = false;
   return st;
 }
 
