@@ -122,3 +122,62 @@ def test_bench_workload_full_size(qc, n, dt, tol, seed):
     st.close()
     del st
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n,dt,tol,rel", [(34, 1, 1e-5, 1e-5), (33, 0, 1e-12, 1e-11)])
+def test_maximum_size(qc, n, dt, tol, rel):
+    # the largest states the API takes (128 GiB): indices above 2^32 in
+    # every kernel, Grover against its closed form, exact sampling against
+    # the closed-form integer CDF, and self-inverse gates on the top qubit
+    import torch
+    N = 1 << n
+    need = N * (8 if dt == 1 else 16)
+    free, _ = torch.cuda.mem_get_info()
+    if free < need + (8 << 30):
+        pytest.skip("needs a GPU with room for a %d GiB state" % (need >> 30))
+    M, iters = 8, 3
+    marked = W.marked_indices(W.rng(n), n, M)
+    st = qc.State(n, dt)
+    st.uniform()
+    for _ in range(iters):
+        st.grover_step(marked)
+    a, b = closed(n, M, iters)
+    g = W.rng(n + 1)
+    idx = np.unique(np.concatenate([marked.astype(np.int64), g.integers(0, N, 2000),
+                                    [0, 1, (1 << 32) - 1, 1 << 32, (1 << 32) + 1, N // 2, N - 2, N - 1]]))
+    ism = np.isin(idx, marked.astype(np.int64))
+    ref = np.where(ism, a, b)
+    got = gather(st, idx)
+    assert np.max(np.abs(got - ref)) <= tol
+    assert np.max(np.abs(got - ref)) <= rel * max(abs(a), abs(b))
+    # the state has one value on the unmarked and one on the marked items
+    vu, vm = got[~ism][0], got[ism][0]
+    assert np.all(got[~ism] == vu) and np.all(got[ism] == vm)
+    p_u = vu.real * vu.real + vu.imag * vu.imag  # the sampler's p_i, rounded the same way
+    p_m = vm.real * vm.real + vm.imag * vm.imag
+    w_u, w_m = int(p_u * 2.0 ** 62), int(p_m * 2.0 ** 62)
+    ms = sorted(int(m) for m in marked)
+
+    def W_at(i):  # closed-form integer CDF
+        cnt = sum(1 for m in ms if m <= i)
+        return (i + 1 - cnt) * w_u + cnt * w_m
+    shots = st.sample(7, 200).cpu().numpy()
+    for s_, t_ in zip(shots, O.sample_targets(7, 200, W_at(N - 1))):
+        lo, hi = 0, N - 1
+        while lo < hi:
+            mid = (lo + hi) // 2
+            if W_at(mid) > t_:
+                hi = mid
+            else:
+                lo = mid + 1
+        assert int(s_) == lo
+    # H and CNOT on the top qubit, each applied twice: the identity
+    H = O.H_MAT
+    st.apply_1q(n - 1, H)
+    st.cnot(0, n - 1)
+    st.cnot(0, n - 1)
+    st.apply_1q(n - 1, H)
+    assert np.max(np.abs(gather(st, idx) - got)) <= 4 * tol
+    st.close()
+    del st
+    torch.cuda.empty_cache()
