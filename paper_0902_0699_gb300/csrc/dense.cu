@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(256) k_dense(typename DenseT<R>::V* __restrict
 // adjacent in K are 128 B apart (leading byte offset), 8-row groups are
 // 16 * 128 = 2048 B apart (stride byte offset).
 #define TC_M 128
+#define TC_T 256  // threads: two per tile row (halves of 16 amplitudes)
 #define TC_K 64
 #define TC_N 64
 #define TC_LBO 128
@@ -176,7 +177,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 // and commits them to an mbarrier, every warp reads its 32 accumulator
 // lanes back and writes its rows.  Wt holds W^T (N x K) split hi, lo.
 // status: set to 1 if an mbarrier wait ran out (the kernel then stops).
-__global__ void __launch_bounds__(TC_M) k_dense_tc(float2* __restrict__ psi, uint64_t ngroups,
+__global__ void __launch_bounds__(TC_T, 2) k_dense_tc(float2* __restrict__ psi, uint64_t ngroups,
                                                    const float* __restrict__ Wt_hi, const float* __restrict__ Wt_lo,
                                                    DenseMap M, int* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char tsm[];
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(TC_M) k_dense_tc(float2* __restrict__ psi, uin
   __shared__ int stop;
   const int tid = threadIdx.x, warp = tid >> 5;
   // W^T into the canonical layout (once per CTA)
-  for (int e = tid; e < TC_N * TC_K; e += TC_M) {
+  for (int e = tid; e < TC_N * TC_K; e += TC_T) {
     const int r = e / TC_K, c = e % TC_K;
     *reinterpret_cast<float*>(B_hi + canon_off(r, c)) = Wt_hi[e];
     *reinterpret_cast<float*>(B_lo + canon_off(r, c)) = Wt_lo[e];
@@ -215,51 +216,59 @@ __global__ void __launch_bounds__(TC_M) k_dense_tc(float2* __restrict__ psi, uin
   for (int l = 0; l < 32; ++l) contig &= (M.offs[l] == (uint64_t)l);
   uint32_t phase = 0;
   const uint64_t ntiles = (ngroups + TC_M - 1) / TC_M;
-  // row tid of a tile, held in registers between its load and its staging
-  float4 nxt[16];
-  bool nlive = false;
-  uint64_t nbase = 0;
+  // Thread tid serves tile row `row` (its TMEM lane: warp & 3 picks the lane
+  // quarter) and half `hf` of it (16 amplitudes; 32 accumulator columns).
+  const int row = tid & (TC_M - 1), hf = tid >> 7;
   // contiguous targets (qubits 0..4 in order): a tile is one 32 KiB block,
-  // moved by all threads together.  Element (i, tid) is row 8i + (tid & 7),
-  // 16-byte segment 4 warp + ((tid >> 3) & 3): a warp reads 8 rows x 64
-  // contiguous bytes (whole sectors) and a quarter-warp writes one
-  // contiguous 128-byte run of the K-major layout.
-  const int crow = tid & 7, cseg = 4 * warp + ((tid >> 3) & 3);
-  auto fetch = [&](uint64_t tile) {
+  // moved by all threads together.  Chunk i of thread tid is row
+  // 8 (8 hf + i) + (tid & 7), 16-byte segment 4 ((tid & 127) >> 5) +
+  // ((tid >> 3) & 3): a warp reads 8 rows x 64 contiguous bytes (whole
+  // sectors) and a quarter-warp writes one contiguous 128-byte run of the
+  // K-major layout.
+  const int crow = tid & 7, cseg = 4 * (row >> 5) + ((tid >> 3) & 3);
+  // A thread's 8 float4 of a tile in registers from its load to its
+  // staging; two register buffers, so tile t+2's loads are in flight during
+  // tile t.
+  auto fetch = [&](uint64_t tile, float4 (&R)[8], bool& rlive, uint64_t& rbase) {
     if (contig) {
       const float4* src = reinterpret_cast<const float4*>(psi) + tile * TC_M * 16;
-      nlive = true;
-      for (int i = 0; i < 16; ++i) {
-        const uint64_t row = tile * TC_M + 8 * i + crow;
-        nxt[i] = row < ngroups ? src[(8 * i + crow) * 16 + cseg] : make_float4(0.f, 0.f, 0.f, 0.f);
+      rlive = true;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int ii = 8 * hf + i;
+        R[i] = tile * TC_M + 8 * ii + crow < ngroups ? src[(8 * ii + crow) * 16 + cseg]
+                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       return;
     }
-    const uint64_t g = tile * TC_M + tid;
-    nlive = g < ngroups;
-    nbase = nlive ? group_base(g, M) : 0;
-    for (int l4 = 0; l4 < 16; ++l4) {
+    const uint64_t g = tile * TC_M + row;
+    rlive = g < ngroups;
+    rbase = rlive ? group_base(g, M) : 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int l4 = 8 * hf + i;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (nlive) {
-        const float2 x0 = psi[nbase | M.offs[2 * l4]], x1 = psi[nbase | M.offs[2 * l4 + 1]];
+      if (rlive) {
+        const float2 x0 = psi[rbase | M.offs[2 * l4]], x1 = psi[rbase | M.offs[2 * l4 + 1]];
         v = make_float4(x0.x, x0.y, x1.x, x1.y);
       }
-      nxt[l4] = v;
+      R[i] = v;
     }
   };
-  if (blockIdx.x < ntiles) fetch(blockIdx.x);
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const bool live = nlive;
-    const uint64_t base = nbase;
-    // stage row tid: 32 amplitudes -> 64 reals, split into TF32 hi and lo
-    for (int l4 = 0; l4 < 16; ++l4) {  // two amplitudes (4 reals) per core-matrix row
-      const float4 v = nxt[l4];
+  // one tile: stage R, MMAs, refill R with tile + 2 grid, epilogue
+  auto body = [&](uint64_t tile, float4 (&R)[8], bool& rlive, uint64_t& rbase) -> bool {
+    const bool live = rlive;
+    const uint64_t base = rbase;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {  // two amplitudes (4 reals) per core-matrix row
+      const float4 v = R[i];
       float4 h, lo;
       tf32_split(v.x, h.x, lo.x);
       tf32_split(v.y, h.y, lo.y);
       tf32_split(v.z, h.z, lo.z);
       tf32_split(v.w, h.w, lo.w);
-      const uint32_t off = contig ? canon_off(8 * l4 + crow, 4 * cseg) : canon_off(tid, 4 * l4);
+      const uint32_t off =
+          contig ? canon_off(8 * (8 * hf + i) + crow, 4 * cseg) : canon_off(row, 4 * (8 * hf + i));
       *reinterpret_cast<float4*>(A_hi + off) = h;
       *reinterpret_cast<float4*>(A_lo + off) = lo;
     }
@@ -279,37 +288,48 @@ __global__ void __launch_bounds__(TC_M) k_dense_tc(float2* __restrict__ psi, uin
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar_a)
                    : "memory");
     }
-    // the next tile's loads overlap the MMAs (rows of different groups)
-    if (tile + gridDim.x < ntiles) fetch(tile + gridDim.x);
+    // tile + 2 grid's loads overlap this tile's MMAs and epilogue and the next tile
+    if (tile + 2ull * gridDim.x < ntiles) fetch(tile + 2ull * gridDim.x, R, rlive, rbase);
     if (!mbar_wait(mbar_a, phase)) {
       if (tid == 0) atomicExch(status, 1);
       stop = 1;
     }
     phase ^= 1u;
     __syncthreads();
-    if (stop) break;
+    if (stop) return false;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    // warp w holds rows 32w .. 32w+31 in TMEM lanes 32w ..
-    float out[64];
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    tmem_ld32(lane_base, out);
-    tmem_ld32(lane_base + 32, out + 32);
+    // lanes 32 (warp & 3) .. hold this warp's rows; columns 32 hf .. 32 hf + 31
+    float out[32];
+    tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 32 * hf, out);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    if (contig) {
-      // rows through shared memory (A_hi is free: the MMAs are done), then
-      // out with the coalesced mapping of the loads
-      for (int l4 = 0; l4 < 16; ++l4)
-        *reinterpret_cast<float4*>(A_hi + canon_off(tid, 4 * l4)) =
+    if (contig) {  // rows through shared memory (A_hi is free: the MMAs are done)
+#pragma unroll
+      for (int l4 = 0; l4 < 8; ++l4)
+        *reinterpret_cast<float4*>(A_hi + canon_off(row, 4 * (8 * hf + l4))) =
             make_float4(out[4 * l4], out[4 * l4 + 1], out[4 * l4 + 2], out[4 * l4 + 3]);
       __syncthreads();
       float4* dst = reinterpret_cast<float4*>(psi) + tile * TC_M * 16;
-      for (int i = 0; i < 16; ++i)
-        if (tile * TC_M + 8 * i + crow < ngroups)
-          dst[(8 * i + crow) * 16 + cseg] = *reinterpret_cast<const float4*>(A_hi + canon_off(8 * i + crow, 4 * cseg));
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int ii = 8 * hf + i;
+        if (tile * TC_M + 8 * ii + crow < ngroups)
+          dst[(8 * ii + crow) * 16 + cseg] = *reinterpret_cast<const float4*>(A_hi + canon_off(8 * ii + crow, 4 * cseg));
+      }
     } else if (live) {
-      for (int l = 0; l < 32; ++l) psi[base | M.offs[l]] = make_float2(out[2 * l], out[2 * l + 1]);
+#pragma unroll
+      for (int l = 0; l < 16; ++l) psi[base | M.offs[16 * hf + l]] = make_float2(out[2 * l], out[2 * l + 1]);
     }
     __syncthreads();  // every lane is read before the next tile's MMAs overwrite TMEM
+    return true;
+  };
+  float4 RA[8], RB[8];
+  bool la = false, lb = false;
+  uint64_t ba = 0, bb = 0;
+  if (blockIdx.x < ntiles) fetch(blockIdx.x, RA, la, ba);
+  if (blockIdx.x + gridDim.x < ntiles) fetch(blockIdx.x + gridDim.x, RB, lb, bb);
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += 2ull * gridDim.x) {
+    if (!body(tile, RA, la, ba)) break;
+    if (tile + gridDim.x < ntiles && !body(tile + gridDim.x, RB, lb, bb)) break;
   }
   // an MMA that a timed-out wait left in flight: one more bounded wait
   if (stop && tid == 0) mbar_wait(mbar_a, phase ^ 1u);
@@ -404,7 +424,7 @@ qc_status dense_launch(qc_state* s, const DenseMap& M, const void* dev_op, int* 
     }
     const uint64_t ntiles = (ngroups + TC_M - 1) / TC_M;
     const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)sm_count() * 2);
-    k_dense_tc<<<grid, TC_M, TC_SMEM, s->stream>>>(reinterpret_cast<float2*>(s->data), ngroups,
+    k_dense_tc<<<grid, TC_T, TC_SMEM, s->stream>>>(reinterpret_cast<float2*>(s->data), ngroups,
                                                      reinterpret_cast<const float*>(dev_op),
                                                      reinterpret_cast<const float*>(dev_op) + TC_N * TC_K, M, status);
   } else if (s->dt == QC_C64) {
