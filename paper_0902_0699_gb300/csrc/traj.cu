@@ -326,9 +326,10 @@ __device__ __forceinline__ float2 noisy_out(uint32_t j, float2 u, const PassArgs
 }
 
 // A pass that maps every 16-byte vector v (amplitudes 2v, 2v+1) of [lo, hi)
-// to f(v, stored vector); sums of the outputs and the output at m.  Four
-// vectors are loaded before any is stored, to keep loads in flight.
-template <class F>
+// to f(v, stored vector); sums of the outputs and the output at m.  UNR
+// vectors are loaded before any is stored, to keep loads in flight (the
+// passes are bound by L2 latency).
+template <int UNR, class F>
 __device__ __forceinline__ void vec_pass(float4* p4, uint32_t lo, uint32_t hi, uint32_t m, int tid, int T, F f,
                                          Acc& acc, float& cmr, float& cmi) {
   const uint32_t vm = m >> 1, vhi = hi >> 1, uT = (uint32_t)T;
@@ -343,13 +344,15 @@ __device__ __forceinline__ void vec_pass(float4* p4, uint32_t lo, uint32_t hi, u
     }
   };
   uint32_t v = (lo >> 1) + (uint32_t)tid;
-  for (; v + 3u * uT < vhi; v += 4u * uT) {
-    const float4 u0 = p4[v], u1 = p4[v + uT], u2 = p4[v + 2u * uT], u3 = p4[v + 3u * uT];
-    one(v, u0);
-    one(v + uT, u1);
-    one(v + 2u * uT, u2);
-    one(v + 3u * uT, u3);
-    acc.flush();
+  for (; v + (UNR - 1) * uT < vhi; v += UNR * uT) {
+    float4 u[UNR];
+#pragma unroll
+    for (int i = 0; i < UNR; ++i) u[i] = p4[v + i * uT];
+#pragma unroll
+    for (int i = 0; i < UNR; ++i) {
+      one(v + i * uT, u[i]);
+      if (i % 4 == 3) acc.flush();
+    }
   }
   for (; v < vhi; v += uT) {
     one(v, p4[v]);
@@ -494,7 +497,7 @@ __global__ void __launch_bounds__(512, MINB) k_traj(TrajParams P) {
         ipow(a0p, re, im);
         return make_float2(re, im);
       };
-      vec_pass(p4, lo, hi, m, tid, T,
+      vec_pass<(MINB == 1 ? 8 : 4)>(p4, lo, hi, m, tid, T,
                [&](uint32_t v, const float4&) {
                  const float2 o0 = amp(2 * v), o1 = amp(2 * v + 1);
                  return make_float4(o0.x, o0.y, o1.x, o1.y);
@@ -630,7 +633,7 @@ __global__ void __launch_bounds__(512, MINB) k_traj(TrajParams P) {
         float cmr = 0.f, cmi = 0.f;
         if ((q.X >> 1) == 0) {
           const bool sw = q.X & 1u;
-          vec_pass(p4, lo, hi, m, tid, T,
+          vec_pass<(MINB == 1 ? 8 : 4)>(p4, lo, hi, m, tid, T,
                    [&](uint32_t v, const float4& u) {
                      const float2 a0 = virt(2 * v, make_float2(u.x, u.y), q);
                      const float2 a1 = virt(2 * v + 1, make_float2(u.z, u.w), q);
@@ -660,7 +663,7 @@ __global__ void __launch_bounds__(512, MINB) k_traj(TrajParams P) {
       Acc acc;
       acc.zero();
       float cmr = 0.f, cmi = 0.f;
-      vec_pass(p4, lo, hi, m, tid, T,
+      vec_pass<(MINB == 1 ? 8 : 4)>(p4, lo, hi, m, tid, T,
                [&](uint32_t v, const float4& u) {
                  const float2 o0 = virt(2 * v, make_float2(u.x, u.y), q), o1 = virt(2 * v + 1, make_float2(u.z, u.w), q);
                  return make_float4(o0.x, o0.y, o1.x, o1.y);
