@@ -61,34 +61,34 @@ __device__ __forceinline__ uint64_t pair_base(uint64_t p, int p0, int p1, uint64
 }
 
 // Scalar form: one pair per work item, 16-byte (c128) or 8-byte (c64)
-// accesses.  Two items are processed per loop trip so that four loads are in
-// flight before the first use.
+// accesses.  UNR items are processed per loop trip so that 2 UNR loads are
+// in flight before the first use (4 for complex128).
 template <typename R, int KIND, int NINS>
 __global__ void __launch_bounds__(256) k_pairs(typename CT<R>::V2* __restrict__ s, uint64_t npairs, int p0,
                                                int p1, uint64_t setm, int t, GateArg<R> G) {
   using IO = AmpIO<R>;
   constexpr bool B1 = touches_bit1_only(KIND);
+  constexpr int UNR = sizeof(R) == 8 ? 4 : 2;
   const uint64_t st = 1ull << t;
   const uint64_t GS = (uint64_t)gridDim.x * blockDim.x;
   uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (; p + GS < npairs; p += 2 * GS) {
-    const uint64_t i0 = pair_base<NINS>(p, p0, p1, setm), j0 = pair_base<NINS>(p + GS, p0, p1, setm);
-    Cx<R> a0 = cmake<R>(0, 0), b0 = cmake<R>(0, 0);
-    if (!B1) {
-      a0 = IO::ld(s + i0);
-      b0 = IO::ld(s + j0);
+  for (; p + (UNR - 1) * GS < npairs; p += UNR * GS) {
+    uint64_t i[UNR];
+    Cx<R> a[UNR], b[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      i[u] = pair_base<NINS>(p + u * GS, p0, p1, setm);
+      a[u] = B1 ? cmake<R>(0, 0) : IO::ld(s + i[u]);
+      b[u] = IO::ld(s + (i[u] | st));
     }
-    Cx<R> a1 = IO::ld(s + (i0 | st)), b1 = IO::ld(s + (j0 | st));
-    apply_gate<R, KIND>(G, a0, a1);
-    apply_gate<R, KIND>(G, b0, b1);
-    if (!B1) {
-      IO::st(s + i0, a0);
-      IO::st(s + j0, b0);
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      apply_gate<R, KIND>(G, a[u], b[u]);
+      if (!B1) IO::st(s + i[u], a[u]);
+      IO::st(s + (i[u] | st), b[u]);
     }
-    IO::st(s + (i0 | st), a1);
-    IO::st(s + (j0 | st), b1);
   }
-  if (p < npairs) {
+  for (; p < npairs; p += GS) {
     const uint64_t i0 = pair_base<NINS>(p, p0, p1, setm);
     Cx<R> a0 = cmake<R>(0, 0);
     if (!B1) a0 = IO::ld(s + i0);
@@ -155,7 +155,7 @@ static void launch_kind(qc_state* s, int nins, int p0, int p1, uint64_t setm, in
     }
   }
   auto k = (nins == 1) ? k_pairs<R, KIND, 1> : k_pairs<R, KIND, 2>;
-  k<<<resident_grid(k, T, npairs, 2 * T), T, 0, s->stream>>>(d, npairs, p0, p1, setm, t, G);
+  k<<<resident_grid(k, T, npairs, (sizeof(R) == 8 ? 4 : 2) * T), T, 0, s->stream>>>(d, npairs, p0, p1, setm, t, G);
 }
 
 template <typename R>
