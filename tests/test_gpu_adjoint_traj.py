@@ -260,3 +260,18 @@ def test_traj_replay_wide_states(qc, autotune):
         prob = O.probs(psi, n)
         assert abs(ps[i] - prob[m] / prob.sum()) <= 1e-5
         assert abs(pr[i] - O.readout_success(prob, n, m, tb.p_readout) / prob.sum()) <= 1e-5
+
+
+def test_traj_degenerate_sizes(qc):
+    # 1..4 qubits: clusters of one or two CTAs, states of 2..16 amplitudes
+    # (one 16-byte vector per CTA at n = 1), noisy enough to exercise the
+    # error passes
+    tb = W.trajectory_batch(24, 1, 4, seed=8, p_gate=0.05, p_readout=0.05)
+    ps, pr, oc, ne, info = run_traj(qc, tb, autotune=1)
+    for i in range(len(tb.nq)):
+        n, m, k = int(tb.nq[i]), int(tb.marked[i]), int(tb.iters[i])
+        psi, errs = O.trajectory_run(n, m, k, tb.seed, i, tb.thr_gate)
+        assert ne[i] == errs
+        prob = O.probs(psi, n)
+        assert abs(ps[i] - prob[m] / prob.sum()) <= 1e-5
+        assert abs(pr[i] - O.readout_success(prob, n, m, tb.p_readout) / prob.sum()) <= 1e-5

@@ -88,3 +88,16 @@ def test_fuse_invalid(qc):
         qc.FusedPlan(4, [(1, 4, 0, 0, np.eye(2))])
     with pytest.raises(qc.QCError):
         qc.FusedPlan(4, [(1, 0, 0, 0, np.eye(2))], kmax=7)
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_fused_two_qubit_state(qc, dt):
+    # the smallest circuit with two-qubit operators: blocks hold the whole state
+    g = W.rng(4)
+    u = W.haar_u2(g, 3)
+    ops = [(1, 0, 0, 0, u[0]), (2, 0, 1, 0, None), (1, 1, 0, 0, u[1]), (3, 1, 0, 3, None),
+           (4, 0, 1, 0, None), (5, 1, 0, 0, u[2])]
+    for kmax in (2, 5):
+        err, nb = run(qc, 2, dt, ops, kmax, True, seed=9)
+        assert err <= (1e-13 if dt == 0 else 2e-6)
+        assert nb == 1

@@ -96,3 +96,20 @@ def test_shor_invalid(qc):
         qc.qc_project(s.h, 6, 3, 0)  # register beyond n
     with pytest.raises(qc.QCError):
         qc.qc_apply_2q(s.h, 2, 2, np.eye(4, dtype=complex))
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_shor_smallest_modulus(qc, dt):
+    # M = 3, x = 2 (period 2): n1 = 4, n2 = 2
+    M, x = 3, 2
+    n1, n2 = sizes(M)
+    n = n1 + n2
+    s = qc.State(n, dt)
+    qc.qc_shor_prepare(s.h, n2, x, M)
+    ref = O.shor_prepare(n, n2, x, M)
+    assert np.max(np.abs(s.numpy() - ref)) <= TOL[dt]
+    pk = qc.qc_project(s.h, 0, n2, 1)
+    assert abs(pk - O.project(ref, n, 0, n2, 1)) <= (1e-12 if dt == 0 else 1e-6)
+    qc.qc_qft_range(s.h, n2, n1)
+    O.qft_range(ref, n, n2, n1)
+    assert np.max(np.abs(s.numpy() - ref)) <= TOL[dt] * 4
