@@ -213,6 +213,11 @@ qc_status qc_fused_plan_create(int n, const qc_op* ops, int n_ops, int kmax, int
 /* Number of blocks and the block size limit. */
 qc_status qc_fused_plan_info(const qc_fused_plan* p, int* n_blocks, int* kmax);
 
+/* Block i of the plan: its qubit count *k, its qubits (local bit b on
+ * qubits[b]; up to 6 ints) and, if U is not NULL, its operator (2 * 4^k
+ * doubles, row-major, (re, im)).  Host data only. */
+qc_status qc_fused_plan_block(const qc_fused_plan* p, int i, int* k, int* qubits, double* U);
+
 /* Applies the blocks to s (one pass each, qc_apply_dense's kernels).  The
  * packed operators are uploaded on the first run for each dtype (a
  * synchronous copy); a run with tensor-core blocks synchronises the stream

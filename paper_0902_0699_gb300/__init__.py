@@ -105,6 +105,7 @@ _SIGS = {
     "qc_fused_plan_create": [_I, _VP, _I, _I, _I, ctypes.POINTER(_VP)],
     "qc_fused_plan_info": [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "qc_fused_plan_run": [_VP, _VP],
+    "qc_fused_plan_block": [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _DP],
     "qc_fused_plan_free": [_VP],
     "qc_density_matrix": [_VP, _I, _I, _I, _DP, _VP, _VP],
     "qc_mixed_spectrum": [_VP, _I, _I, _I, _DP, _DP, _DP, _VP],
@@ -306,6 +307,16 @@ class FusedPlan:
         nb, km = _I(), _I()
         _check(lib().qc_fused_plan_info(self.h, ctypes.byref(nb), ctypes.byref(km)))
         return nb.value, km.value
+
+    def block(self, i: int):
+        """(qubits, U) of block i."""
+        k = _I()
+        qs = (_I * 6)()
+        _check(lib().qc_fused_plan_block(self.h, i, ctypes.byref(k), qs, None))
+        U = np.zeros(2 << (2 * k.value))
+        _check(lib().qc_fused_plan_block(self.h, i, None, None, _dptr(U)))
+        d = 1 << k.value
+        return [qs[j] for j in range(k.value)], (U[0::2] + 1j * U[1::2]).reshape(d, d)
 
     def run(self, state_h):
         _check(lib().qc_fused_plan_run(state_h, self.h))

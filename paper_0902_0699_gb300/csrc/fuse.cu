@@ -223,6 +223,20 @@ QC_API qc_status qc_fused_plan_info(const qc_fused_plan* p, int* n_blocks, int* 
   return QC_OK;
 }
 
+QC_API qc_status qc_fused_plan_block(const qc_fused_plan* p, int i, int* k, int* qubits, double* U) {
+  clear_error();
+  if (!p || i < 0 || i >= (int)p->blocks.size()) {
+    set_error("qc_fused_plan_block: no block %d", i);
+    return QC_EINVAL;
+  }
+  const FBlock& b = p->blocks[i];
+  if (k) *k = b.k;
+  if (qubits)
+    for (int j = 0; j < b.k; ++j) qubits[j] = b.q[j];
+  if (U) memcpy(U, b.U.data(), sizeof(double) * b.U.size());
+  return QC_OK;
+}
+
 QC_API qc_status qc_fused_plan_run(qc_state* s, qc_fused_plan* p) {
   clear_error();
   qc_status st = check_state(s);

@@ -32,3 +32,21 @@ def test_plan_rejects_bad_operators(qc):
         qc.FusedPlan(4, [(9, 0, 1, 0, None)])
     with pytest.raises(qc.QCError):
         qc.FusedPlan(4, [(3, 0, 1, 0, None)])  # CPHASE needs k >= 1
+
+
+def test_plan_blocks_are_unitary_and_bounded(qc):
+    import workloads as W
+    n, layers = 10, 6
+    circ = W.random_circuit(n, layers, seed=24)
+    ops = []
+    for l in range(layers):
+        for q in range(n):
+            ops.append((1, q, 0, 0, circ.U[l, q]))
+        for (c, t) in circ.cnot_pairs(l):
+            ops.append((2, c, t, 0, None))
+    p = qc.FusedPlan(n, ops, kmax=5, pad=True)
+    nb, km = p.info()
+    for i in range(nb):
+        qs, U = p.block(i)
+        assert len(qs) == 5 and len(set(qs)) == 5 and all(0 <= q < n for q in qs)
+        assert np.max(np.abs(U @ U.conj().T - np.eye(32))) < 1e-13
