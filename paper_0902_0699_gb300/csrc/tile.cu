@@ -144,7 +144,7 @@ template <typename R> struct TileProg {
 // (QFT passes: level j's 2^j ladder phases e^{2 pi i x / 2^{j+1}} at
 // LAD[2^j - 1 + x], so a warp reads consecutive entries), TWA[128], TWB[64].
 #define TS_TWA 128
-#define TS_TWB 64
+#define TS_TWB 128  // x < 2^{c+k} <= 2^14
 
 __device__ __forceinline__ uint64_t tile_global(uint64_t e, uint64_t T, int lo, int k, int c) {
   const uint64_t cm = (1ull << c) - 1ull;
@@ -340,10 +340,13 @@ __global__ void k_roots(typename CT<R>::V2* tlo, typename CT<R>::V2* thi, int n,
 
 // --------------------------------------------------------------------------
 // Tile-size choices: c low contiguous bits give 128-byte rows; k group bits;
-// the tile holds 2^{k+c} amplitudes (64 KiB).
+// the tile holds 2^{k+c} amplitudes (64 KiB complex128, up to 128 KiB
+// complex64: 32 complex64 qubits in three passes, 13 + 10 + 9).
 template <typename R> struct TileCfg;
 template <> struct TileCfg<double> { static constexpr int C = 3, K = 9, BOT = 12; };
-template <> struct TileCfg<float> { static constexpr int C = 4, K = 9, BOT = 12; };
+// complex64: 128 KiB tiles (k = 10, c = 4); the lowest group (c = 0) stops at
+// 13 qubits, where its tile and ladder table take 64 KiB each
+template <> struct TileCfg<float> { static constexpr int C = 4, K = 10, BOT = 13; };
 
 struct Group {
   int lo, k;
