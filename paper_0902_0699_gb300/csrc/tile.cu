@@ -162,6 +162,46 @@ __device__ __forceinline__ typename TA<R>::E omega(const typename CT<R>::V2* __r
   return TA<R>::mul(TA<R>::from(a), TA<R>::from(b));
 }
 
+// QR consecutive QFT levels jtop, jtop-1, .., jtop-QR+1 in one shared-memory
+// round trip: each thread holds the 2^QR elements that differ in the block's
+// bits in registers.  Level j (local bit lv = j - jtop + QR - 1) pairs
+// elements across local bit lv; its ladder phase e^{2 pi i x / 2^{j+1}}
+// uses x = group bits below j = (local bits below lv, placed above the
+// block's lowest group qubit) | (the thread's group bits below the block).
+template <typename R, int QR>
+__device__ __forceinline__ void qft_levels_regs(typename TA<R>::E* sm, int NE, int c, int jtop,
+                                                const typename TA<R>::E* LAD) {
+  using A = TA<R>;
+  using E = typename A::E;
+  constexpr int NR = 1 << QR;
+  const int jlo = jtop - QR + 1;  // the block's lowest group qubit
+  const int bl = c + jlo;         // its index bit
+  for (int p = threadIdx.x; p < (NE >> QR); p += blockDim.x) {
+    const int base = ((p >> bl) << (bl + QR)) | (p & ((1 << bl) - 1));
+    E a[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) a[i] = sm[base | (i << bl)];
+    const int xlow = (base >> c) & ((1 << jlo) - 1);
+#pragma unroll
+    for (int lv = QR - 1; lv >= 0; --lv) {
+      const int j = jlo + lv;
+#pragma unroll
+      for (int i = 0; i < NR; ++i) {
+        if ((i >> lv) & 1) continue;
+        const int i1 = i | (1 << lv);
+        const E s0 = A::add(a[i], a[i1]);
+        E d = A::sub(a[i], a[i1]);
+        const int x = ((i & ((1 << lv) - 1)) << jlo) | xlow;
+        if (x) d = A::mul(LAD[(1 << j) - 1 + x], d);
+        a[i] = s0;
+        a[i1] = d;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NR; ++i) sm[base | (i << bl)] = a[i];
+  }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(512) k_tile(typename CT<R>::V2* __restrict__ s, uint64_t ntiles,
                                               const TileProg<R> P, const typename CT<R>::V2* __restrict__ tlo,
@@ -203,19 +243,56 @@ __global__ void __launch_bounds__(512) k_tile(typename CT<R>::V2* __restrict__ s
     }
     // load: 16-byte vectors; for complex64 two neighbouring elements (c >= 1
     // or a fully contiguous tile, so e and e+1 are neighbours in memory)
+    // eight 16-byte loads in flight per thread before the first shared-memory
+    // store (the tile is read once; with one or two CTAs per SM the load
+    // phase is otherwise latency bound)
+    constexpr int LU = 8;
     if (sizeof(R) == 8) {
-      for (int e = threadIdx.x; e < NE; e += blockDim.x) sm[e] = A::from(s[tile_global(e, T, lo, k, c)]);
+      for (int e0 = threadIdx.x; e0 < NE; e0 += LU * blockDim.x) {
+        V2 v[LU];
+#pragma unroll
+        for (int u = 0; u < LU; ++u) {
+          const int e = e0 + u * blockDim.x;
+          if (e < NE) v[u] = s[tile_global(e, T, lo, k, c)];
+        }
+#pragma unroll
+        for (int u = 0; u < LU; ++u) {
+          const int e = e0 + u * blockDim.x;
+          if (e < NE) sm[e] = A::from(v[u]);
+        }
+      }
     } else {
-      for (int e = 2 * threadIdx.x; e < NE; e += 2 * blockDim.x) {
-        const float4 v = *reinterpret_cast<const float4*>(s + tile_global(e, T, lo, k, c));
-        sm[e] = A::from(CT<R>::make(v.x, v.y));
-        sm[e + 1] = A::from(CT<R>::make(v.z, v.w));
+      for (int e0 = 2 * threadIdx.x; e0 < NE; e0 += 2 * LU * blockDim.x) {
+        float4 v[LU];
+#pragma unroll
+        for (int u = 0; u < LU; ++u) {
+          const int e = e0 + 2 * u * blockDim.x;
+          if (e < NE) v[u] = *reinterpret_cast<const float4*>(s + tile_global(e, T, lo, k, c));
+        }
+#pragma unroll
+        for (int u = 0; u < LU; ++u) {
+          const int e = e0 + 2 * u * blockDim.x;
+          if (e < NE) {
+            sm[e] = A::from(CT<R>::make(v[u].x, v[u].y));
+            sm[e + 1] = A::from(CT<R>::make(v[u].z, v[u].w));
+          }
+        }
       }
     }
     __syncthreads();
     for (int o = 0; o < P.nops; ++o) {
       const int b = c + P.q[o];
       const int kind = P.kind[o];
+      // four descending QFT levels in registers (complex64: the passes are
+      // bound by shared-memory traffic)
+      if (sizeof(R) == 4 && kind == TOP_QFTLEVEL && o + 3 < P.nops && P.kind[o + 1] == kind &&
+          P.kind[o + 2] == kind && P.kind[o + 3] == kind && P.q[o + 1] == P.q[o] - 1 &&
+          P.q[o + 2] == P.q[o] - 2 && P.q[o + 3] == P.q[o] - 3) {
+        qft_levels_regs<R, 4>(sm, NE, c, P.q[o], LAD);
+        __syncthreads();
+        o += 3;
+        continue;
+      }
       // two butterfly levels on neighbouring qubits: one shared-memory round
       // trip (radix 4).  QFT levels come in descending order j, j-1; plain
       // Hadamard butterflies commute, so any neighbouring pair qualifies.
