@@ -550,7 +550,8 @@ qc_status launch_hall(qc_state* s) {
 // bits: rev(h, m, l) = (rev l, rev m, rev h).  The block for middle value m
 // (with m <= rev m) exchanges the 2^b x 2^b tiles of m and rev m through
 // shared memory (rows of 2^b contiguous amplitudes, padded against bank
-// conflicts).
+// conflicts).  Launched with b = 5 and 256 threads (4 elements per thread
+// and tile).
 template <typename R>
 __global__ void __launch_bounds__(256) k_bitrev(typename CT<R>::V2* __restrict__ s, int n, int b) {
   using V2 = typename CT<R>::V2;
@@ -563,10 +564,24 @@ __global__ void __launch_bounds__(256) k_bitrev(typename CT<R>::V2* __restrict__
   for (uint64_t m = blockIdx.x; m < M; m += gridDim.x) {
     const uint64_t mr = nm ? (__brevll((unsigned long long)m) >> (64 - nm)) : 0ull;
     if (mr < m) continue;
-    for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
-      const int h = e >> b, l = e & (W - 1);
-      A[h * WP + l] = s[((uint64_t)h << (n - b)) | (m << b) | (uint64_t)l];
-      if (mr != m) B[h * WP + l] = s[((uint64_t)h << (n - b)) | (mr << b) | (uint64_t)l];
+    // every load of both tiles in flight before the first shared-memory store
+    // (W * W = 4 blockDim.x elements per tile)
+    {
+      V2 va[4], vb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = threadIdx.x + u * blockDim.x;
+        const int h = e >> b, l = e & (W - 1);
+        va[u] = s[((uint64_t)h << (n - b)) | (m << b) | (uint64_t)l];
+        if (mr != m) vb[u] = s[((uint64_t)h << (n - b)) | (mr << b) | (uint64_t)l];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = threadIdx.x + u * blockDim.x;
+        const int h = e >> b, l = e & (W - 1);
+        A[h * WP + l] = va[u];
+        if (mr != m) B[h * WP + l] = vb[u];
+      }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
