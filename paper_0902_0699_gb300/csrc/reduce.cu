@@ -4,9 +4,11 @@
 //
 // Partial sums go to per-block slots in the state's scratch and are added
 // in block order by one final block, so every result is deterministic for a
-// given launch shape.  complex64 squares are formed exactly with the FP32
-// two-product (x*x = p + e, e = fma(x, x, -p)) and accumulated as float
-// pairs over short runs before they are added in FP64.
+// given launch shape.  complex64 squares and products are formed exactly
+// with the FP32 two-product (x*y = p + e, e = fma(x, y, -p)) and summed as
+// float pairs (two-sum) over runs of 32 amplitudes before they are added in
+// FP64: GB300 issues FP64 at about 1/70 of its FP32 rate, which would
+// otherwise bound these passes well below memory bandwidth.
 #include <algorithm>
 #include <cmath>
 
@@ -68,16 +70,99 @@ __device__ __forceinline__ void ff_acc(float& s, float& c, float p, float e) {
   c += err + e;
 }
 
-// ---------------------------------------------------------------- sum ----
+// ------------------------------------------------ Born probabilities ----
+// p_i = re*re + im*im, each product and the sum rounded on its own (the
+// same operations as the FP64 reference; complex64 inputs are widened
+// first, which makes the products exact).
+//
+// GB300 issues FP64 at about 1.6 operations per SM and clock.  For
+// complex64 the exact square of a float (at most 48 significant bits) is
+// assembled as a binary64 from the IEEE-754 fields with integer operations,
+// so one FP64 add per amplitude remains; infinities and NaNs take the FP64
+// formula.  complex128 squares need a rounded 106-bit product, which costs
+// more in integer operations than the FP64 pipe takes for it.
 template <typename R>
-__global__ void __launch_bounds__(RED_T) k_sum(const typename CT<R>::V2* __restrict__ s, uint64_t N,
-                                               double* __restrict__ part) {
+__device__ __forceinline__ double prob_fp64(typename CT<R>::V2 v) {
+  const double re = (double)v.x, im = (double)v.y;
+  return __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
+}
+
+// x*x as an exact binary64 for a finite float x: x = m 2^(f - 150) with the
+// integer significand m < 2^24 (f = 1 for subnormals), x^2 = m^2 2^(2f - 300)
+// with 1 <= L <= 48 significant bits; the biased exponent stays in
+// [725, 1278], always normal.
+__device__ __forceinline__ double sq_exact_f32(uint32_t b) {
+  int f = (int)(b >> 23);
+  uint32_t m = b & 0x7fffffu;
+  if (f) m |= 0x800000u;
+  else if (!m) return 0.0;
+  else f = 1;
+  const uint64_t q = (uint64_t)m * m;  // 32 x 32 -> 64 (a 64-bit multiply runs far slower)
+  const int L = 64 - __clzll((long long)q);
+  const uint64_t sig = q << (53 - L);
+  const uint64_t E = (uint64_t)(2 * f - 300 - (53 - L) + 1075);
+  return __longlong_as_double((long long)((E << 52) | (sig & 0xFFFFFFFFFFFFFull)));
+}
+
+template <typename R>
+__device__ __forceinline__ double prob_of(typename CT<R>::V2 v);
+
+template <>
+__device__ __forceinline__ double prob_of<double>(double2 v) {
+  return prob_fp64<double>(v);
+}
+
+// a call, so that the compiler cannot if-convert the FP64 formula into the
+// common path (every amplitude would then pay for it)
+__device__ __noinline__ double prob_nonfinite_f32(float2 v) { return prob_fp64<float>(v); }
+
+template <>
+__device__ __forceinline__ double prob_of<float>(float2 v) {
+  const uint32_t a = __float_as_uint(v.x) & 0x7fffffffu, b = __float_as_uint(v.y) & 0x7fffffffu;
+  if (a >= 0x7f800000u || b >= 0x7f800000u) return prob_nonfinite_f32(v);  // inf or NaN
+  return __dadd_rn(sq_exact_f32(a), sq_exact_f32(b));
+}
+
+// ---------------------------------------------------------------- sum ----
+__global__ void __launch_bounds__(RED_T) k_sum_c128(const double2* __restrict__ s, uint64_t N,
+                                                    double* __restrict__ part) {
   double a = 0.0, b = 0.0;
   const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += G) {
-    const auto v = s[i];
-    a += (double)v.x;
-    b += (double)v.y;
+    const double2 v = s[i];
+    a += v.x;
+    b += v.y;
+  }
+  block_sum2(a, b);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+  }
+}
+
+// complex64: float-pair runs of RUN vectors (2 RUN amplitudes, every
+// rounding error kept by the two-sum), FP64 across runs; the FP64 pipe sees
+// four operations per run instead of four per amplitude.
+#define RUN 16
+__global__ void __launch_bounds__(RED_T) k_sum_c64(const float4* __restrict__ s, uint64_t N2,
+                                                   double* __restrict__ part) {
+  double a = 0.0, b = 0.0;
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  while (i < N2) {
+    float as = 0.f, ac = 0.f, bs = 0.f, bc = 0.f;
+#pragma unroll 4
+    for (int r = 0; r < RUN; ++r, i += G) {
+      if (i < N2) {
+        const float4 v = s[i];
+        ff_acc(as, ac, v.x, 0.f);
+        ff_acc(as, ac, v.z, 0.f);
+        ff_acc(bs, bc, v.y, 0.f);
+        ff_acc(bs, bc, v.w, 0.f);
+      }
+    }
+    a += (double)as + (double)ac;
+    b += (double)bs + (double)bc;
   }
   block_sum2(a, b);
   if (threadIdx.x == 0) {
@@ -88,12 +173,15 @@ __global__ void __launch_bounds__(RED_T) k_sum(const typename CT<R>::V2* __restr
 
 qc_status launch_sum(qc_state* s) {
   const uint64_t N = 1ull << s->n;
-  const unsigned nb = std::min<unsigned>(grid_for(N, RED_T * 4, 8), RED_MAXB);
   double* part = s->scratch + QC_SCR_PARTIALS;
-  if (s->dt == QC_C128)
-    k_sum<double><<<nb, RED_T, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), N, part);
-  else
-    k_sum<float><<<nb, RED_T, 0, s->stream>>>(reinterpret_cast<const float2*>(s->data), N, part);
+  unsigned nb;
+  if (s->dt == QC_C128) {
+    nb = std::min<unsigned>(grid_for(N, RED_T * 4, 8), RED_MAXB);
+    k_sum_c128<<<nb, RED_T, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), N, part);
+  } else {  // n >= 1: N / 2 >= 1 vectors of two amplitudes
+    nb = std::min<unsigned>(grid_for(N / 2, RED_T * 4, 8), RED_MAXB);
+    k_sum_c64<<<nb, RED_T, 0, s->stream>>>(reinterpret_cast<const float4*>(s->data), N / 2, part);
+  }
   k_final2<<<1, RED_T, 0, s->stream>>>(part, nb, s->scratch + QC_SCR_SUM);
   qc_status st = check_launch("amplitude sum", 2);
   if (!st) s->sum_valid = true;
@@ -118,8 +206,8 @@ __global__ void __launch_bounds__(RED_T) k_norm_c128(const double2* __restrict__
   }
 }
 
-// complex64: exact FP32 squares, float-pair runs of 8 vectors (16 amps),
-// FP64 across runs.
+// complex64: exact FP32 squares, float-pair runs of RUN vectors, FP64
+// across runs.
 __global__ void __launch_bounds__(RED_T) k_norm_c64(const float4* __restrict__ s, uint64_t N2,
                                                     double* __restrict__ part) {
   double acc = 0.0;
@@ -127,14 +215,16 @@ __global__ void __launch_bounds__(RED_T) k_norm_c64(const float4* __restrict__ s
   uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   while (i < N2) {
     float hs = 0.f, hc = 0.f;
-#pragma unroll 1
-    for (int r = 0; r < 8 && i < N2; ++r, i += G) {
-      const float4 v = s[i];
-      const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll 4
+    for (int r = 0; r < RUN; ++r, i += G) {
+      if (i < N2) {
+        const float4 v = s[i];
+        const float x[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float p = x[k] * x[k];
-        ff_acc(hs, hc, p, fmaf(x[k], x[k], -p));
+        for (int k = 0; k < 4; ++k) {
+          const float p = x[k] * x[k];
+          ff_acc(hs, hc, p, fmaf(x[k], x[k], -p));
+        }
       }
     }
     acc += (double)hs + (double)hc;
@@ -170,15 +260,6 @@ qc_status reduce_norm(const qc_state* s, double* out_host) {
 }
 
 // -------------------------------------------------------------- probs ----
-// p_i = re*re + im*im, each product and the sum rounded on its own (the
-// same operations as the FP64 reference; complex64 inputs are widened
-// first, which makes the products exact).
-template <typename R>
-__device__ __forceinline__ double prob_of(typename CT<R>::V2 v) {
-  const double re = (double)v.x, im = (double)v.y;
-  return __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
-}
-
 template <typename R>
 __global__ void __launch_bounds__(RED_T) k_probs(const typename CT<R>::V2* __restrict__ s, uint64_t N,
                                                  double* __restrict__ p) {
@@ -196,41 +277,162 @@ qc_status launch_probs(const qc_state* s, double* out) {
 }
 
 // ------------------------------------------------------------- expect ----
-// <psi|P|psi> = sum_j conj(C[j^x]) i^{|x&z|} (-1)^{|j&z|} C[j].
-template <typename R>
-__global__ void __launch_bounds__(RED_T) k_expect(const typename CT<R>::V2* __restrict__ s, uint64_t N,
-                                                  uint64_t x, uint64_t z, double* __restrict__ part) {
-  double ar = 0.0, ai = 0.0;
+// <psi|P|psi> = i^{|x&z|} h,  h = sum_j conj(C[j^x]) (-1)^{|j&z|} C[j].
+//
+// x = 0: h = sum_j (-1)^{|j&z|} |C_j|^2 (real).  x != 0: with b the lowest
+// set bit of x, the terms of j0 (bit b clear) and j1 = j0 ^ x add up to
+// (-1)^{|j0&z|} (u + sigma conj(u)), u = conj(C[j1]) C[j0], sigma =
+// (-1)^{|x&z|}: 2 Re u when sigma = 1, 2i Im u when sigma = -1.  So every
+// amplitude is read once and a pair costs two real products.
+
+// sign bit of (-1)^{|j&z|} as a 64-bit mask
+__device__ __forceinline__ uint64_t parity_sign(uint64_t j, uint64_t z) {
+  return (uint64_t)(__popcll(j & z) & 1) << 63;
+}
+
+__device__ __forceinline__ double flip(double v, uint64_t sg) {
+  return __longlong_as_double((long long)((uint64_t)__double_as_longlong(v) ^ sg));
+}
+
+__device__ __forceinline__ float flipf(float v, uint64_t sg) {
+  return __uint_as_float(__float_as_uint(v) ^ (uint32_t)(sg >> 32));
+}
+
+// complex128, x = 0: signed |C_j|^2
+__global__ void __launch_bounds__(RED_T) k_expect_diag_c128(const double2* __restrict__ s, uint64_t N, uint64_t z,
+                                                            double* __restrict__ part) {
+  double a = 0.0;
   const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += G) {
-    const auto v = s[j];
-    const auto w = s[j ^ x];
-    double vr = (double)v.x, vi = (double)v.y;
-    if (__popcll(j & z) & 1) {
-      vr = -vr;
-      vi = -vi;
-    }
-    const double wr = (double)w.x, wi = (double)w.y;
-    ar = fma(wr, vr, ar);
-    ar = fma(wi, vi, ar);
-    ai = fma(wr, vi, ai);
-    ai = fma(-wi, vr, ai);
+    const double2 v = s[j];
+    const uint64_t sg = parity_sign(j, z);
+    a = fma(flip(v.x, sg), v.x, a);
+    a = fma(flip(v.y, sg), v.y, a);
   }
-  block_sum2(ar, ai);
+  double b = 0.0;
+  block_sum2(a, b);
   if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = ar;
-    part[2 * blockIdx.x + 1] = ai;
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = 0.0;
+  }
+}
+
+// complex64, x = 0: exact FP32 squares, signed, float-pair runs
+__global__ void __launch_bounds__(RED_T) k_expect_diag_c64(const float4* __restrict__ s, uint64_t N2, uint64_t z,
+                                                           double* __restrict__ part) {
+  double acc = 0.0;
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t z0 = (z & 1ull) << 63;
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  while (i < N2) {
+    float hs = 0.f, hc = 0.f;
+#pragma unroll 4
+    for (int r = 0; r < RUN; ++r, i += G) {
+      if (i < N2) {
+        const float4 v = s[i];
+        const uint64_t s0 = parity_sign(2 * i, z), s1 = s0 ^ z0;
+        const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const uint64_t sg = k < 2 ? s0 : s1;
+          const float p = x[k] * x[k];
+          ff_acc(hs, hc, flipf(p, sg), flipf(fmaf(x[k], x[k], -p), sg));
+        }
+      }
+    }
+    acc += (double)hs + (double)hc;
+  }
+  double b = 0.0;
+  block_sum2(acc, b);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = acc;
+    part[2 * blockIdx.x + 1] = 0.0;
+  }
+}
+
+// complex128, x != 0: sum over pairs of (-1)^{|j0&z|} Re u (IM = false) or
+// Im u (IM = true), u = conj(w) v, v = C[j0], w = C[j0 ^ x]
+template <bool IM>
+__global__ void __launch_bounds__(RED_T) k_expect_pair_c128(const double2* __restrict__ s, uint64_t NP, int b,
+                                                            uint64_t x, uint64_t z, double* __restrict__ part) {
+  double a = 0.0;
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+#pragma unroll 4
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < NP; p += G) {
+    const uint64_t j0 = insert0(p, b);
+    const double2 v = s[j0], w = s[j0 ^ x];
+    const uint64_t sg = parity_sign(j0, z);
+    // Re u = wr vr + wi vi;  Im u = wr vi - wi vr
+    const double c0 = flip(w.x, sg), c1 = flip(IM ? -w.y : w.y, sg);
+    a = fma(c0, IM ? v.y : v.x, a);
+    a = fma(c1, IM ? v.x : v.y, a);
+  }
+  double b2 = 0.0;
+  block_sum2(a, b2);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = 0.0;
+  }
+}
+
+// complex64, x != 0: the two products exactly as float pairs
+// (two-product), float-pair runs, FP64 across runs
+template <bool IM>
+__global__ void __launch_bounds__(RED_T) k_expect_pair_c64(const float2* __restrict__ s, uint64_t NP, int b,
+                                                           uint64_t x, uint64_t z, double* __restrict__ part) {
+  double acc = 0.0;
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  while (p < NP) {
+    float hs = 0.f, hc = 0.f;
+#pragma unroll 4
+    for (int r = 0; r < 2 * RUN; ++r, p += G) {
+      if (p < NP) {
+        const uint64_t j0 = insert0(p, b);
+        const float2 v = s[j0], w = s[j0 ^ x];
+        const uint64_t sg = parity_sign(j0, z);
+        const float c0 = flipf(w.x, sg), c1 = flipf(IM ? -w.y : w.y, sg);
+        const float d0 = IM ? v.y : v.x, d1 = IM ? v.x : v.y;
+        float q = c0 * d0;
+        ff_acc(hs, hc, q, fmaf(c0, d0, -q));
+        q = c1 * d1;
+        ff_acc(hs, hc, q, fmaf(c1, d1, -q));
+      }
+    }
+    acc += (double)hs + (double)hc;
+  }
+  double b2 = 0.0;
+  block_sum2(acc, b2);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = acc;
+    part[2 * blockIdx.x + 1] = 0.0;
   }
 }
 
 qc_status reduce_expect(const qc_state* s, uint64_t x, uint64_t z, double* out_host) {
   const uint64_t N = 1ull << s->n;
   double* part = s->scratch + QC_SCR_PARTIALS;
-  const unsigned nb = std::min<unsigned>(grid_for(N, RED_T * 4, 8), RED_MAXB);
-  if (s->dt == QC_C128)
-    k_expect<double><<<nb, RED_T, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), N, x, z, part);
-  else
-    k_expect<float><<<nb, RED_T, 0, s->stream>>>(reinterpret_cast<const float2*>(s->data), N, x, z, part);
+  const bool c128 = (s->dt == QC_C128);
+  const bool im = x && (__builtin_popcountll(x & z) & 1);  // sigma = -1
+  unsigned nb;
+  if (!x) {
+    if (c128) {
+      nb = std::min<unsigned>(grid_for(N, RED_T * 4, 8), RED_MAXB);
+      k_expect_diag_c128<<<nb, RED_T, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), N, z, part);
+    } else {  // n >= 1: N / 2 >= 1 vectors of two amplitudes
+      nb = std::min<unsigned>(grid_for(N / 2, RED_T * 4, 8), RED_MAXB);
+      k_expect_diag_c64<<<nb, RED_T, 0, s->stream>>>(reinterpret_cast<const float4*>(s->data), N / 2, z, part);
+    }
+  } else {
+    const int b = __builtin_ctzll(x);
+    nb = std::min<unsigned>(grid_for(N / 2, RED_T * 4, 8), RED_MAXB);
+    const double2* d2 = reinterpret_cast<const double2*>(s->data);
+    const float2* f2 = reinterpret_cast<const float2*>(s->data);
+    if (c128 && im) k_expect_pair_c128<true><<<nb, RED_T, 0, s->stream>>>(d2, N / 2, b, x, z, part);
+    else if (c128) k_expect_pair_c128<false><<<nb, RED_T, 0, s->stream>>>(d2, N / 2, b, x, z, part);
+    else if (im) k_expect_pair_c64<true><<<nb, RED_T, 0, s->stream>>>(f2, N / 2, b, x, z, part);
+    else k_expect_pair_c64<false><<<nb, RED_T, 0, s->stream>>>(f2, N / 2, b, x, z, part);
+  }
   k_final2<<<1, RED_T, 0, s->stream>>>(part, nb, s->scratch + QC_SCR_MISC);
   qc_status st = check_launch("expect", 2);
   if (st) return st;
@@ -238,9 +440,10 @@ qc_status reduce_expect(const qc_state* s, uint64_t x, uint64_t z, double* out_h
   cudaError_t e = cudaMemcpyAsync(h, s->scratch + QC_SCR_MISC, sizeof h, cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "expect readback");
-  // multiply by i^{|x&z|}
+  // h from the pair sums (times 2: both members of each pair), then i^{|x&z|}
+  const double r = !x ? h[0] : (im ? 0.0 : 2.0 * h[0]);
+  const double i = !x ? 0.0 : (im ? 2.0 * h[0] : 0.0);
   const int ny = __builtin_popcountll(x & z) & 3;
-  const double r = h[0], i = h[1];
   const double rr[4] = {r, -i, -r, i}, ii[4] = {i, r, -i, -r};
   out_host[0] = rr[ny];
   out_host[1] = ii[ny];
@@ -335,11 +538,12 @@ __device__ __forceinline__ uint64_t thread_weights(const typename CT<R>::V2* __r
   return sum;
 }
 
-// Per-block weight sums; status bits for unusable probabilities.
+// Per-block weight sums (coalesced: the saturating sum does not depend on
+// which thread adds which weight); status bits for unusable probabilities.
 template <typename R>
 __global__ void __launch_bounds__(SMP_T) k_wsum(const typename CT<R>::V2* __restrict__ s, uint64_t N,
                                                 uint64_t* __restrict__ bsum, uint64_t* __restrict__ status) {
-  // coalesced: the sum does not depend on which thread adds which weight
+  __shared__ uint64_t ws[SMP_T / 32];
   const uint64_t base = (uint64_t)blockIdx.x * SMP_BLOCK;
   bool bad = false;
   uint64_t t = 0;
@@ -348,10 +552,23 @@ __global__ void __launch_bounds__(SMP_T) k_wsum(const typename CT<R>::V2* __rest
     const uint64_t i = base + (uint64_t)k * SMP_T + threadIdx.x;
     if (i < N) t = sat_add(t, weight_of<R>(s[i], &bad));
   }
-  uint64_t tot = 0;
-  block_excl_scan_u64(t, &tot);
-  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+  for (int o = 16; o > 0; o >>= 1) t = sat_add(t, __shfl_xor_sync(0xffffffffu, t, o));
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = t;
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr((unsigned long long*)status, SMP_BAD_P);
+  if (threadIdx.x == 0) {
+    uint64_t a = 0;
+    for (int w = 0; w < SMP_T / 32; ++w) a = sat_add(a, ws[w]);
+    bsum[blockIdx.x] = a;
+  }
+}
+
+static void launch_wsum(qc_dtype dt, const void* psi, uint64_t N, uint64_t* bsum, uint64_t* status,
+                        cudaStream_t st) {
+  const unsigned nb = (unsigned)((N + SMP_BLOCK - 1) / SMP_BLOCK);
+  if (dt == QC_C128)
+    k_wsum<double><<<nb, SMP_T, 0, st>>>(reinterpret_cast<const double2*>(psi), N, bsum, status);
+  else
+    k_wsum<float><<<nb, SMP_T, 0, st>>>(reinterpret_cast<const float2*>(psi), N, bsum, status);
 }
 
 // Exclusive scan of the block sums in place (one block); tail[0] receives
@@ -374,6 +591,62 @@ __global__ void __launch_bounds__(1024) k_scan_bsum(uint64_t* __restrict__ bsum,
     if (total == ~0ull) atomicOr((unsigned long long*)status, SMP_OVERFLOW);
   }
 }
+
+// Large block counts: chunks of SCAN_CHUNK block sums; one CTA per chunk
+// sums it (coalesced), the chunk totals take k_scan_bsum, and one CTA per
+// chunk then rewrites its block sums as exclusive offsets.
+#define SCAN_T 256
+#define SCAN_PER 16
+#define SCAN_CHUNK (SCAN_T * SCAN_PER)
+
+__global__ void __launch_bounds__(SCAN_T) k_chunk_sum(const uint64_t* __restrict__ bsum, uint64_t nb,
+                                                      uint64_t* __restrict__ csum) {
+  const uint64_t base = (uint64_t)blockIdx.x * SCAN_CHUNK;
+  uint64_t t = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_PER; ++k) {
+    const uint64_t i = base + (uint64_t)k * SCAN_T + threadIdx.x;
+    if (i < nb) t = sat_add(t, bsum[i]);
+  }
+  uint64_t tot = 0;
+  block_excl_scan_u64(t, &tot);
+  if (threadIdx.x == 0) csum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_chunk_scan(uint64_t* __restrict__ bsum, uint64_t nb,
+                                                       const uint64_t* __restrict__ coff) {
+  const uint64_t base = (uint64_t)blockIdx.x * SCAN_CHUNK + (uint64_t)threadIdx.x * SCAN_PER;
+  uint64_t v[SCAN_PER];
+  uint64_t t = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_PER; ++k) {
+    v[k] = base + k < nb ? bsum[base + k] : 0ull;
+    t = sat_add(t, v[k]);
+  }
+  uint64_t run = coff[blockIdx.x] + block_excl_scan_u64(t, nullptr);
+#pragma unroll
+  for (int k = 0; k < SCAN_PER; ++k) {
+    if (base + k < nb) bsum[base + k] = run;
+    run += v[k];
+  }
+}
+
+// Exclusive offsets of the nb block sums in place, total in tail[0],
+// SMP_OVERFLOW in *status if the total does not fit; csum holds
+// ceil(nb / SCAN_CHUNK) words (unused when nb <= SCAN_CHUNK).
+static void scan_block_sums(uint64_t* bsum, uint64_t nb, uint64_t* csum, uint64_t* tail, uint64_t* status,
+                            cudaStream_t st) {
+  if (nb <= SCAN_CHUNK) {
+    k_scan_bsum<<<1, 1024, 0, st>>>(bsum, nb, tail, status);
+    return;
+  }
+  const uint64_t nc = (nb + SCAN_CHUNK - 1) / SCAN_CHUNK;
+  k_chunk_sum<<<(unsigned)nc, SCAN_T, 0, st>>>(bsum, nb, csum);
+  k_scan_bsum<<<1, 1024, 0, st>>>(csum, nc, tail, status);
+  k_chunk_scan<<<(unsigned)nc, SCAN_T, 0, st>>>(bsum, nb, csum);
+}
+
+static uint64_t scan_words(uint64_t nb) { return nb <= SCAN_CHUNK ? 0 : (nb + SCAN_CHUNK - 1) / SCAN_CHUNK; }
 
 template <typename R>
 __global__ void __launch_bounds__(SMP_T) k_wcdf(const typename CT<R>::V2* __restrict__ s, uint64_t N,
@@ -451,8 +724,8 @@ qc_status launch_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_
   const uint64_t N = 1ull << s->n;
   const uint64_t nb = (N + SMP_BLOCK - 1) / SMP_BLOCK;
   const bool local = (uint64_t)shots <= nb;
-  // [cdf (many shots only)] [block offsets nb] [total] [status]
-  const uint64_t words = (local ? 0 : N) + nb + 2;
+  // [cdf (many shots only)] [block offsets nb] [total] [status] [chunk sums]
+  const uint64_t words = (local ? 0 : N) + nb + 2 + scan_words(nb);
   uint64_t* buf = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&buf, words * sizeof(uint64_t), s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "sampler buffer");
@@ -460,17 +733,15 @@ qc_status launch_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_
   uint64_t* bsum = buf + (local ? 0 : N);
   uint64_t* tail = bsum + nb;
   uint64_t* status = tail + 1;
+  uint64_t* csum = status + 1;
   e = cudaMemsetAsync(status, 0, sizeof(uint64_t), s->stream);
   if (e != cudaSuccess) {
     cudaFreeAsync(buf, s->stream);
     return cuda_fail(e, "sampler status reset");
   }
-  if (s->dt == QC_C128)
-    k_wsum<double><<<(unsigned)nb, SMP_T, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), N, bsum, status);
-  else
-    k_wsum<float><<<(unsigned)nb, SMP_T, 0, s->stream>>>(reinterpret_cast<const float2*>(s->data), N, bsum, status);
-  k_scan_bsum<<<1, 1024, 0, s->stream>>>(bsum, nb, tail, status);
-  qc_status st = check_launch("sample weights", 2);
+  launch_wsum(s->dt, s->data, N, bsum, status, s->stream);
+  scan_block_sums(bsum, nb, csum, tail, status, s->stream);
+  qc_status st = check_launch("sample weights", nb <= SCAN_CHUNK ? 2 : 4);
   uint64_t h[2] = {0, 0};
   if (!st) {
     e = cudaMemcpyAsync(h, tail, sizeof h, cudaMemcpyDeviceToHost, s->stream);
@@ -568,17 +839,12 @@ QC_API qc_status qc_sample_noalloc(const void* psi_dev, int n, qc_dtype dt, uint
   const uint64_t nb = (N + SMP_BLOCK - 1) / SMP_BLOCK;
   e = cudaMemsetAsync(status, 0, sizeof(uint64_t), st);  // the previous call's status is stale
   if (e != cudaSuccess) return cuda_fail(e, "qc_sample_noalloc: status reset");
-  if (dt == QC_C128) {
-    const double2* d = reinterpret_cast<const double2*>(psi_dev);
-    k_wsum<double><<<(unsigned)nb, SMP_T, 0, st>>>(d, N, bsum, status);
-    k_scan_bsum<<<1, 1024, 0, st>>>(bsum, nb, nullptr, status);
-    k_wcdf<double><<<(unsigned)nb, SMP_T, 0, st>>>(d, N, bsum, cdf);
-  } else {
-    const float2* d = reinterpret_cast<const float2*>(psi_dev);
-    k_wsum<float><<<(unsigned)nb, SMP_T, 0, st>>>(d, N, bsum, status);
-    k_scan_bsum<<<1, 1024, 0, st>>>(bsum, nb, nullptr, status);
-    k_wcdf<float><<<(unsigned)nb, SMP_T, 0, st>>>(d, N, bsum, cdf);
-  }
+  launch_wsum(dt, psi_dev, N, bsum, status, st);
+  k_scan_bsum<<<1, 1024, 0, st>>>(bsum, nb, nullptr, status);
+  if (dt == QC_C128)
+    k_wcdf<double><<<(unsigned)nb, SMP_T, 0, st>>>(reinterpret_cast<const double2*>(psi_dev), N, bsum, cdf);
+  else
+    k_wcdf<float><<<(unsigned)nb, SMP_T, 0, st>>>(reinterpret_cast<const float2*>(psi_dev), N, bsum, cdf);
   k_noalloc_total<<<1, 1, 0, st>>>(cdf, N, status);
   qc_status rs = check_launch("qc_sample_noalloc: cdf", 4);
   if (rs) return rs;

@@ -203,7 +203,7 @@ __device__ __forceinline__ void qft_levels_regs(typename TA<R>::E* sm, int NE, i
 }
 
 template <typename R>
-__global__ void __launch_bounds__(512) k_tile(typename CT<R>::V2* __restrict__ s, uint64_t ntiles,
+__global__ void __launch_bounds__(512, sizeof(R) == 8 ? 2 : 1) k_tile(typename CT<R>::V2* __restrict__ s, uint64_t ntiles,
                                               const TileProg<R> P, const typename CT<R>::V2* __restrict__ tlo,
                                               const typename CT<R>::V2* __restrict__ thi) {
   using A = TA<R>;
@@ -243,10 +243,12 @@ __global__ void __launch_bounds__(512) k_tile(typename CT<R>::V2* __restrict__ s
     }
     // load: 16-byte vectors; for complex64 two neighbouring elements (c >= 1
     // or a fully contiguous tile, so e and e+1 are neighbours in memory)
-    // eight 16-byte loads in flight per thread before the first shared-memory
-    // store (the tile is read once; with one or two CTAs per SM the load
-    // phase is otherwise latency bound)
-    constexpr int LU = 8;
+    // several 16-byte loads in flight per thread before the first
+    // shared-memory store (the tile is read once; with one or two CTAs per SM
+    // the load phase is otherwise latency bound).  complex128 keeps two CTAs
+    // per SM (64 registers a thread), so four loads; complex64 runs one CTA
+    // per SM and takes eight.
+    constexpr int LU = sizeof(R) == 8 ? 4 : 8;
     if (sizeof(R) == 8) {
       for (int e0 = threadIdx.x; e0 < NE; e0 += LU * blockDim.x) {
         V2 v[LU];

@@ -204,6 +204,79 @@ def test_reductions(qc, dt, n):
 
 
 @pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n", [1, 2, 7, 14])
+def test_expect_pauli_all_pairings(qc, dt, n):
+    # x = 0 (diagonal), and x != 0 with its lowest set bit anywhere, both
+    # signs of (-1)^{|x&z|} (real or imaginary pair sums), top qubit
+    s, v = mk(qc, n, dt, seed=900 + n)
+    x_ = as_dt(v, dt)
+    g = W.rng(n)
+    N = 1 << n
+    cases = {(0, 0), (0, N - 1), (N - 1, 0), (N - 1, N - 1), (1 << (n - 1), 1 << (n - 1)), (1 << (n - 1), 0)}
+    cases |= {(int(a), int(b)) for a, b in zip(g.integers(0, N, 12), g.integers(0, N, 12))}
+    for xm, zm in sorted(cases):
+        e = s.expect_pauli(xm, zm)
+        ref = O.expect_pauli(x_, n, xm, zm)
+        assert abs(e - ref) <= 1e-12, (xm, zm)
+        assert e.imag == 0.0  # Hermitian Pauli string: exactly real
+
+
+def adversarial_amplitudes(g, N, dt):
+    """Amplitude bit patterns that stress p = re*re + im*im rounded in
+    binary64: short significands (ties when a complex128 square is rounded,
+    ties in the sum for complex64), components many binades apart, exact
+    zeros, subnormal values, and complex128 values on both sides of 2^-500
+    and 2^500."""
+    sign = np.where(g.random((N, 2)) < 0.5, -1.0, 1.0)
+    if dt == 1:
+        e = g.integers(-40, 1, size=(N, 2))
+        e[N // 2:] = g.integers(-149, 2, size=(N - N // 2, 2))
+        x = np.ldexp(g.random((N, 2)) + 1.0, e)
+        short = g.random((N, 2)) < 0.25
+        x[short] = np.ldexp(g.integers(4096, 8192, size=short.sum()).astype(np.float64), -12 + e[short])
+        x[g.random((N, 2)) < 0.1] = 0.0
+        x[:64] = np.ldexp(g.integers(1, 1 << 20, size=(64, 2)).astype(np.float64), -149)  # subnormal
+        x = (x * sign).astype(np.float32).astype(np.float64)
+    else:
+        e = g.integers(-60, 2, size=(N, 2))
+        e[: N // 4] = g.integers(-560, 540, size=(N // 4, 2))
+        x = np.ldexp(g.random((N, 2)) + 1.0, e)
+        # x = M 2^-k with odd M > 2^26.5: the square's 106-bit significand
+        # product rounds at an exact tie
+        short = g.random((N, 2)) < 0.25
+        M = 2 * g.integers(47453133, 1 << 26, size=short.sum()) + 1
+        x[short] = np.ldexp(M.astype(np.float64), -27 - g.integers(0, 30, size=short.sum()))
+        x[g.random((N, 2)) < 0.1] = 0.0
+        x[:8] = [[2.0 ** -500, 2.0 ** -501], [2.0 ** 500, 0.0], [2.0 ** -1074, 1.0], [2.0 ** -1022, 2.0 ** -600],
+                 [np.nextafter(2.0 ** -500, 0.0), 0.5], [2.0 ** 501, 0.0], [0.0, 0.0], [1.0, 1.0]]
+        x = x * sign
+    return x[:, 0] + 1j * x[:, 1]
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_probs_and_weights_adversarial_bits(qc, dt):
+    # the probabilities are formed from the IEEE fields with integer
+    # operations: every value must equal binary64 re*re + im*im bit for bit,
+    # and the sampler's integer weights must follow them
+    n = 14
+    g = W.rng(4242 + dt)
+    v = adversarial_amplitudes(g, 1 << n, dt)
+    s, _ = mk(qc, n, dt, vec=v)
+    p = s.probs().cpu().numpy()
+    pr = O.probs(as_dt(v, dt), n)
+    assert np.array_equal(p.view(np.uint64), pr.view(np.uint64))
+    # a power-of-two scale keeps every significand: total probability <= 1
+    q = np.where(np.abs(v) < 2.0 ** 100, v, 0.0)
+    q = q * 2.0 ** -math.ceil(0.5 * math.log2(np.sum(np.abs(q) ** 2)))
+    s2, _ = mk(qc, n, dt, vec=q)
+    pq = O.probs(as_dt(q, dt), n)
+    assert np.sum(pq) <= 1.0
+    for shots in (3, 50):
+        got = s2.sample(91, shots).cpu().numpy().astype(np.uint64)
+        assert np.array_equal(got, O.sample_from_probs(pq, 91, shots))
+
+
+@pytest.mark.parametrize("dt", [0, 1])
 @pytest.mark.parametrize("n", [1, 3, 12, 15])
 def test_sample_bit_exact(qc, dt, n):
     s, v = mk(qc, n, dt, seed=n + 11)
@@ -224,6 +297,21 @@ def test_sample_block_local_and_cdf_paths(qc, dt, n, shots):
     for seed in (3, 2 ** 33 + 1):
         got = s.sample(seed, shots).cpu().numpy().astype(np.uint64)
         assert np.array_equal(got, O.sample_from_probs(p, seed, shots))
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_sample_chunked_block_scan(qc, dt):
+    # 2^24 amplitudes: 8192 block sums, scanned in two chunks of 4096
+    n = 24
+    g = W.rng(24 + dt)
+    v = (g.standard_normal(1 << n) + 1j * g.standard_normal(1 << n)) * np.exp(-np.arange(1 << n) / 2.0 ** 22)
+    v /= np.linalg.norm(v)
+    s, _ = mk(qc, n, dt, vec=v)
+    pr = O.probs(as_dt(v, dt), n)
+    assert np.array_equal(s.probs().cpu().numpy(), pr)
+    for shots in (5, 8193):  # block-local rescans, then the full integer CDF
+        got = s.sample(2 ** 35 + 9, shots).cpu().numpy().astype(np.uint64)
+        assert np.array_equal(got, O.sample_from_probs(pr, 2 ** 35 + 9, shots))
 
 
 @pytest.mark.parametrize("shots", [4, 64])
