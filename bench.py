@@ -315,8 +315,9 @@ def run_ours(args, ws, rank, local):
 def qft_bytes(n, amp):
     """Algorithmic bytes of the QFT as built: one read+write pass per tile
     group plus the bit-reversal pass."""
-    C, K = (3, 9) if amp == 16 else (4, 9)
-    g0 = min(n, C + K)
+    # lowest group up to BOT qubits, the others up to K (csrc/tile.cu TileCfg)
+    BOT, K = (12, 9) if amp == 16 else (13, 10)
+    g0 = min(n, BOT)
     rest = n - g0
     passes = 1 + (-(-rest // K) if rest > 0 else 0)
     return (passes + 1) * 2 * (1 << n) * amp

@@ -202,8 +202,11 @@ __device__ __forceinline__ void qft_levels_regs(typename TA<R>::E* sm, int NE, i
   }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(512, sizeof(R) == 8 ? 2 : 1) k_tile(typename CT<R>::V2* __restrict__ s, uint64_t ntiles,
+// QREG: complex64 QFT programs apply four levels at a time in registers
+// (127 registers a thread, one CTA per SM); every other program keeps two
+// CTAs per SM (64 registers), which small tiles need to hide latency.
+template <typename R, bool QREG>
+__global__ void __launch_bounds__(512, QREG ? 1 : 2) k_tile(typename CT<R>::V2* __restrict__ s, uint64_t ntiles,
                                               const TileProg<R> P, const typename CT<R>::V2* __restrict__ tlo,
                                               const typename CT<R>::V2* __restrict__ thi) {
   using A = TA<R>;
@@ -245,10 +248,9 @@ __global__ void __launch_bounds__(512, sizeof(R) == 8 ? 2 : 1) k_tile(typename C
     // or a fully contiguous tile, so e and e+1 are neighbours in memory)
     // several 16-byte loads in flight per thread before the first
     // shared-memory store (the tile is read once; with one or two CTAs per SM
-    // the load phase is otherwise latency bound).  complex128 keeps two CTAs
-    // per SM (64 registers a thread), so four loads; complex64 runs one CTA
-    // per SM and takes eight.
-    constexpr int LU = sizeof(R) == 8 ? 4 : 8;
+    // the load phase is otherwise latency bound): four within the
+    // 64-register budget, eight at one CTA per SM.
+    constexpr int LU = QREG ? 8 : 4;
     if (sizeof(R) == 8) {
       for (int e0 = threadIdx.x; e0 < NE; e0 += LU * blockDim.x) {
         V2 v[LU];
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(512, sizeof(R) == 8 ? 2 : 1) k_tile(typename C
       const int kind = P.kind[o];
       // four descending QFT levels in registers (complex64: the passes are
       // bound by shared-memory traffic)
-      if (sizeof(R) == 4 && kind == TOP_QFTLEVEL && o + 3 < P.nops && P.kind[o + 1] == kind &&
+      if (QREG && kind == TOP_QFTLEVEL && o + 3 < P.nops && P.kind[o + 1] == kind &&
           P.kind[o + 2] == kind && P.kind[o + 3] == kind && P.q[o + 1] == P.q[o] - 1 &&
           P.q[o + 2] == P.q[o] - 2 && P.q[o + 3] == P.q[o] - 3) {
         qft_levels_regs<R, 4>(sm, NE, c, P.q[o], LAD);
@@ -470,24 +472,47 @@ static qc_status run_tile(qc_state* s, TileProg<R>& P, const typename CT<R>::V2*
   const int tb = P.k + P.c;
   const uint64_t ntiles = 1ull << (s->n - tb);
   const size_t smem = tile_smem<R>(P.k, P.c, P.twiddle != 0, P.qft != 0);
+  constexpr int threads = 512;
+  if constexpr (sizeof(R) == 4) {
+    if (P.qft) {
+      static bool attr_q = false;
+      if (!attr_q) {
+        cudaFuncSetAttribute(k_tile<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_q = true;
+      }
+      const unsigned grid = resident_grid(k_tile<R, true>, threads, (int64_t)ntiles, 1, smem);
+      k_tile<R, true><<<grid, threads, smem, s->stream>>>(reinterpret_cast<V2*>(s->data), ntiles, P, tlo, thi);
+      return check_launch("tile pass");
+    }
+  }
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_tile<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_tile<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  const int threads = 512;
-  const unsigned grid = resident_grid(k_tile<R>, threads, (int64_t)ntiles, 1, smem);
-  k_tile<R><<<grid, threads, smem, s->stream>>>(reinterpret_cast<V2*>(s->data), ntiles, P, tlo, thi);
+  const unsigned grid = resident_grid(k_tile<R, false>, threads, (int64_t)ntiles, 1, smem);
+  k_tile<R, false><<<grid, threads, smem, s->stream>>>(reinterpret_cast<V2*>(s->data), ntiles, P, tlo, thi);
   return check_launch("tile pass");
 }
 
+// Contiguous low bits of a group's tile: at least C (128-byte rows) and, for
+// small groups, enough to fill the tile to 2^TB amplitudes, so that a pass
+// has few large tiles with long rows rather than many small ones (each tile
+// costs a DRAM round trip before its compute).  TB: 64 KiB tiles (two CTAs
+// per SM), 128 KiB for the complex64 QFT kernel (one CTA per SM).  The QFT
+// twiddle tables need c + k <= 14.
 template <typename R>
-static void prog_init(TileProg<R>& P, const Group& g, int n) {
-  const int C = TileCfg<R>::C;
+static int tile_c(const Group& g, bool qreg) {
+  const int TB = sizeof(R) == 8 ? 12 : (qreg ? 14 : 13);
+  return std::min(g.lo, std::max(TileCfg<R>::C, TB - g.k));
+}
+
+template <typename R>
+static void prog_init(TileProg<R>& P, const Group& g, int n, bool qreg = false) {
   P.nops = 0;
   P.lo = g.lo;
   P.k = g.k;
-  P.c = std::min(C, g.lo);
+  P.c = tile_c<R>(g, qreg);
   P.n = n;
   P.twiddle = 0;
   P.qft = 0;
@@ -653,7 +678,7 @@ static qc_status qft_impl(qc_state* s) {
   for (int gi = (int)groups.size() - 1; gi >= 0 && !st; --gi) {
     const Group& g = groups[gi];
     TileProg<R> P;
-    prog_init(P, g, n);
+    prog_init(P, g, n, sizeof(R) == 4);  // complex64 QFT passes run the one-CTA kernel
     P.nl = nl;
     P.qft = 1;
     for (int j = g.k - 1; j >= 0; --j) {
