@@ -30,15 +30,20 @@ __device__ __forceinline__ uint64_t group_base(uint64_t g, const DenseMap& M) {
 }
 
 // ------------------------------------------------------ CUDA cores -------
-// A CTA stages DENSE_GROUPS groups in shared memory, then every thread
-// forms outputs sum_l' U[l][l'] x[l'] with U in shared memory.
-#define DENSE_GROUPS 16
+// A CTA stages DENSE_AMPS amplitudes (DENSE_AMPS / 2^k groups) in shared
+// memory, with all DENSE_PER loads of a thread in flight before its first
+// shared-memory store, then every thread forms outputs
+// sum_l' U[l][l'] x[l'] with U in shared memory.
+#define DENSE_T 256
+#define DENSE_AMPS 2048
+#define DENSE_PER (DENSE_AMPS / DENSE_T)
 
 template <typename R> struct DenseT;
 template <> struct DenseT<float> {
   typedef float2 V;
   typedef float2 S;  // shared-memory element
   static __device__ __forceinline__ S load(const V* p, uint64_t i) { return p[i]; }
+  static __device__ __forceinline__ S cvt(const V& v) { return v; }
   static __device__ __forceinline__ void store(V* p, uint64_t i, const S& z) { p[i] = z; }
   static __device__ __forceinline__ S zero() { return make_float2(0.f, 0.f); }
   static __device__ __forceinline__ void mac(S& acc, const S& u, const S& x) {
@@ -50,10 +55,8 @@ template <> struct DenseT<float> {
 template <> struct DenseT<double> {
   typedef double2 V;
   typedef ffc S;
-  static __device__ __forceinline__ S load(const V* p, uint64_t i) {
-    const double2 v = p[i];
-    return ffc_make(ff_from_d(v.x), ff_from_d(v.y));
-  }
+  static __device__ __forceinline__ S cvt(const V& v) { return ffc_make(ff_from_d(v.x), ff_from_d(v.y)); }
+  static __device__ __forceinline__ S load(const V* p, uint64_t i) { return cvt(p[i]); }
   static __device__ __forceinline__ void store(V* p, uint64_t i, const S& z) {
     p[i] = make_double2(ff_to_d(z.re), ff_to_d(z.im));
   }
@@ -65,9 +68,9 @@ template <> struct DenseT<double> {
   static __device__ __forceinline__ S from_d(double re, double im) { return ffc_make(ff_from_d(re), ff_from_d(im)); }
 };
 
-// dynamic shared memory: U (4^k elements) then X (DENSE_GROUPS * 2^k)
+// dynamic shared memory: U (4^k elements) then X (DENSE_AMPS)
 template <typename R>
-__global__ void __launch_bounds__(256) k_dense(typename DenseT<R>::V* __restrict__ psi, uint64_t ngroups,
+__global__ void __launch_bounds__(DENSE_T) k_dense(typename DenseT<R>::V* __restrict__ psi, uint64_t ngroups,
                                                const double* __restrict__ U, DenseMap M) {
   typedef DenseT<R> D;
   typedef typename D::S S;
@@ -81,12 +84,21 @@ __global__ void __launch_bounds__(256) k_dense(typename DenseT<R>::V* __restrict
     const int l = e / dim, lp = e % dim;
     Us[lp * dim + l] = D::from_d(U[2 * e], U[2 * e + 1]);
   }
-  for (uint64_t g0 = (uint64_t)blockIdx.x * DENSE_GROUPS; g0 < ngroups; g0 += (uint64_t)gridDim.x * DENSE_GROUPS) {
-    const int ng = (int)min((uint64_t)DENSE_GROUPS, ngroups - g0);
+  const int G = DENSE_AMPS >> M.k;  // groups per iteration (k <= 6: at least 32)
+  for (uint64_t g0 = (uint64_t)blockIdx.x * G; g0 < ngroups; g0 += (uint64_t)gridDim.x * G) {
+    const int ng = (int)min((uint64_t)G, ngroups - g0);
     __syncthreads();  // U staged; the previous groups' outputs are written
-    for (int e = threadIdx.x; e < ng * dim; e += blockDim.x) {
+    typename D::V v[DENSE_PER];
+#pragma unroll
+    for (int u = 0; u < DENSE_PER; ++u) {
+      const int e = threadIdx.x + u * DENSE_T;
       const int gi = e >> M.k, l = e & (dim - 1);
-      X[e] = D::load(psi, group_base(g0 + gi, M) | M.offs[l]);
+      if (gi < ng) v[u] = psi[group_base(g0 + gi, M) | M.offs[l]];
+    }
+#pragma unroll
+    for (int u = 0; u < DENSE_PER; ++u) {
+      const int e = threadIdx.x + u * DENSE_T;
+      if ((e >> M.k) < ng) X[e] = D::cvt(v[u]);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < ng * dim; e += blockDim.x) {
@@ -428,28 +440,28 @@ qc_status dense_launch(qc_state* s, const DenseMap& M, const void* dev_op, int* 
                                                      reinterpret_cast<const float*>(dev_op),
                                                      reinterpret_cast<const float*>(dev_op) + TC_N * TC_K, M, status);
   } else if (s->dt == QC_C64) {
-    const size_t smem = sizeof(float2) * ((size_t)dim * dim + (size_t)DENSE_GROUPS * dim);
+    const size_t smem = sizeof(float2) * ((size_t)dim * dim + DENSE_AMPS);
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(k_dense<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(float2) * (64 * 64 + DENSE_GROUPS * 64)));
+                           (int)(sizeof(float2) * (64 * 64 + DENSE_AMPS)));
       attr = true;
     }
-    const unsigned grid =
-        (unsigned)std::min<uint64_t>((ngroups + DENSE_GROUPS - 1) / DENSE_GROUPS, (uint64_t)sm_count() * 4);
-    k_dense<float><<<grid, 256, smem, s->stream>>>(reinterpret_cast<float2*>(s->data), ngroups,
+    const uint64_t G = DENSE_AMPS >> M.k;
+    const unsigned grid = resident_grid(k_dense<float>, DENSE_T, (int64_t)((ngroups + G - 1) / G), 1, smem);
+    k_dense<float><<<grid, DENSE_T, smem, s->stream>>>(reinterpret_cast<float2*>(s->data), ngroups,
                                                     reinterpret_cast<const double*>(dev_op), M);
   } else {
-    const size_t smem = sizeof(ffc) * ((size_t)dim * dim + (size_t)DENSE_GROUPS * dim);
+    const size_t smem = sizeof(ffc) * ((size_t)dim * dim + DENSE_AMPS);
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(k_dense<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(ffc) * (64 * 64 + DENSE_GROUPS * 64)));
+                           (int)(sizeof(ffc) * (64 * 64 + DENSE_AMPS)));
       attr = true;
     }
-    const unsigned grid =
-        (unsigned)std::min<uint64_t>((ngroups + DENSE_GROUPS - 1) / DENSE_GROUPS, (uint64_t)sm_count() * 4);
-    k_dense<double><<<grid, 256, smem, s->stream>>>(reinterpret_cast<double2*>(s->data), ngroups,
+    const uint64_t G = DENSE_AMPS >> M.k;
+    const unsigned grid = resident_grid(k_dense<double>, DENSE_T, (int64_t)((ngroups + G - 1) / G), 1, smem);
+    k_dense<double><<<grid, DENSE_T, smem, s->stream>>>(reinterpret_cast<double2*>(s->data), ngroups,
                                                      reinterpret_cast<const double*>(dev_op), M);
   }
   s->sum_valid = false;
