@@ -419,7 +419,9 @@ __device__ __forceinline__ unsigned long long sqw(float x) {
 // Read-out weight of amplitude v: trunc(re^2 2^62) + trunc(im^2 2^62).
 __device__ __forceinline__ unsigned long long ro_weight(float2 v) { return sqw(v.x) + sqw(v.y); }
 
-// Iterations per table of error draws (shared memory: 12 KiB).
+// Iterations per table of error draws (shared memory: 12 KiB).  The
+// dirty-iteration bitmask is written by threads 0..TCH-1, so a CTA has at
+// least TCH threads (the plan's shapes use 256 or 512).
 #define TCH 256
 
 // MINB = resident CTAs per SM the register budget is sized for (the plan's
@@ -788,6 +790,10 @@ typedef void (*TrajKernel)(TrajParams);
 static TrajKernel traj_kernel(int minb) { return minb == 1 ? k_traj<1> : k_traj<2>; }
 
 static qc_status traj_launch(qc_traj_plan* p, int G, int T, int grid, int minb, const TrajParams& prm) {
+  if (T < TCH || T > 512 || T % 32) {  // the kernel's tables assume TCH <= T <= 512
+    set_error("trajectory launch: %d threads per CTA (need %d..512, a multiple of 32)", T, TCH);
+    return QC_EINVAL;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(T);
@@ -924,8 +930,13 @@ QC_API qc_status qc_traj_plan_create(const qc_traj_desc* d, void* stream, int au
   for (auto& c : cands)
     if (c.T == 512 && c.G >= best.G) best = c;
   if (autotune && cands.size() > 1) {
-    // time each shape on an evenly spaced sample of the cost-sorted list
-    const int stride = std::max(1, d->n_inst / 32);
+    // time each shape on an evenly spaced sample of the cost-sorted list,
+    // large enough to fill every candidate's co-resident clusters four times
+    // over: the run's time is a throughput, and a sample of a few instances
+    // would only measure the latency of the largest ones (which favours wide
+    // clusters that leave SMs idle)
+    const int want = std::max(32, 4 * maxc);
+    const int stride = std::max(1, d->n_inst / want);
     std::vector<TrajInst> samp;
     for (int i = 0; i < d->n_inst; i += stride) {
       TrajInst t = h[i];
