@@ -165,6 +165,16 @@ FF_HD void two_sum(float a, float b, float& s, float& e) {
   e = ff_add_rn(ff_sub_rn(a, ff_sub_rn(s, v)), ff_sub_rn(b, v));
 }
 
+// Dekker fast two-sum: s + e == a + b exactly when |a| >= |b| (or a == 0).
+// Used for the final renormalisation of a result whose high part dominates;
+// where cancellation leaves it smaller, the error stays at the level of the
+// low part (about 2^-48 of the operands), which absolute amplitude errors
+// tolerate.
+FF_HD void fast_two_sum(float a, float b, float& s, float& e) {
+  s = ff_add_rn(a, b);
+  e = ff_sub_rn(b, ff_sub_rn(s, a));
+}
+
 FF_HD ff ff_make(float hi, float lo) {
   ff r;
   r.hi = hi;
@@ -177,7 +187,7 @@ FF_HD ff ff_add(ff a, ff b) {
   two_sum(a.hi, b.hi, s, e);
   e = ff_add_rn(e, ff_add_rn(a.lo, b.lo));
   float h, l;
-  two_sum(s, e, h, l);
+  fast_two_sum(s, e, h, l);
   return ff_make(h, l);
 }
 FF_HD ff ff_neg(ff a) { return ff_make(-a.hi, -a.lo); }
@@ -189,7 +199,7 @@ FF_HD ff ff_mul(ff a, ff b) {
   e = ff_fma(a.hi, b.lo, e);
   e = ff_fma(a.lo, b.hi, e);
   float h, l;
-  two_sum(p, e, h, l);
+  fast_two_sum(p, e, h, l);  // |e| <= ulp(p): exact
   return ff_make(h, l);
 }
 
@@ -207,7 +217,7 @@ FF_HD ff ff_dot2m(ff a, ff b, ff c, ff d) {
   t = ff_fma(-c.hi, d.lo, t);
   t = ff_fma(-c.lo, d.hi, t);
   float h, l;
-  two_sum(s, t, h, l);
+  fast_two_sum(s, t, h, l);
   return ff_make(h, l);
 }
 // a*b + c*d
