@@ -176,55 +176,96 @@ qc_status launch_grover_step(qc_state* s, const uint64_t* marked, int m) {
 
 // ---------------------------------------------------- whole small run ----
 // HALL|0..0> followed by `iters` Grover steps, one block, state in shared
-// memory.  The mean is recomputed from the amplitudes every step (FP64).
+// memory.  The mean is recomputed from the amplitudes every step.  One SM
+// completes about 1.6 FP64 operations per clock, which would bound every
+// step (a block-wide FP64 sum and an FP64 diffusion), so the run stays on
+// the FP32 pipe: complex128 keeps the state as double-float (about 48
+// bits) from the first to the last step, complex64 sums in float pairs.
+template <typename R> struct SmallRun;
+template <> struct SmallRun<double> {
+  using E = ffc;
+  __device__ static E start(double a) { return ffc_make(ff_from_d(a), ff_make(0.f, 0.f)); }
+  __device__ static double2 out(E z) { return make_double2(ff_to_d(z.re), ff_to_d(z.im)); }
+  __device__ static E neg(E z) { return ffc_make(ff_neg(z.re), ff_neg(z.im)); }
+  __device__ static ff re(E z) { return z.re; }
+  __device__ static ff im(E z) { return z.im; }
+  // 2m = S 2^{1-n} (an exact power-of-two scaling of the double-float sum)
+  __device__ static E two_mean(ff sr, ff si, float scale) {
+    return ffc_make(ff_make(sr.hi * scale, sr.lo * scale), ff_make(si.hi * scale, si.lo * scale));
+  }
+  __device__ static E diffuse(E t2, E z) { return ffc_sub(t2, z); }
+};
+template <> struct SmallRun<float> {
+  using E = Cx<float>;
+  __device__ static E start(double a) { return cmake<float>((float)a, 0.f); }
+  __device__ static float2 out(E z) { return make_float2(z.re, z.im); }
+  __device__ static E neg(E z) { return cmake<float>(-z.re, -z.im); }
+  __device__ static ff re(E z) { return ff_make(z.re, 0.f); }
+  __device__ static ff im(E z) { return ff_make(z.im, 0.f); }
+  __device__ static E two_mean(ff sr, ff si, float scale) {
+    return cmake<float>((sr.hi + sr.lo) * scale, (si.hi + si.lo) * scale);
+  }
+  __device__ static E diffuse(E t2, E z) { return cmake<float>(t2.re - z.re, t2.im - z.im); }
+};
+
+__device__ __forceinline__ ff shfl_xor_ff(ff v, int o) {
+  return ff_make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+
 template <typename R>
 __global__ void __launch_bounds__(1024) k_grover_small(typename CT<R>::V2* __restrict__ s, int n,
                                                        const MarkedList* __restrict__ ML, int iters) {
+  using G = SmallRun<R>;
+  using E = typename G::E;
   extern __shared__ __align__(16) unsigned char smraw[];
-  Cx<R>* sm = reinterpret_cast<Cx<R>*>(smraw);
-  __shared__ double red[2][32];
-  __shared__ double mean[2];
+  E* sm = reinterpret_cast<E*>(smraw);
+  __shared__ ff red[2][32];
+  __shared__ E t2s;
   const int N = 1 << n;
-  const R a = (R)(1.0 / sqrt(ldexp(1.0, n)));
-  for (int i = threadIdx.x; i < N; i += blockDim.x) sm[i] = cmake<R>(a, (R)0);
+  const float scale = ldexpf(1.f, 1 - n);  // 2 / N, exact
+  const E a = G::start(1.0 / sqrt(ldexp(1.0, n)));
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sm[i] = a;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const ff zero = ff_make(0.f, 0.f);
   for (int it = 0; it < iters; ++it) {
     // oracle (Eq. oracle1)
     for (int i = threadIdx.x; i < ML->m; i += blockDim.x) {
       const uint64_t j = ML->idx[i];
-      sm[j] = cmake<R>(-sm[j].re, -sm[j].im);
+      sm[j] = G::neg(sm[j]);
     }
     __syncthreads();
-    double ar = 0.0, ai = 0.0;
+    // amplitude sum in double-float: per thread, across the warp, across warps
+    ff sr = zero, si = zero;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-      ar += (double)sm[i].re;
-      ai += (double)sm[i].im;
+      const E z = sm[i];
+      sr = ff_add(sr, G::re(z));
+      si = ff_add(si, G::im(z));
     }
     for (int o = 16; o > 0; o >>= 1) {
-      ar += __shfl_xor_sync(0xffffffffu, ar, o);
-      ai += __shfl_xor_sync(0xffffffffu, ai, o);
+      sr = ff_add(sr, shfl_xor_ff(sr, o));
+      si = ff_add(si, shfl_xor_ff(si, o));
     }
     if (lane == 0) {
-      red[0][warp] = ar;
-      red[1][warp] = ai;
+      red[0][warp] = sr;
+      red[1][warp] = si;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double tr = 0.0, ti = 0.0;
-      for (int w = 0; w < nw; ++w) {
-        tr += red[0][w];
-        ti += red[1][w];
+    if (warp == 0) {
+      ff r = lane < nw ? red[0][lane] : zero, q = lane < nw ? red[1][lane] : zero;
+      for (int o = 16; o > 0; o >>= 1) {
+        r = ff_add(r, shfl_xor_ff(r, o));
+        q = ff_add(q, shfl_xor_ff(q, o));
       }
-      mean[0] = tr / (double)N;
-      mean[1] = ti / (double)N;
+      if (lane == 0) t2s = G::two_mean(r, q, scale);
     }
     __syncthreads();
-    const R t2r = (R)(2.0 * mean[0]), t2i = (R)(2.0 * mean[1]);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) sm[i] = cmake<R>(t2r - sm[i].re, t2i - sm[i].im);
+    // diffusion: C -> 2m - C (HALL . Inv . HALL)
+    const E t2 = t2s;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) sm[i] = G::diffuse(t2, sm[i]);
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < N; i += blockDim.x) s[i] = CT<R>::make(sm[i].re, sm[i].im);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) s[i] = G::out(sm[i]);
 }
 
 qc_status launch_grover_run(qc_state* s, const uint64_t* marked, int m, int iters) {
