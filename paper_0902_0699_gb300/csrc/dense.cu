@@ -19,6 +19,9 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 
 namespace qc {
@@ -191,7 +194,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 // status: set to 1 if an mbarrier wait ran out (the kernel then stops).
 __global__ void __launch_bounds__(TC_T, 2) k_dense_tc(float2* __restrict__ psi, uint64_t ngroups,
                                                    const float* __restrict__ Wt_hi, const float* __restrict__ Wt_lo,
-                                                   DenseMap M, int* __restrict__ status) {
+                                                   DenseMap M, int* __restrict__ status,
+                                                   const __grid_constant__ CUtensorMap out_map, int use_tma) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   unsigned char* A_hi = tsm;
   unsigned char* A_lo = tsm + TC_A_BYTES;
@@ -268,9 +272,14 @@ __global__ void __launch_bounds__(TC_T, 2) k_dense_tc(float2* __restrict__ psi, 
     }
   };
   // one tile: stage R, MMAs, refill R with tile + 2 grid, epilogue
+  const bool tma_out = contig && use_tma;
   auto body = [&](uint64_t tile, float4 (&R)[8], bool& rlive, uint64_t& rbase) -> bool {
     const bool live = rlive;
     const uint64_t base = rbase;
+    if (tma_out) {  // the previous tile's output store has read A_hi
+      if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+      __syncthreads();
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {  // two amplitudes (4 reals) per core-matrix row
       const float4 v = R[i];
@@ -314,7 +323,29 @@ __global__ void __launch_bounds__(TC_T, 2) k_dense_tc(float2* __restrict__ psi, 
     float out[32];
     tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 32 * hf, out);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    if (contig) {  // rows through shared memory (A_hi is free: the MMAs are done)
+    if (tma_out) {
+      // rows into two 128 x 32-float boxes (A_hi is free: the MMAs are done)
+      // in the tensor map's 128-byte swizzle (16-byte chunk c of row r at
+      // chunk c ^ (r & 7), so a warp's 32 rows hit every bank), then one
+      // tensor store per box writes them back as plain rows (rows past the
+      // state are clipped by the map)
+      unsigned char* box = A_hi + hf * (TC_M * 128);
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        *reinterpret_cast<float4*>(box + row * 128 + ((j ^ (row & 7)) << 4)) =
+            make_float4(out[4 * j], out[4 * j + 1], out[4 * j + 2], out[4 * j + 3]);
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
+                           reinterpret_cast<uint64_t>(&out_map)),
+                       "r"(32 * h), "r"((int)(tile * TC_M)), "r"(a_hi + (uint32_t)(h * TC_M * 128))
+                       : "memory");
+        asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+      }
+    } else if (contig) {  // rows through shared memory (A_hi is free: the MMAs are done)
 #pragma unroll
       for (int l4 = 0; l4 < 8; ++l4)
         *reinterpret_cast<float4*>(A_hi + canon_off(row, 4 * (8 * hf + l4))) =
@@ -345,6 +376,8 @@ __global__ void __launch_bounds__(TC_T, 2) k_dense_tc(float2* __restrict__ psi, 
   }
   // an MMA that a timed-out wait left in flight: one more bounded wait
   if (stop && tid == 0) mbar_wait(mbar_a, phase ^ 1u);
+  // output stores in flight finish before the CTA (and its shared memory) ends
+  if (tma_out && tid == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;\n" ::"r"(tmem));
@@ -422,6 +455,40 @@ void dense_pack(qc_dtype dt, int k, const double* U, void* host_out) {
     }
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (looked up
+// once; null if the driver does not provide it).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    looked = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// The state as a 2-D float tensor of 64-float rows (one group of 32
+// amplitudes each), stored back by boxes of 128 rows x 32 floats with the
+// 128-byte swizzle; false if it cannot be encoded (the kernel then stages
+// its output through shared memory with ordinary stores).
+static bool dense_out_map(const qc_state* s, uint64_t ngroups, CUtensorMap* tm) {
+  const PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+  if (!fn || (reinterpret_cast<uintptr_t>(s->data) & 15)) return false;
+  const cuuint64_t gdim[2] = {(cuuint64_t)TC_K, (cuuint64_t)ngroups};
+  const cuuint64_t gstride[1] = {(cuuint64_t)TC_K * sizeof(float)};
+  const cuuint32_t box[2] = {32, TC_M};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, s->data, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 // Launches one block on the state's stream (no allocation, no sync);
 // dev_op holds dense_pack's output; status (tensor cores) is a device word
 // that a timed-out wait sets to 1.
@@ -436,9 +503,15 @@ qc_status dense_launch(qc_state* s, const DenseMap& M, const void* dev_op, int* 
     }
     const uint64_t ntiles = (ngroups + TC_M - 1) / TC_M;
     const unsigned grid = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)sm_count() * 2);
+    bool contig = true;  // targets 0..4 in order: a group is 32 contiguous amplitudes
+    for (int l = 0; l < dim; ++l) contig &= (M.offs[l] == (uint64_t)l);
+    CUtensorMap tm;
+    memset(&tm, 0, sizeof tm);
+    const int use_tma = contig && dense_out_map(s, ngroups, &tm);
     k_dense_tc<<<grid, TC_T, TC_SMEM, s->stream>>>(reinterpret_cast<float2*>(s->data), ngroups,
                                                      reinterpret_cast<const float*>(dev_op),
-                                                     reinterpret_cast<const float*>(dev_op) + TC_N * TC_K, M, status);
+                                                     reinterpret_cast<const float*>(dev_op) + TC_N * TC_K, M, status,
+                                                     tm, use_tma);
   } else if (s->dt == QC_C64) {
     const size_t smem = sizeof(float2) * ((size_t)dim * dim + DENSE_AMPS);
     static bool attr = false;

@@ -37,7 +37,8 @@ def run(qc, n, dt, qubits, U, seed):
     return np.max(np.abs(got - ref))
 
 
-@pytest.mark.parametrize("n,qubits", [(12, [0, 1, 2, 3, 4]), (14, [0, 1, 2, 3, 4]), (13, [7, 2, 11, 0, 5]),
+@pytest.mark.parametrize("n,qubits", [(12, [0, 1, 2, 3, 4]), (14, [0, 1, 2, 3, 4]), (11, [0, 1, 2, 3, 4]),
+                                      (22, [0, 1, 2, 3, 4]), (13, [7, 2, 11, 0, 5]),
                                       (9, [4, 0, 8, 2, 6]), (5, [0, 1, 2, 3, 4]), (16, [15, 3, 9, 1, 12])])
 def test_tensor_core_block_c64(qc, n, qubits):
     U = unitary(W.rng(n + sum(qubits)), 32)
