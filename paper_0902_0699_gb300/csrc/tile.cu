@@ -150,6 +150,19 @@ template <typename R> struct TileProg {
 #define TS_TWA 128
 #define TS_TWB 128  // x < 2^{c+k} <= 2^14
 
+// Ladder levels kept in the table.  complex128 stops at level 10 (2047
+// double-float entries, 32 KiB), so the 12-qubit lowest group's pass fits
+// two CTAs per SM; its level 11 phase is L_11(y) = L_10(y >> 1) times
+// e^{2 pi i / 2^12} for odd y, the latter stored after the table.
+template <typename R>
+__host__ __device__ constexpr int lad_levels(int k) {
+  return sizeof(R) == 8 ? (k < 11 ? k : 11) : k;
+}
+template <typename R>
+__host__ __device__ constexpr int lad_entries(int k) {
+  return (1 << lad_levels<R>(k)) - 1 + (k > lad_levels<R>(k) ? 1 : 0);
+}
+
 __device__ __forceinline__ uint64_t tile_global(uint64_t e, uint64_t T, int lo, int k, int c) {
   const uint64_t cm = (1ull << c) - 1ull;
   const uint64_t tmid = T & ((1ull << (lo - c)) - 1ull);
@@ -222,16 +235,26 @@ __global__ void __launch_bounds__(512, QREG ? 1 : 2) k_tile(typename CT<R>::V2* 
   const int NE = 1 << (k + c);
   E* V = sm + NE;
   E* LAD = V + (P.twiddle ? (1 << k) : 0);
-  E* TWA = LAD + (P.qft ? ((1 << k) - 1) : 0);
+  const int kl = lad_levels<R>(k);  // levels in the table
+  E* TWA = LAD + (P.qft ? lad_entries<R>(k) : 0);
   E* TWB = TWA + TS_TWA;
   const int hi = lo + k - 1;
   const typename A::S sc = A::scale_const(P.scale_p);
   if (P.qft) {
     // ladder tables, one per level: LAD[2^j - 1 + x] = e^{2 pi i x / 2^{j+1}}
-    for (int a = threadIdx.x; a < (1 << k) - 1; a += blockDim.x) {
+    for (int a = threadIdx.x; a < (1 << kl) - 1; a += blockDim.x) {
       const int j = 31 - __clz(a + 1);
       LAD[a] = A::root((uint64_t)(a + 1 - (1 << j)), j + 1);
     }
+    if (k > kl && threadIdx.x == 0) LAD[(1 << kl) - 1] = A::root(1, k);  // e^{2 pi i / 2^k}
+  }
+  // L_j(y) = e^{2 pi i y / 2^{j+1}}, y < 2^j (j <= kl: one level past the table)
+  auto ladder = [&](int j, int y) -> E {
+    if (j < kl) return LAD[(1 << j) - 1 + y];
+    const E m = LAD[(1 << (j - 1)) - 1 + (y >> 1)];
+    return (y & 1) ? A::mul(m, LAD[(1 << kl) - 1]) : m;
+  };
+  if (P.qft) {
     // twiddle remainder: Omega_{hi+1}^x = TWA[x & 127] * TWB[x >> 7], x < 2^{c+k}
     if (P.twiddle)
       for (int i = threadIdx.x; i < TS_TWA + TS_TWB; i += blockDim.x) {
@@ -331,11 +354,10 @@ __global__ void __launch_bounds__(512, QREG ? 1 : 2) k_tile(typename CT<R>::V2* 
             t1 = A::add(d0, id1);
             u1 = A::sub(d0, id1);
             if (x) {
-              const E* Lh = LAD + (1 << jh) - 1;  // L(y) = Lh[y] for y < 2^jh
-              u0 = A::mul(Lh[2 * x], u0);
-              t1 = A::mul(Lh[x], t1);
+              u0 = A::mul(ladder(jh, 2 * x), u0);
+              t1 = A::mul(ladder(jh, x), t1);
               const int x3 = 3 * x;  // < 1.5 2^jh; L(y + 2^jh) = -L(y)
-              u1 = A::mul(Lh[x3 & ((1 << jh) - 1)], u1);
+              u1 = A::mul(ladder(jh, x3 & ((1 << jh) - 1)), u1);
               if (x3 >> jh) u1 = A::neg(u1);
             }
           } else {  // plain butterflies on both bits
@@ -375,7 +397,7 @@ __global__ void __launch_bounds__(512, QREG ? 1 : 2) k_tile(typename CT<R>::V2* 
           E d = A::sub(a0, a1);
           if (lad) {
             const int x = (e0 >> c) & ((1 << j) - 1);
-            if (x) d = A::mul(LAD[(1 << j) - 1 + x], d);
+            if (x) d = A::mul(ladder(j, x), d);
           }
           sm[e1] = d;
         }
@@ -443,6 +465,8 @@ __global__ void k_roots(typename CT<R>::V2* tlo, typename CT<R>::V2* thi, int n,
 // complex64: 32 complex64 qubits in three passes, 13 + 10 + 9).
 template <typename R> struct TileCfg;
 template <> struct TileCfg<double> { static constexpr int C = 3, K = 9, BOT = 12; };
+// the ladder helper reaches one level past the table (levels 0..10)
+static_assert(TileCfg<double>::BOT <= 12 && TileCfg<double>::K <= 12, "complex128 groups of at most 12 qubits");
 // complex64: 128 KiB tiles (k = 10, c = 4); the lowest group (c = 0) stops at
 // 13 qubits, where its tile and ladder table take 64 KiB each
 template <> struct TileCfg<float> { static constexpr int C = 4, K = 10, BOT = 13; };
@@ -478,7 +502,7 @@ template <typename R>
 static size_t tile_smem(int k, int c, bool twiddle, bool qft) {
   using E = typename TA<R>::E;
   return sizeof(E) * (((size_t)1 << (k + c)) + (twiddle ? ((size_t)1 << k) : 0) +
-                      (qft ? ((size_t)1 << k) - 1 : 0) + TS_TWA + TS_TWB);
+                      (qft ? (size_t)lad_entries<R>(k) : 0) + TS_TWA + TS_TWB);
 }
 
 template <typename R>
