@@ -144,9 +144,9 @@ template <typename R> struct TileProg {
   typename TA<R>::M U[QC_TILE_MAXOPS];
 };
 
-// Shared memory after the tile: V[2^k] (twiddle passes), LAD[2^k - 1]
+// Shared memory after the tile: V[2^k] (twiddle passes), LAD[lad_entries(k)]
 // (QFT passes: level j's 2^j ladder phases e^{2 pi i x / 2^{j+1}} at
-// LAD[2^j - 1 + x], so a warp reads consecutive entries), TWA[128], TWB[64].
+// LAD[2^j - 1 + x], so a warp reads consecutive entries), TWA[128], TWB[128].
 #define TS_TWA 128
 #define TS_TWB 128  // x < 2^{c+k} <= 2^14
 
