@@ -266,8 +266,10 @@ qc_status qc_qft_range(qc_state* s, int lo, int width);
 
 /* ----------------------------------------------------------- reductions -- */
 
-/* sum_i |C_i|^2 accumulated in FP64 (the normalisation of sec. 2).
- * Synchronises the stream; *out_host receives the value. */
+/* sum_i |C_i|^2 (the normalisation of sec. 2): FP64 for complex128; for
+ * complex64 the exact float squares are summed as float pairs over runs of
+ * 32 amplitudes and the runs in FP64.  Synchronises the stream; *out_host
+ * receives the value. */
 qc_status qc_norm(const qc_state* s, double* out_host);
 
 /* Born-rule probabilities p_i = |C_i|^2 in FP64 (re*re + im*im, rounded
@@ -275,8 +277,11 @@ qc_status qc_norm(const qc_state* s, double* out_host);
 qc_status qc_probs(const qc_state* s, double* out_dev);
 
 /* <psi|P|psi> for the Pauli string P = i^{|x&z|} X^x Z^z (X on bits of
- * xmask only, Z on zmask only, Y where both are set), FP64 accumulation.
- * out_host[0..1] = (re, im).  Synchronises the stream. */
+ * xmask only, Z on zmask only, Y where both are set).  P is Hermitian and
+ * the amplitude pairs (j, j^x) are combined, so the value is exactly real:
+ * out_host[0..1] = (value, 0).  FP64 accumulation (complex64: exact float
+ * products in float-pair runs, the runs in FP64).  Synchronises the
+ * stream. */
 qc_status qc_expect_pauli(const qc_state* s, uint64_t xmask, uint64_t zmask, double out_host[2]);
 
 /* Scale the state by 1/sqrt(sum |C|^2) (FP64 norm).  *norm_out_host (if not
@@ -293,9 +298,10 @@ qc_status qc_renormalize(qc_state* s, double* norm_out_host);
  * Requires every p_i in [0, 2] and 0 < total <= 2^63 (so sum p_i <= 2;
  * QC_EINVAL otherwise) and shots >= 0.  With shots <= 2^n / 2048 each shot
  * rescans the one block of 2048 amplitudes that holds its target, and the
- * temporary device buffer is 8 * (2^n / 2048 + 2) bytes; with more shots
- * the full W is written, 8 * (2^n + 2^n / 2048 + 2) bytes (QC_ENOMEM if it
- * does not fit).  Both give the outcomes above.  Synchronises the stream
+ * temporary device buffer is 8 * (2^n / 2048 + 2) bytes (plus 8 bytes per
+ * 4096 blocks for n >= 24, whose block sums are scanned in chunks); with
+ * more shots the full W is written as well, 8 * 2^n bytes more (QC_ENOMEM
+ * if it does not fit).  Both give the outcomes above.  Synchronises the stream
  * once (to read the total back). */
 qc_status qc_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_t* out_dev);
 
