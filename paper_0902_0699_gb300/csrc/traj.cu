@@ -240,15 +240,31 @@ struct Track {
   ff S[2], c[2], a[2], Q;
   float b;
   bool mapped;  // the map is not the identity
-  __device__ void anchor(const ff g5[5]) {  // after a pass with reductions
-    S[0] = g5[0];
-    S[1] = g5[1];
-    Q = g5[2];
-    c[0] = g5[3];
-    c[1] = g5[4];
+  // From the last pass: Tz = sum_j (-1)^{|j&tz|} stored_j for the next
+  // noisy iteration's Z mask tz (0: not taken) and the stored value at m.
+  ff Tz[2], cst[2];
+  uint32_t tz;
+  __device__ void anchor(const ff g[7], uint32_t z) {  // after a pass with reductions
+    S[0] = g[0];
+    S[1] = g[1];
+    Q = g[2];
+    c[0] = cst[0] = g[3];
+    c[1] = cst[1] = g[4];
+    Tz[0] = g[5];
+    Tz[1] = g[6];
+    tz = z;
     a[0] = a[1] = ff_make(0.f, 0.f);
     b = 1.f;
     mapped = false;
+  }
+  // W = sum_j (-1)^{|j&z|} (O psi)_j for z = tz != 0 without reading the
+  // state: with psi_j = a + b stored_j (j != m), psi_m = c, s = (-1)^{|m&z|}
+  // and sum_j (-1)^{|j&z|} = 0,  W = b (Tz - s cst) - s (a + c).
+  __device__ ff Wz(int i, bool s_neg) const {
+    ff t = s_neg ? ff_add(Tz[i], cst[i]) : ff_sub(Tz[i], cst[i]);
+    if (b < 0.f) t = ff_neg(t);
+    const ff u = ff_add(a[i], c[i]);
+    return s_neg ? ff_add(t, u) : ff_sub(t, u);
   }
   // k = 2/N, a power of two, so scaling by it is exact
   __device__ void clean_step(float k) {
@@ -279,17 +295,24 @@ struct Track {
 // independent and average out).
 struct Acc {
   float sr, cr, si, ci, q, cq, gr, gi, gq;
-  __device__ void zero() { sr = cr = si = ci = q = cq = gr = gi = gq = 0.f; }
+  float tr, tcr, ti, tci, gtr, gti;  // sum of (-1)^{|j&tz|} o_j (when tz != 0)
+  __device__ void zero() { sr = cr = si = ci = q = cq = gr = gi = gq = tr = tcr = ti = tci = gtr = gti = 0.f; }
   __device__ void add(float2 o) {
     gr += o.x;
     gi += o.y;
     gq = fmaf(o.x, o.x, fmaf(o.y, o.y, gq));
   }
+  __device__ void add_t(float2 o, bool neg) {
+    gtr += neg ? -o.x : o.x;
+    gti += neg ? -o.y : o.y;
+  }
   __device__ void flush() {
     ff_add(sr, cr, gr);
     ff_add(si, ci, gi);
     ff_add(q, cq, gq);
-    gr = gi = gq = 0.f;
+    ff_add(tr, tcr, gtr);
+    ff_add(ti, tci, gti);
+    gr = gi = gq = gtr = gti = 0.f;
   }
 };
 
@@ -298,6 +321,7 @@ struct PassArgs {
   float ar, ai, b, cr, ci;  // pending map and the virtual marked amplitude
   float t2r, t2i, sf;       // 2 m and s of a noisy iteration
   uint32_t m, X, ax, az, bz;
+  uint32_t tz;  // Z mask of the next noisy iteration's signed sum (0: none)
   int aa, ba;
 };
 
@@ -331,13 +355,18 @@ __device__ __forceinline__ float2 noisy_out(uint32_t j, float2 u, const PassArgs
 // passes are bound by L2 latency).
 template <int UNR, class F>
 __device__ __forceinline__ void vec_pass(float4* p4, uint32_t lo, uint32_t hi, uint32_t m, int tid, int T, F f,
-                                         Acc& acc, float& cmr, float& cmi) {
+                                         Acc& acc, float& cmr, float& cmi, uint32_t tz = 0u) {
   const uint32_t vm = m >> 1, vhi = hi >> 1, uT = (uint32_t)T;
   auto one = [&](uint32_t v, const float4& u) {
     const float4 o = f(v, u);
     p4[v] = o;
     acc.add(make_float2(o.x, o.y));
     acc.add(make_float2(o.z, o.w));
+    if (tz) {
+      const bool s0 = __popc((2 * v) & tz) & 1;
+      acc.add_t(make_float2(o.x, o.y), s0);
+      acc.add_t(make_float2(o.z, o.w), s0 != (bool)(tz & 1u));
+    }
     if (v == vm) {
       cmr = (m & 1) ? o.z : o.x;
       cmi = (m & 1) ? o.w : o.y;
@@ -378,6 +407,13 @@ __device__ __forceinline__ void pair_pass(float4* p4, uint32_t lo, uint32_t hi, 
     acc.add(o1);
     acc.add(o2);
     acc.add(o3);
+    if (q.tz) {
+      const bool s0 = __popc((2 * v) & q.tz) & 1, s2 = __popc((2 * vx) & q.tz) & 1, odd = q.tz & 1u;
+      acc.add_t(o0, s0);
+      acc.add_t(o1, s0 != odd);
+      acc.add_t(o2, s2);
+      acc.add_t(o3, s2 != odd);
+    }
     acc.flush();
     if (v == vm) {
       cmr = (q.m & 1) ? o1.x : o0.x;
@@ -433,11 +469,12 @@ __global__ void __launch_bounds__(512, MINB) k_traj(TrajParams P) {
   const int rank = (int)cluster.block_rank();
   const int cid = blockIdx.x / G;
   __shared__ Xch xch;
-  __shared__ float2 shf[5 * 32];  // block_ff_sum rows
+  __shared__ float2 shf[7 * 32];  // block_ff_sum rows
   __shared__ unsigned long long shu[32];
-  __shared__ Pauli pA, pB;
+  __shared__ Pauli pA;
   __shared__ int sh_err;
   __shared__ int sh_flag;
+  __shared__ int sh_read;  // this noisy iteration needs the reading pass for W
   __shared__ float wtab[QC_TRAJ_MAX_QUBITS + 1];
   __shared__ unsigned long long sh_target;
   __shared__ PassArgs sh_q;
@@ -465,16 +502,17 @@ __global__ void __launch_bounds__(512, MINB) k_traj(TrajParams P) {
     // one block reduction of a pass's sums, exchanged over the cluster; the
     // totals re-anchor thread 0's scalars
     Track tr;
-    auto reduce_anchor = [&](Acc& acc, float cmr, float cmi) {
-      float h[5] = {acc.sr, acc.si, acc.q, cmr, cmi}, l[5] = {acc.cr, acc.ci, acc.cq, 0.f, 0.f};
-      block_ff_sum<5>(h, l, shf);
+    auto reduce_anchor = [&](Acc& acc, float cmr, float cmi, uint32_t tz) {
+      float h[7] = {acc.sr, acc.si, acc.q, cmr, cmi, acc.tr, acc.ti};
+      float l[7] = {acc.cr, acc.ci, acc.cq, 0.f, 0.f, acc.tcr, acc.tci};
+      block_ff_sum<7>(h, l, shf);
       if (tid == 0)
-        for (int v = 0; v < 5; ++v) xch.v[buf][v] = make_float2(h[v], l[v]);
+        for (int v = 0; v < 7; ++v) xch.v[buf][v] = make_float2(h[v], l[v]);
       __threadfence();
       cluster.sync();
-      ff g5[5];
-      cluster_gather<5>(cluster, xch, buf, 0, g5);
-      if (tid == 0) tr.anchor(g5);
+      ff g7[7];
+      cluster_gather<7>(cluster, xch, buf, 0, g7);
+      if (tid == 0) tr.anchor(g7, tz);
     };
     // ---- stage 0: E0 HALL |0..0> = E0 |s>: psi[j] = i^a (-1)^{|(j^x)&z|} 2^{-n/2}
     if (tid < 32) {
@@ -505,7 +543,7 @@ __global__ void __launch_bounds__(512, MINB) k_traj(TrajParams P) {
                  return make_float4(o0.x, o0.y, o1.x, o1.y);
                },
                acc, cmr, cmi);
-      reduce_anchor(acc, cmr, cmi);
+      reduce_anchor(acc, cmr, cmi, 0u);
     }
     const float two_over_n = ldexpf(1.f, 1 - n);
     for (int base = 0; base < I.iters; base += TCH) {
@@ -554,7 +592,6 @@ __global__ void __launch_bounds__(512, MINB) k_traj(TrajParams P) {
           Pauli e[4];
           for (int sg = 0; sg < 4; ++sg) e[sg] = Pauli{ex[li][sg], ez[li][sg], ey[li][sg] & 3};
           const Pauli B = pmul(hconj(e[1]), e[0]), A = pmul(e[3], hconj(e[2]));
-          pB = B;
           PassArgs q;
           tr.to_args(q.ar, q.ai, q.b, q.cr, q.ci);
           q.m = m;
@@ -564,9 +601,27 @@ __global__ void __launch_bounds__(512, MINB) k_traj(TrajParams P) {
           q.bz = (uint32_t)B.z;
           q.aa = A.a;
           q.ba = B.a;
-          if (!B.z) {  // sum of O psi: S with the marked amplitude's sign flipped
+          // the next noisy iteration of this chunk: when its B has a Z part,
+          // this pass also sums its outputs signed by that part, so the
+          // next one needs no extra reading pass
+          q.tz = 0u;
+          for (int w = (li + 1) >> 5; w < TCH / 32; ++w) {
+            uint32_t bits = dirty[w];
+            if (w == ((li + 1) >> 5)) bits &= ~0u << ((li + 1) & 31);
+            if (bits) {
+              const int l2 = 32 * w + __ffs((int)bits) - 1;  // < cnt: later bits are never set
+              const Pauli f0{ex[l2][0], ez[l2][0], ey[l2][0] & 3}, f1{ex[l2][1], ez[l2][1], ey[l2][1] & 3};
+              q.tz = (uint32_t)pmul(hconj(f1), f0).z;
+              break;
+            }
+          }
+          const bool have_w = B.z && tr.tz == (uint32_t)B.z;  // taken by the previous pass
+          sh_read = B.z && !have_w;
+          if (!sh_read) {  // W = the sum of B's Z-signed O psi
+            const bool sn = __popc(m & (uint32_t)B.z) & 1;
             float sc[3];
-            grover_scalars(tr.W(0), tr.W(1), tr.Q, B.a, n, sc);
+            if (B.z) grover_scalars(tr.Wz(0, sn), tr.Wz(1, sn), tr.Q, B.a, n, sc);
+            else grover_scalars(tr.W(0), tr.W(1), tr.Q, B.a, n, sc);  // S with the marked amplitude's sign flipped
             q.t2r = sc[0];
             q.t2i = sc[1];
             q.sf = sc[2];
@@ -574,7 +629,7 @@ __global__ void __launch_bounds__(512, MINB) k_traj(TrajParams P) {
           sh_q = q;
         }
         __syncthreads();
-        if (pB.z) {
+        if (sh_read) {
           // sum of O psi, signed by Z^zB: one extra reading pass
           const PassArgs q = sh_q;
           float hr = 0.f, lr = 0.f, hi_ = 0.f, li_ = 0.f;
@@ -642,11 +697,11 @@ __global__ void __launch_bounds__(512, MINB) k_traj(TrajParams P) {
                      const float2 o0 = noisy_out(2 * v, sw ? a1 : a0, q), o1 = noisy_out(2 * v + 1, sw ? a0 : a1, q);
                      return make_float4(o0.x, o0.y, o1.x, o1.y);
                    },
-                   acc, cmr, cmi);
+                   acc, cmr, cmi, q.tz);
         } else {
           pair_pass(p4, lo, hi, tid, T, q, acc, cmr, cmi);
         }
-        reduce_anchor(acc, cmr, cmi);
+        reduce_anchor(acc, cmr, cmi, q.tz);
       }
       __syncthreads();  // the tables are read before the next chunk clears them
     }
@@ -671,7 +726,7 @@ __global__ void __launch_bounds__(512, MINB) k_traj(TrajParams P) {
                  return make_float4(o0.x, o0.y, o1.x, o1.y);
                },
                acc, cmr, cmi);
-      reduce_anchor(acc, cmr, cmi);
+      reduce_anchor(acc, cmr, cmi, 0u);
     }
     // ---- read-out: success probabilities and one seeded measurement
     buf ^= 1;
