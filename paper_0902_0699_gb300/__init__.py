@@ -539,3 +539,100 @@ def version() -> str:
 def kernel_launches() -> int:
     """Kernels this library has launched in this process so far."""
     return int(lib().qc_kernel_launches())
+
+
+# ------------------------------------------ the adjoint gradient in autograd --
+
+class Circuit:
+    """A parameterised circuit on n qubits and a Hamiltonian, for
+    energy(theta, circuit).  gates: (kind, q0, q1, param) with the QC_G_*
+    kinds (param indexes theta for rotations; q1 only for CNOT); terms:
+    Pauli terms (xmask, zmask, coeff) with real coefficients."""
+
+    def __init__(self, n: int, gates, terms, dt: int = QC_C128):
+        self.n, self.dt = int(n), int(dt)
+        gl = [tuple(int(v) for v in g) for g in gates]
+        tl = [(int(x), int(z), float(c)) for (x, z, c) in terms]
+        self.n_gates, self.n_terms = len(gl), len(tl)
+        self.gates = (Gate * max(1, len(gl)))(*[Gate(*g) for g in gl])
+        self.terms = (PauliTerm * max(1, len(tl)))(*[PauliTerm(*t) for t in tl])
+        rot = [g[3] for g in gl if g[0] in (QC_G_RX, QC_G_RY, QC_G_RZ)]
+        self.n_params = max(rot) + 1 if rot else 0
+
+    def energy_and_grad(self, theta):
+        """E_b and dE_b/dtheta for theta of shape (B, P) (float64, CUDA): one
+        qc_adjoint_grad call (forward, then the adjoint backward sweep)."""
+        import torch
+        B, P = theta.shape
+        psi = torch.empty(B << self.n, dtype=torch_dtype(self.dt), device=theta.device)
+        lam = torch.empty_like(psi)
+        E = torch.empty(B, dtype=torch.float64, device=theta.device)
+        grad = torch.empty(B, P, dtype=torch.float64, device=theta.device)
+        _check(lib().qc_adjoint_grad(self.n, self.dt, B, self.gates, self.n_gates, _VP(theta.data_ptr()), P, P,
+                                     self.terms, self.n_terms, _VP(psi.data_ptr()), _VP(lam.data_ptr()),
+                                     _VP(E.data_ptr()), _VP(grad.data_ptr()), _stream_handle(None)))
+        return E, grad
+
+    def energy(self, theta):
+        """E_b for theta of shape (B, P): the forward pass and the Pauli
+        expectations, no backward sweep."""
+        import torch
+        B, P = theta.shape
+        psi = torch.empty(B << self.n, dtype=torch_dtype(self.dt), device=theta.device)
+        _check(lib().qc_circuit_forward(self.n, self.dt, B, self.gates, self.n_gates, _VP(theta.data_ptr()), P,
+                                        _VP(psi.data_ptr()), _stream_handle(None)))
+        E = torch.empty(B, dtype=torch.float64)
+        for b in range(B):
+            s = State(self.n, self.dt, tensor=psi[b << self.n:(b + 1) << self.n])
+            E[b] = sum(c * s.expect_pauli(x, z).real for (x, z, c) in
+                       ((t.xmask, t.zmask, t.coeff) for t in self.terms[:self.n_terms]))
+            s.close()
+        return E.to(theta.device)
+
+
+_ADJ = None
+
+
+def _adjoint_function():
+    """torch.autograd.Function whose forward runs the adjoint method: the
+    energy and its whole gradient come from one forward and one backward
+    sweep over the state (uncomputation with U^dagger, no stored
+    intermediate states); backward only scales the saved gradient."""
+    global _ADJ
+    if _ADJ is None:
+        import torch
+        from torch.autograd.function import once_differentiable
+
+        class AdjointEnergy(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, theta, circuit):
+                if not theta.is_cuda:
+                    raise ValueError("energy(): theta must be a CUDA tensor (there is no CPU path)")
+                vec = theta.dim() == 1
+                th = (theta.detach().unsqueeze(0) if vec else theta.detach()).to(torch.float64).contiguous()
+                if th.shape[1] < circuit.n_params:
+                    raise ValueError("energy(): theta has %d angles, the circuit uses %d"
+                                     % (th.shape[1], circuit.n_params))
+                if ctx.needs_input_grad[0]:
+                    E, grad = circuit.energy_and_grad(th)
+                    ctx.save_for_backward(grad)
+                else:
+                    E = circuit.energy(th)
+                ctx.vec, ctx.tdtype = vec, theta.dtype
+                return E[0] if vec else E
+
+            @staticmethod
+            @once_differentiable
+            def backward(ctx, gE):
+                (grad,) = ctx.saved_tensors
+                g = (gE.reshape(-1, 1).to(torch.float64) * grad).to(ctx.tdtype)
+                return (g[0] if ctx.vec else g), None
+
+        _ADJ = AdjointEnergy
+    return _ADJ
+
+
+def energy(theta, circuit: Circuit):
+    """E(theta) = <psi(theta)|H|psi(theta)> for theta of shape (P,) or (B, P),
+    differentiable in theta through the adjoint gradient kernels."""
+    return _adjoint_function().apply(theta, circuit)

@@ -275,3 +275,56 @@ def test_traj_degenerate_sizes(qc):
         prob = O.probs(psi, n)
         assert abs(ps[i] - prob[m] / prob.sum()) <= 1e-5
         assert abs(pr[i] - O.readout_success(prob, n, m, tb.p_readout) / prob.sum()) <= 1e-5
+
+
+# ---------------------------------------------------------- torch.autograd --
+
+def ansatz_circuit(qc, circ, dt):
+    gates = []
+    for g in O.ansatz_gates(circ):
+        if g[0] == "cnot":
+            gates.append((qc.QC_G_CNOT, g[1], g[2], 0))
+        else:
+            gates.append((qc.QC_G_RY if g[0] == "ry" else qc.QC_G_RZ, g[1], 0, g[2]))
+    return qc.Circuit(circ.n, gates, W.ansatz_hamiltonian(circ.n), dt)
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_autograd_energy_and_grad_vs_oracle(qc, dt):
+    import torch
+    circs = W.ansatz(6, 4, seed=21, batch=3)
+    C = ansatz_circuit(qc, circs[0], dt)
+    theta = torch.tensor(np.stack([c.theta for c in circs]), dtype=torch.float64, device="cuda",
+                         requires_grad=True)
+    E = qc.energy(theta, C)
+    w = torch.tensor([1.0, -2.0, 0.5], dtype=torch.float64, device="cuda")  # upstream gradient
+    (E * w).sum().backward()
+    tol = 1e-12 if dt == 0 else 2e-5
+    terms = W.ansatz_hamiltonian(6)
+    for b, c in enumerate(circs):
+        Er, gr = O.adjoint_gradient(c, terms)
+        assert abs(float(E[b].detach()) - Er) <= tol
+        assert np.max(np.abs(theta.grad[b].cpu().numpy() - w[b].item() * gr)) <= 3 * tol
+    # without autograd: the forward pass and the expectations only
+    with torch.no_grad():
+        E2 = qc.energy(theta, C)
+    assert float(torch.max(torch.abs(E2 - E.detach()))) <= tol
+
+
+def test_autograd_gradcheck_finite_differences(qc):
+    import torch
+    circ = W.ansatz(3, 2, seed=4)[0]
+    C = ansatz_circuit(qc, circ, 0)
+    theta = torch.tensor(circ.theta, dtype=torch.float64, device="cuda", requires_grad=True)
+    assert qc.energy(theta, C).dim() == 0  # one angle vector: a scalar energy
+    assert torch.autograd.gradcheck(lambda t: qc.energy(t, C), (theta,), eps=1e-6, atol=1e-8, rtol=1e-6)
+
+
+def test_autograd_rejects_host_theta(qc):
+    import torch
+    circ = W.ansatz(3, 1, seed=1)[0]
+    C = ansatz_circuit(qc, circ, 0)
+    with pytest.raises(ValueError):
+        qc.energy(torch.tensor(circ.theta), C)
+    with pytest.raises(ValueError):
+        qc.energy(torch.zeros(2, dtype=torch.float64, device="cuda"), C)  # fewer angles than used
