@@ -12,6 +12,7 @@ significant qubit).
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -636,3 +637,66 @@ def energy(theta, circuit: Circuit):
     """E(theta) = <psi(theta)|H|psi(theta)> for theta of shape (P,) or (B, P),
     differentiable in theta through the adjoint gradient kernels."""
     return _adjoint_function().apply(theta, circuit)
+
+
+# ------------------------------------------------- batched noisy trajectories --
+
+def _threshold(p: float) -> int:
+    """floor(p * 2^32), the integer threshold of a draw (qc_traj_desc)."""
+    if not 0.0 <= p <= 1.0:
+        raise ValueError("probability %r outside [0, 1]" % (p,))
+    return min(int(math.floor(p * 4294967296.0)), 0xFFFFFFFF)
+
+
+class TrajectoryPlan:
+    """A batch of noisy Grover trajectories (qc_traj_plan_*): nq, marked and
+    iters per instance, per-gate Pauli noise p_gate and read-out flips
+    p_readout.  Creating it validates and uploads the batch and (autotune)
+    times the launch shapes; run() executes every instance in one persistent
+    launch and returns device tensors p_success, p_readout, outcome and
+    n_errors."""
+
+    def __init__(self, nq, marked, iters, seed: int, p_gate: float = 1e-3, p_readout: float = 1e-3,
+                 autotune: bool = True, stream=None):
+        self._nq = np.ascontiguousarray(nq, dtype=np.int32)
+        self._mk = np.ascontiguousarray(marked, dtype=np.uint64)
+        self._it = np.ascontiguousarray(iters, dtype=np.int32)
+        if not (len(self._nq) == len(self._mk) == len(self._it)):
+            raise ValueError("nq, marked and iters need one entry per instance")
+        self.n_inst = len(self._nq)
+        d = TrajDesc(self.n_inst, self._nq.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                     self._mk.ctypes.data_as(_U64P), self._it.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                     int(seed), _threshold(p_gate), _threshold(p_readout), float(p_readout))
+        self.h = ctypes.c_void_p()
+        _check(lib().qc_traj_plan_create(ctypes.byref(d), _stream_handle(stream), int(bool(autotune)),
+                                         ctypes.byref(self.h)))
+
+    @property
+    def shape(self):
+        """(CTAs per instance, threads per CTA, grid) of the chosen launch."""
+        v = [ctypes.c_int(), ctypes.c_int(), ctypes.c_int()]
+        _check(lib().qc_traj_plan_info(self.h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def run(self):
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        out = {"p_success": torch.empty(self.n_inst, dtype=torch.float64, device=dev),
+               "p_readout": torch.empty(self.n_inst, dtype=torch.float64, device=dev),
+               "outcome": torch.empty(self.n_inst, dtype=torch.int64, device=dev),
+               "n_errors": torch.empty(self.n_inst, dtype=torch.int32, device=dev)}
+        o = TrajOut(out["p_success"].data_ptr(), out["p_readout"].data_ptr(), out["outcome"].data_ptr(),
+                    out["n_errors"].data_ptr())
+        _check(lib().qc_traj_plan_run(self.h, ctypes.byref(o)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().qc_traj_plan_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,5 +1,5 @@
-"""Host side of the autograd binding: the circuit's packed gate and Pauli
-arrays and its parameter count (no GPU)."""
+"""Host side of the binding: the circuit's packed gate and Pauli arrays,
+its parameter count and the trajectory thresholds (no GPU)."""
 import paper_0902_0699_gb300 as qc
 
 
@@ -16,3 +16,9 @@ def test_circuit_packing():
 def test_autograd_function_is_a_torch_function():
     import torch
     assert issubclass(qc._adjoint_function(), torch.autograd.Function)
+
+
+def test_trajectory_thresholds_follow_the_descriptor_definition():
+    import workloads as W
+    for p in (0.0, 1e-3, 0.35, 0.5, 1.0 - 2 ** -40, 1.0):
+        assert qc._threshold(p) == W.prob_threshold(p)

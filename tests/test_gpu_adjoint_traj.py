@@ -328,3 +328,32 @@ def test_autograd_rejects_host_theta(qc):
         qc.energy(torch.tensor(circ.theta), C)
     with pytest.raises(ValueError):
         qc.energy(torch.zeros(2, dtype=torch.float64, device="cuda"), C)  # fewer angles than used
+
+
+def test_trajectory_plan_wrapper(qc):
+    # the Python wrapper against the noiseless closed form and the raw C calls
+    import torch
+    tb = W.trajectory_batch(40, 6, 12, seed=77, p_gate=0.0, p_readout=0.0)
+    plan = qc.TrajectoryPlan(tb.nq, tb.marked, tb.iters, tb.seed, p_gate=0.0, p_readout=0.0, autotune=False)
+    out = plan.run()
+    torch.cuda.synchronize()
+    ps = out["p_success"].cpu().numpy()
+    for i in range(len(tb.nq)):
+        th = math.asin(2.0 ** (-tb.nq[i] / 2.0))
+        assert abs(ps[i] - math.sin((2 * tb.iters[i] + 1) * th) ** 2) <= 1e-5
+    assert int(out["n_errors"].sum()) == 0
+    assert len(plan.shape) == 3
+    plan.close()
+    tb2 = W.trajectory_batch(24, 8, 12, seed=78, p_gate=0.01, p_readout=0.01)
+    # the same (default) launch shape on both sides, so the reductions add in
+    # the same order
+    plan = qc.TrajectoryPlan(tb2.nq, tb2.marked, tb2.iters, tb2.seed, p_gate=0.01, p_readout=0.01,
+                             autotune=False)
+    got = plan.run()
+    torch.cuda.synchronize()
+    plan.close()
+    ps, pr, oc, ne, _ = run_traj(qc, tb2)  # raw qc_traj_plan_* calls
+    assert np.array_equal(got["n_errors"].cpu().numpy(), ne)
+    assert np.array_equal(got["outcome"].cpu().numpy().astype(np.uint64), oc)
+    assert np.array_equal(got["p_success"].cpu().numpy(), ps)
+    assert np.array_equal(got["p_readout"].cpu().numpy(), pr)
