@@ -601,7 +601,7 @@ def extra_c5():
     import paper_0902_0699_gb300 as qc
     import workloads as W
     n, layers = 20, 50
-    res = {}
+    res, first = {}, {}
     for dt, B, name in ((qc.QC_C64, 64, "c64_batch64"), (qc.QC_C128, 1, "c128_batch1")):
         circs = W.ansatz(n, layers, seed=5, batch=B)
         P = circs[0].n_params
@@ -644,6 +644,17 @@ def extra_c5():
         res[name] = {"qubits": n, "gates": len(gl), "angles": P, "batch": B, "forward_ms": tf,
                      "grad_ms (forward+backward)": tg, "grad_time_over_forward": tg / tf,
                      "energy_mean": float(E.mean().item())}
+        # batch element 0 has the same angles in both runs (seed 5, row 0)
+        fwd()
+        torch.cuda.synchronize()
+        nrm = float((psi[: 1 << n].abs().double() ** 2).sum().item())
+        first[name] = (float(E[0].item()), grad[0].cpu().numpy(), nrm)
+    e64, g64, n64 = first["c64_batch64"]
+    e128, g128, n128 = first["c128_batch1"]
+    res["c64_vs_c128"] = {"energy_abs_diff": abs(e64 - e128), "grad_max_abs_diff": float(np.max(np.abs(g64 - g128))),
+                          "grad_max_abs_c128": float(np.max(np.abs(g128))),
+                          "norm_error_after_forward_c64": abs(n64 - 1.0), "norm_error_after_forward_c128": abs(n128 - 1.0),
+                          "note": "batch element 0 of the complex64 run against the complex128 run, same angles"}
     return res
 
 
