@@ -481,6 +481,54 @@ def extra_c1():
             "note": "grover_run (one kernel, state in shared memory) + probs + 1000 samples (sampling syncs the stream once, to read the weight total)"}
 
 
+def extra_red(reps=3):
+    """One call of each reduction on a 1 GiB random state per type (26 qubits
+    complex128, 27 qubits complex64): Born probabilities, 1000 samples, the
+    norm and three Pauli expectations (diagonal, X-type, Y-type pairing).
+    One warm-up pass calls each once, in that order, before the timed
+    repeats (so a profiler's first six launches per type are one of each
+    kernel).  Times are CUDA-event averages; GB/s counts one read of the
+    state (plus the probabilities written, for probs)."""
+    import torch
+    import paper_0902_0699_gb300 as qc
+    out = {}
+    for n, dt, name in [(26, qc.QC_C128, "c128"), (27, qc.QC_C64, "c64")]:
+        g = torch.Generator(device="cuda")
+        g.manual_seed(5)
+        rdt = torch.float64 if dt == qc.QC_C128 else torch.float32
+        t = torch.randn(2 << n, dtype=rdt, device="cuda", generator=g)
+        t /= t.norm()
+        st = qc.State(n, dt, tensor=torch.view_as_complex(t.view(-1, 2)).contiguous())
+        del t
+        sb = (1 << n) * (16 if dt == qc.QC_C128 else 8)
+        calls = {"probs": (lambda: st.probs(), sb + 8 * (1 << n)),
+                 "sample_1000": (lambda: st.sample(12345, 1000), sb),
+                 "norm": (lambda: st.norm(), sb),
+                 "expect_z": (lambda: st.expect_pauli(0, 5), sb),
+                 "expect_x": (lambda: st.expect_pauli(1 << (n - 1), 0), sb),
+                 "expect_y": (lambda: st.expect_pauli(1 << (n - 1), 1 << (n - 1)), sb)}
+        for fn, _ in calls.values():  # one warm-up pass over all calls first
+            fn()
+        torch.cuda.synchronize()
+        res = {}
+        for key, (fn, nbytes) in calls.items():
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / reps
+            res[key] = {"ms": ms, "GBps": nbytes / ms / 1e6}
+        out["%s_n%d" % (name, n)] = res
+        st.close()
+        del st
+        torch.cuda.empty_cache()
+    out["note"] = ("norm and expect return a host scalar and sample reads the weight total, so those "
+                   "calls include one stream sync each; the state (1 GiB) is larger than L2")
+    return out
+
+
 def extra_c2():
     import numpy as np
     import torch
@@ -827,7 +875,7 @@ def main():
         fn = {"c64": extra_c64, "c1": extra_c1, "c2": extra_c2, "c4": extra_c4, "c5": extra_c5,
               # a small trajectory batch (96 instances, 16..18 qubits) for profiling
               "c4s": lambda: extra_c4(96, 16, 18, seed=7, autotune=0), "f3": extra_f3,
-              "dense": extra_dense, "dense26": lambda: extra_dense(26, 2)}[args.only]
+              "dense": extra_dense, "dense26": lambda: extra_dense(26, 2), "red": extra_red}[args.only]
         print(json.dumps({args.only: fn()}), flush=True)
         return 0
     out, st, step_fn, ops, N = run_ours(args, ws, rank, local)
