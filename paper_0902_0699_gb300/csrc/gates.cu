@@ -62,9 +62,12 @@ __device__ __forceinline__ uint64_t pair_base(uint64_t p, int p0, int p1, uint64
 
 // Scalar form: one pair per work item, 16-byte (c128) or 8-byte (c64)
 // accesses.  UNR items are processed per loop trip so that 2 UNR loads are
-// in flight before the first use (4 for complex128).
+// in flight before the first use (4 for complex128).  The register budget
+// of four blocks per SM is declared: with it the complex128 exchange (CNOT)
+// streams at 0.93-0.95 of copy bandwidth on GB300, without it at 0.82-0.86
+// (same register count, different schedule).
 template <typename R, int KIND, int NINS>
-__global__ void __launch_bounds__(256) k_pairs(typename CT<R>::V2* __restrict__ s, uint64_t npairs, int p0,
+__global__ void __launch_bounds__(256, 4) k_pairs(typename CT<R>::V2* __restrict__ s, uint64_t npairs, int p0,
                                                int p1, uint64_t setm, int t, GateArg<R> G) {
   using IO = AmpIO<R>;
   constexpr bool B1 = touches_bit1_only(KIND);
@@ -155,7 +158,12 @@ static void launch_kind(qc_state* s, int nins, int p0, int p1, uint64_t setm, in
     }
   }
   auto k = (nins == 1) ? k_pairs<R, KIND, 1> : k_pairs<R, KIND, 2>;
-  k<<<resident_grid(k, T, npairs, (sizeof(R) == 8 ? 4 : 2) * T), T, 0, s->stream>>>(d, npairs, p0, p1, setm, t, G);
+  unsigned g = resident_grid(k, T, npairs, (sizeof(R) == 8 ? 4 : 2) * T);
+  // complex128: three blocks per SM (24 warps, 96 16-byte loads in flight
+  // per warp) stream best on GB300; a fourth adds DRAM contention (H: 0.92-
+  // 0.95 of copy bandwidth with three, 0.89-0.91 with four).
+  if (sizeof(R) == 8) g = std::min<unsigned>(g, 3u * (unsigned)sm_count());
+  k<<<g, T, 0, s->stream>>>(d, npairs, p0, p1, setm, t, G);
 }
 
 template <typename R>
