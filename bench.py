@@ -208,8 +208,7 @@ def run_ours(args, ws, rank, local):
         if ev: ev.mark("grover")
         st_.qft()
         if ev: ev.mark("qft")
-        st_.probs()
-        shots = st_.sample(12345, 1000)
+        _, shots = st_.probs_sample(12345, 1000)  # probabilities and samples from one read
         if ev: ev.mark("probs_sample")
         for t in range(n):
             if sweep_ev is not None: sweep_ev[("h", t)][0].record()
@@ -484,9 +483,10 @@ def extra_c1():
 def extra_red(reps=3):
     """One call of each reduction on a 1 GiB random state per type (26 qubits
     complex128, 27 qubits complex64): Born probabilities, 1000 samples, the
-    norm and three Pauli expectations (diagonal, X-type, Y-type pairing).
+    norm and three Pauli expectations (diagonal, X-type, Y-type pairing);
+    then probabilities and samples from one read (probs_sample).
     One warm-up pass calls each once, in that order, before the timed
-    repeats (so a profiler's first six launches per type are one of each
+    repeats (so a profiler's first seven launches per type are one of each
     kernel).  Times are CUDA-event averages; GB/s counts one read of the
     state (plus the probabilities written, for probs)."""
     import torch
@@ -506,7 +506,8 @@ def extra_red(reps=3):
                  "norm": (lambda: st.norm(), sb),
                  "expect_z": (lambda: st.expect_pauli(0, 5), sb),
                  "expect_x": (lambda: st.expect_pauli(1 << (n - 1), 0), sb),
-                 "expect_y": (lambda: st.expect_pauli(1 << (n - 1), 1 << (n - 1)), sb)}
+                 "expect_y": (lambda: st.expect_pauli(1 << (n - 1), 1 << (n - 1)), sb),
+                 "probs_sample_1000": (lambda: st.probs_sample(12345, 1000), sb + 8 * (1 << n))}
         for fn, _ in calls.values():  # one warm-up pass over all calls first
             fn()
         torch.cuda.synchronize()

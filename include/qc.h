@@ -305,6 +305,18 @@ qc_status qc_renormalize(qc_state* s, double* norm_out_host);
  * once (to read the total back). */
 qc_status qc_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_t* out_dev);
 
+/* Born-rule probabilities and seeded measurement together (sec. 5.2: the
+ * probability of each outcome, then ProjA/Randx draws): probs_dev receives
+ * exactly what qc_probs writes and out_dev exactly the outcomes of
+ * qc_sample(s, seed, shots, out_dev), but the state is read once for both --
+ * the pass that writes p_i also forms the sampler's block weight sums.
+ * probs_dev: 2^n doubles of device memory; out_dev: `shots` uint64 of device
+ * memory (may be NULL when shots = 0, which only writes the probabilities).
+ * Same requirements, temporary buffer and stream synchronisation as
+ * qc_sample; on QC_EINVAL from the probability check the probabilities have
+ * been written and no outcome has. */
+qc_status qc_probs_sample(const qc_state* s, double* probs_dev, uint64_t seed, int64_t shots, uint64_t* out_dev);
+
 /* Seeded measurement for callers that cannot allocate device memory.  The
  * paper has no counterpart; this entry point exists for library users.
  *

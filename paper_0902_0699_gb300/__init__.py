@@ -92,6 +92,7 @@ _SIGS = {
     "qc_expect_pauli": [_VP, _U64, _U64, _DP],
     "qc_renormalize": [_VP, _DP],
     "qc_sample": [_VP, _U64, _I64, _VP],
+    "qc_probs_sample": [_VP, _VP, _U64, _I64, _VP],
     "qc_sample_noalloc": [_VP, _I, _I, _U64, _I64, _VP, _VP],
     "qc_traj_plan_create": [ctypes.POINTER(TrajDesc), _VP, _I, ctypes.POINTER(_VP)],
     "qc_traj_plan_run": [_VP, ctypes.POINTER(TrajOut)],
@@ -423,6 +424,10 @@ def qc_sample(h, seed: int, shots: int, out_dev_ptr: int):
     _check(lib().qc_sample(h, seed, shots, ctypes.c_void_p(out_dev_ptr)))
 
 
+def qc_probs_sample(h, probs_dev_ptr: int, seed: int, shots: int, out_dev_ptr: int):
+    _check(lib().qc_probs_sample(h, ctypes.c_void_p(probs_dev_ptr), seed, shots, ctypes.c_void_p(out_dev_ptr)))
+
+
 # --------------------------------------------------- torch-facing helpers ----
 
 def torch_dtype(dt: int):
@@ -531,6 +536,15 @@ class State:
         out = torch.empty(max(shots, 1), dtype=torch.int64, device=self.tensor.device)
         qc_sample(self.h, seed, shots, out.data_ptr())
         return out[:shots]
+
+    def probs_sample(self, seed, shots):
+        """(probabilities, outcomes) as probs() and sample(seed, shots) give
+        them, from one read of the state."""
+        import torch
+        p = torch.empty(1 << self.n, dtype=torch.float64, device=self.tensor.device)
+        out = torch.empty(max(shots, 1), dtype=torch.int64, device=self.tensor.device)
+        qc_probs_sample(self.h, p.data_ptr(), seed, shots, out.data_ptr())
+        return p, out[:shots]
 
 
 def version() -> str:

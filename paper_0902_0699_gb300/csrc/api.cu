@@ -476,6 +476,19 @@ QC_API qc_status qc_renormalize(qc_state* s, double* norm_out) {
   return launch_scale(s, 1.0 / sqrt(nrm));
 }
 
+QC_API qc_status qc_probs_sample(const qc_state* s, double* probs_dev, uint64_t seed, int64_t shots,
+                                 uint64_t* out_dev) {
+  clear_error();
+  qc_status st = check_state(s);
+  if (st) return st;
+  if (!probs_dev || shots < 0 || (shots > 0 && !out_dev)) {
+    set_error("NULL probabilities, bad shots (%lld) or NULL output", (long long)shots);
+    return QC_EINVAL;
+  }
+  if (shots == 0) return launch_probs(s, probs_dev);
+  return launch_sample(s, seed, shots, out_dev, probs_dev);
+}
+
 QC_API qc_status qc_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_t* out_dev) {
   clear_error();
   qc_status st = check_state(s);

@@ -328,7 +328,9 @@ qc_status reduce_norm(const qc_state* s, double* out_host);
 qc_status launch_probs(const qc_state* s, double* out);
 qc_status reduce_expect(const qc_state* s, uint64_t x, uint64_t z, double* out_host);
 qc_status launch_scale(qc_state* s, double f);
-qc_status launch_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_t* out);
+// probs: if not NULL, the Born probabilities are written there by the same
+// pass that forms the sampler's block weights.
+qc_status launch_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_t* out, double* probs = nullptr);
 
 // Dense k-qubit blocks (dense.cu): the qubit map of a block, the packed
 // device form of its operator, and an asynchronous launch.

@@ -538,20 +538,11 @@ __device__ __forceinline__ uint64_t thread_weights(const typename CT<R>::V2* __r
   return sum;
 }
 
-// Per-block weight sums (coalesced: the saturating sum does not depend on
-// which thread adds which weight); status bits for unusable probabilities.
-template <typename R>
-__global__ void __launch_bounds__(SMP_T) k_wsum(const typename CT<R>::V2* __restrict__ s, uint64_t N,
-                                                uint64_t* __restrict__ bsum, uint64_t* __restrict__ status) {
+// Block b's weight sum from each thread's partial sum t, into bsum[b];
+// status bit SMP_BAD_P if any thread saw an unusable probability.
+__device__ __forceinline__ void block_wsum_out(uint64_t t, bool bad, uint64_t* __restrict__ bsum,
+                                               uint64_t* __restrict__ status) {
   __shared__ uint64_t ws[SMP_T / 32];
-  const uint64_t base = (uint64_t)blockIdx.x * SMP_BLOCK;
-  bool bad = false;
-  uint64_t t = 0;
-#pragma unroll
-  for (int k = 0; k < SMP_PER; ++k) {
-    const uint64_t i = base + (uint64_t)k * SMP_T + threadIdx.x;
-    if (i < N) t = sat_add(t, weight_of<R>(s[i], &bad));
-  }
   for (int o = 16; o > 0; o >>= 1) t = sat_add(t, __shfl_xor_sync(0xffffffffu, t, o));
   if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = t;
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr((unsigned long long*)status, SMP_BAD_P);
@@ -562,9 +553,53 @@ __global__ void __launch_bounds__(SMP_T) k_wsum(const typename CT<R>::V2* __rest
   }
 }
 
+// Per-block weight sums (coalesced: the saturating sum does not depend on
+// which thread adds which weight); status bits for unusable probabilities.
+template <typename R>
+__global__ void __launch_bounds__(SMP_T) k_wsum(const typename CT<R>::V2* __restrict__ s, uint64_t N,
+                                                uint64_t* __restrict__ bsum, uint64_t* __restrict__ status) {
+  const uint64_t base = (uint64_t)blockIdx.x * SMP_BLOCK;
+  bool bad = false;
+  uint64_t t = 0;
+#pragma unroll
+  for (int k = 0; k < SMP_PER; ++k) {
+    const uint64_t i = base + (uint64_t)k * SMP_T + threadIdx.x;
+    if (i < N) t = sat_add(t, weight_of<R>(s[i], &bad));
+  }
+  block_wsum_out(t, bad, bsum, status);
+}
+
+// The same block sums, and the probabilities p_i written out, from one read
+// of the state (the Born probability is computed once and used for both).
+template <typename R>
+__global__ void __launch_bounds__(SMP_T) k_probs_wsum(const typename CT<R>::V2* __restrict__ s, uint64_t N,
+                                                      double* __restrict__ p, uint64_t* __restrict__ bsum,
+                                                      uint64_t* __restrict__ status) {
+  const uint64_t base = (uint64_t)blockIdx.x * SMP_BLOCK;
+  bool bad = false;
+  uint64_t t = 0;
+#pragma unroll
+  for (int k = 0; k < SMP_PER; ++k) {
+    const uint64_t i = base + (uint64_t)k * SMP_T + threadIdx.x;
+    if (i < N) {
+      const double pi = prob_of<R>(s[i]);
+      p[i] = pi;
+      t = sat_add(t, weight_of_p(pi, &bad));
+    }
+  }
+  block_wsum_out(t, bad, bsum, status);
+}
+
 static void launch_wsum(qc_dtype dt, const void* psi, uint64_t N, uint64_t* bsum, uint64_t* status,
-                        cudaStream_t st) {
+                        cudaStream_t st, double* probs = nullptr) {
   const unsigned nb = (unsigned)((N + SMP_BLOCK - 1) / SMP_BLOCK);
+  if (probs) {
+    if (dt == QC_C128)
+      k_probs_wsum<double><<<nb, SMP_T, 0, st>>>(reinterpret_cast<const double2*>(psi), N, probs, bsum, status);
+    else
+      k_probs_wsum<float><<<nb, SMP_T, 0, st>>>(reinterpret_cast<const float2*>(psi), N, probs, bsum, status);
+    return;
+  }
   if (dt == QC_C128)
     k_wsum<double><<<nb, SMP_T, 0, st>>>(reinterpret_cast<const double2*>(psi), N, bsum, status);
   else
@@ -720,7 +755,7 @@ __global__ void __launch_bounds__(SMP_T) k_sample_local(const typename CT<R>::V2
   }
 }
 
-qc_status launch_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_t* out) {
+qc_status launch_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_t* out, double* probs) {
   const uint64_t N = 1ull << s->n;
   const uint64_t nb = (N + SMP_BLOCK - 1) / SMP_BLOCK;
   const bool local = (uint64_t)shots <= nb;
@@ -739,7 +774,7 @@ qc_status launch_sample(const qc_state* s, uint64_t seed, int64_t shots, uint64_
     cudaFreeAsync(buf, s->stream);
     return cuda_fail(e, "sampler status reset");
   }
-  launch_wsum(s->dt, s->data, N, bsum, status, s->stream);
+  launch_wsum(s->dt, s->data, N, bsum, status, s->stream, probs);
   scan_block_sums(bsum, nb, csum, tail, status, s->stream);
   qc_status st = check_launch("sample weights", nb <= SCAN_CHUNK ? 2 : 4);
   uint64_t h[2] = {0, 0};

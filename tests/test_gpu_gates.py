@@ -330,6 +330,33 @@ def test_sample_sparse_state(qc, shots):
     assert set(got.tolist()) <= {5, 40000, 40001, 131071}
 
 
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n,shots", [(1, 5), (11, 1), (12, 3), (16, 33), (20, 1000), (24, 5), (24, 8193)])
+def test_probs_sample_one_pass(qc, dt, n, shots):
+    # the fused entry point writes what qc_probs writes and draws what
+    # qc_sample draws: block-local rescans, the full CDF, one block (n < 11),
+    # and the chunked block scan (n = 24)
+    s, v = mk(qc, n, dt, seed=3 * n + shots + dt)
+    pr = O.probs(as_dt(v, dt), n)
+    for seed in (0, 2 ** 35 + 9):
+        p, got = s.probs_sample(seed, shots)
+        assert np.array_equal(p.cpu().numpy(), pr)
+        got = got.cpu().numpy().astype(np.uint64)
+        assert np.array_equal(got, O.sample_from_probs(pr, seed, shots))
+        assert np.array_equal(got, s.sample(seed, shots).cpu().numpy().astype(np.uint64))
+    p, got = s.probs_sample(1, 0)  # no shots: probabilities only
+    assert got.numel() == 0 and np.array_equal(p.cpu().numpy(), pr)
+
+
+def test_probs_sample_rejects_unusable_probabilities(qc):
+    n = 13
+    vec = np.full(1 << n, 1.5 + 0j)
+    s, _ = mk(qc, n, 0, vec=vec)
+    with pytest.raises(qc.QCError) as e:
+        s.probs_sample(1, 10)
+    assert e.value.status == qc.QC_EINVAL
+
+
 def test_sample_rejects_unusable_probabilities(qc):
     n = 13
     for vec in (np.zeros(1 << n, dtype=complex), np.full(1 << n, 1.5 + 0j), np.full(1 << n, 0.9 + 0j)):
