@@ -217,6 +217,76 @@ __global__ void __launch_bounds__(ADJ_T) k_fwd_rot2(typename CT<R>::V2* __restri
   }
 }
 
+// The same pass for complex64 with 16-byte accesses: an item is two
+// neighbouring pairs (q >= 1: amplitudes i0, i0+1 and i0 + 2^q, i0 + 2^q + 1)
+// or one pair (q = 0: amplitudes 2v, 2v+1 in one vector); four items per
+// trip on three blocks per SM (eight-byte loads, one pair per trip, streamed
+// the 64-state batch at 0.78 of copy bandwidth on GB300).
+constexpr int FWD_UNR = 4;
+__device__ __forceinline__ void rot_v(const Mat2<float>& M, float4& A, float4& B) {
+  Cx<float> a0 = cmake(A.x, A.y), c0 = cmake(A.z, A.w), a1 = cmake(B.x, B.y), c1 = cmake(B.z, B.w);
+  apply2<float, MK_GENERAL>(M, a0, a1);
+  apply2<float, MK_GENERAL>(M, c0, c1);
+  A = make_float4(a0.re, a0.im, c0.re, c0.im);
+  B = make_float4(a1.re, a1.im, c1.re, c1.im);
+}
+__global__ void __launch_bounds__(ADJ_T, 4) k_fwd_rot2_c64(float2* __restrict__ psi, int n, GateDev ga, GateDev gb,
+                                                           const double* __restrict__ theta, int64_t stride) {
+  const int b = blockIdx.y;
+  float2* s = psi + ((uint64_t)b << n);
+  const Mat2<float> M = block_matrix<float>(ga.kind, theta[(int64_t)b * stride + ga.param], gb.kind,
+                                            theta[(int64_t)b * stride + gb.param]);
+  const int q = ga.q0;
+  const uint64_t G = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q == 0) {
+    float4* w = reinterpret_cast<float4*>(s);
+    const uint64_t items = 1ull << (n - 1);
+    for (; v + (FWD_UNR - 1) * G < items; v += FWD_UNR * G) {
+      float4 A[FWD_UNR];
+#pragma unroll
+      for (int u = 0; u < FWD_UNR; ++u) A[u] = w[v + u * G];
+#pragma unroll
+      for (int u = 0; u < FWD_UNR; ++u) {
+        Cx<float> a0 = cmake(A[u].x, A[u].y), a1 = cmake(A[u].z, A[u].w);
+        apply2<float, MK_GENERAL>(M, a0, a1);
+        w[v + u * G] = make_float4(a0.re, a0.im, a1.re, a1.im);
+      }
+    }
+    for (; v < items; v += G) {
+      const float4 A = w[v];
+      Cx<float> a0 = cmake(A.x, A.y), a1 = cmake(A.z, A.w);
+      apply2<float, MK_GENERAL>(M, a0, a1);
+      w[v] = make_float4(a0.re, a0.im, a1.re, a1.im);
+    }
+    return;
+  }
+  const uint64_t items = 1ull << (n - 2), st = 1ull << q;
+  for (; v + (FWD_UNR - 1) * G < items; v += FWD_UNR * G) {
+    uint64_t i0[FWD_UNR];
+    float4 A[FWD_UNR], B[FWD_UNR];
+#pragma unroll
+    for (int u = 0; u < FWD_UNR; ++u) {
+      i0[u] = insert0(2 * (v + u * G), q);
+      A[u] = *reinterpret_cast<const float4*>(s + i0[u]);
+      B[u] = *reinterpret_cast<const float4*>(s + (i0[u] | st));
+    }
+#pragma unroll
+    for (int u = 0; u < FWD_UNR; ++u) {
+      rot_v(M, A[u], B[u]);
+      *reinterpret_cast<float4*>(s + i0[u]) = A[u];
+      *reinterpret_cast<float4*>(s + (i0[u] | st)) = B[u];
+    }
+  }
+  for (; v < items; v += G) {
+    const uint64_t i0 = insert0(2 * v, q);
+    float4 A = *reinterpret_cast<const float4*>(s + i0), B = *reinterpret_cast<const float4*>(s + (i0 | st));
+    rot_v(M, A, B);
+    *reinterpret_cast<float4*>(s + i0) = A;
+    *reinterpret_cast<float4*>(s + (i0 | st)) = B;
+  }
+}
+
 // CNOT ring CNOT(0,1) .. CNOT(n-2,n-1), CNOT(n-1,0) as a basis permutation
 // j -> A(j): A(j)_k = j_0 ^ .. ^ j_k for k >= 1 and A(j)_0 = j_1 ^ .. ^ j_{n-1}.
 __device__ __forceinline__ uint64_t ring_fwd(uint64_t x, int n) {
@@ -499,6 +569,10 @@ template <typename R>
 static int forward_passes(const std::vector<AdjOp>& ops, int n, int B, const double* theta, int64_t stride,
                           Bufs<R>& bf, cudaStream_t st) {
   const dim3 grid(gx_for<R>(n, B), B);
+  // complex64 rotation pairs: three blocks per SM over the whole batch
+  const uint64_t vitems = n >= 2 ? (1ull << (n - 2)) : 1ull;
+  const unsigned gxv = (unsigned)std::max<uint64_t>(
+      1, std::min<uint64_t>((vitems + FWD_UNR * ADJ_T - 1) / (FWD_UNR * ADJ_T), 3ull * sm_count() / (uint64_t)B));
   const uint64_t tot = (uint64_t)B << n;
   k_zero_state_batch<R><<<grid_for(tot, ADJ_T, 8), ADJ_T, 0, st>>>(bf.psi, n, B);
   int nk = 1;
@@ -507,6 +581,14 @@ static int forward_passes(const std::vector<AdjOp>& ops, int n, int B, const dou
       k_ring<R><<<grid, ADJ_T, 0, st>>>(bf.psi, bf.spare, n, 0);
       std::swap(bf.psi, bf.spare);
     } else if (op.kind == AOP_ROT2) {
+      if constexpr (sizeof(R) == 4) {
+        if (n >= 2) {
+          k_fwd_rot2_c64<<<dim3(gxv, B), ADJ_T, 0, st>>>(reinterpret_cast<float2*>(bf.psi), n, op.a, op.b, theta,
+                                                         stride);
+          ++nk;
+          continue;
+        }
+      }
       k_fwd_rot2<R><<<grid, ADJ_T, 0, st>>>(bf.psi, n, op.a, op.b, theta, stride);
     } else {
       k_fwd_gate<R><<<grid, ADJ_T, 0, st>>>(bf.psi, n, op.a, theta, stride);
