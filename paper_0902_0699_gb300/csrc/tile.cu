@@ -615,53 +615,56 @@ qc_status launch_hall(qc_state* s) {
 }
 
 // ------------------------------------------------------- bit reversal ----
-// In-place reversal of all n index bits.  Index = (h, m, l) with h, l of b
+// In-place reversal of all n index bits.  Index = (h, m, l) with h, l of B
 // bits: rev(h, m, l) = (rev l, rev m, rev h).  The block for middle value m
-// (with m <= rev m) exchanges the 2^b x 2^b tiles of m and rev m through
-// shared memory (rows of 2^b contiguous amplitudes, padded against bank
-// conflicts).  Launched with b = 5 and 256 threads (4 elements per thread
-// and tile).
-template <typename R>
-__global__ void __launch_bounds__(256) k_bitrev(typename CT<R>::V2* __restrict__ s, int n, int b) {
+// (with m <= rev m) exchanges the 2^B x 2^B tiles of m and rev m through
+// shared memory (rows of 2^B contiguous amplitudes, padded against bank
+// conflicts).  The pass is latency bound (load both tiles, synchronise,
+// store), so many small blocks beat few large ones: complex128 runs B = 4
+// with 128 threads (twelve blocks per SM; 0.76 of copy bandwidth on GB300
+// at 30 qubits, against 0.63 for B = 5 with 256 threads); complex64 keeps
+// B = 5 with 256 threads (rows of 256 bytes).
+template <typename R, int B, int T>
+__global__ void __launch_bounds__(T) k_bitrev(typename CT<R>::V2* __restrict__ s, int n) {
   using V2 = typename CT<R>::V2;
-  const int W = 1 << b, WP = W + 1;
+  constexpr int W = 1 << B, WP = W + 1, PER = W * W / T;
+  static_assert(PER * T == W * W, "whole tiles per block");
   extern __shared__ __align__(16) unsigned char smraw[];
   V2* A = reinterpret_cast<V2*>(smraw);
-  V2* B = A + W * WP;
-  const int nm = n - 2 * b;
+  V2* Bt = A + W * WP;
+  const int nm = n - 2 * B;
   const uint64_t M = 1ull << nm;
   for (uint64_t m = blockIdx.x; m < M; m += gridDim.x) {
     const uint64_t mr = nm ? (__brevll((unsigned long long)m) >> (64 - nm)) : 0ull;
     if (mr < m) continue;
     // every load of both tiles in flight before the first shared-memory store
-    // (W * W = 4 blockDim.x elements per tile)
     {
-      V2 va[4], vb[4];
+      V2 va[PER], vb[PER];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int e = threadIdx.x + u * blockDim.x;
-        const int h = e >> b, l = e & (W - 1);
-        va[u] = s[((uint64_t)h << (n - b)) | (m << b) | (uint64_t)l];
-        if (mr != m) vb[u] = s[((uint64_t)h << (n - b)) | (mr << b) | (uint64_t)l];
+      for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + u * T;
+        const int h = e >> B, l = e & (W - 1);
+        va[u] = s[((uint64_t)h << (n - B)) | (m << B) | (uint64_t)l];
+        if (mr != m) vb[u] = s[((uint64_t)h << (n - B)) | (mr << B) | (uint64_t)l];
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int e = threadIdx.x + u * blockDim.x;
-        const int h = e >> b, l = e & (W - 1);
+      for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + u * T;
+        const int h = e >> B, l = e & (W - 1);
         A[h * WP + l] = va[u];
-        if (mr != m) B[h * WP + l] = vb[u];
+        if (mr != m) Bt[h * WP + l] = vb[u];
       }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
-      const int h = e >> b, l = e & (W - 1);
-      const int rl = (int)(__brev((unsigned)l) >> (32 - b)), rh = (int)(__brev((unsigned)h) >> (32 - b));
+    for (int e = threadIdx.x; e < W * W; e += T) {
+      const int h = e >> B, l = e & (W - 1);
+      const int rl = (int)(__brev((unsigned)l) >> (32 - B)), rh = (int)(__brev((unsigned)h) >> (32 - B));
       // element (h, m, l) of the output is the input at rev(h, m, l)
       if (mr != m) {
-        s[((uint64_t)h << (n - b)) | (m << b) | (uint64_t)l] = B[rl * WP + rh];
-        s[((uint64_t)h << (n - b)) | (mr << b) | (uint64_t)l] = A[rl * WP + rh];
+        s[((uint64_t)h << (n - B)) | (m << B) | (uint64_t)l] = Bt[rl * WP + rh];
+        s[((uint64_t)h << (n - B)) | (mr << B) | (uint64_t)l] = A[rl * WP + rh];
       } else {
-        s[((uint64_t)h << (n - b)) | (m << b) | (uint64_t)l] = A[rl * WP + rh];
+        s[((uint64_t)h << (n - B)) | (m << B) | (uint64_t)l] = A[rl * WP + rh];
       }
     }
     __syncthreads();
@@ -688,15 +691,15 @@ static qc_status bitrev_impl(qc_state* s) {
   using V2 = typename CT<R>::V2;
   V2* d = reinterpret_cast<V2*>(s->data);
   const int n = s->n;
-  const int b = 5;
+  constexpr int b = sizeof(R) == 8 ? 4 : 5, T = sizeof(R) == 8 ? 128 : 256;
   if (n < 2 * b) {
     k_bitrev_small<R><<<1, 256, sizeof(V2) << n, s->stream>>>(d, n);
     return check_launch("bitrev small");
   }
   const size_t smem = 2 * (size_t)(1 << b) * ((1 << b) + 1) * sizeof(V2);
   const uint64_t M = 1ull << (n - 2 * b);
-  const unsigned grid = resident_grid(k_bitrev<R>, 256, (int64_t)M, 1, smem);
-  k_bitrev<R><<<grid, 256, smem, s->stream>>>(d, n, b);
+  const unsigned grid = resident_grid(k_bitrev<R, b, T>, T, (int64_t)M, 1, smem);
+  k_bitrev<R, b, T><<<grid, T, smem, s->stream>>>(d, n);
   return check_launch("bitrev");
 }
 
