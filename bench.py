@@ -356,11 +356,20 @@ def run_e2e(args, st, step_fn, ops_per_step, N):
     ev_free = [torch.cuda.Event(), torch.cuda.Event()]
     issued_free = [False, False]
 
+    copies = {"h2d": [], "d2h": []}  # (start, end) events per copy, on the copy's own stream
+
+    def timed_copy(kind, stream, fn):
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        z.record(stream)
+        copies[kind].append((a, z))
+
     def upload(b):
         with torch.cuda.stream(s_in):
             if issued_free[b]:
                 s_in.wait_event(ev_free[b])  # the previous download of this buffer is done
-            states[b].tensor.copy_(host_in, non_blocking=True)
+            timed_copy("h2d", s_in, lambda: states[b].tensor.copy_(host_in, non_blocking=True))
             ev_in[b].record(s_in)
 
     def run(b):
@@ -370,7 +379,7 @@ def run_e2e(args, st, step_fn, ops_per_step, N):
         ev_done[b].record(comp)
         with torch.cuda.stream(s_out):
             s_out.wait_event(ev_done[b])
-            host_out.copy_(states[b].tensor, non_blocking=True)
+            timed_copy("d2h", s_out, lambda: host_out.copy_(states[b].tensor, non_blocking=True))
             host_shots.copy_(shots, non_blocking=True)
             ev_free[b].record(s_out)
         issued_free[b] = True
@@ -385,15 +394,21 @@ def run_e2e(args, st, step_fn, ops_per_step, N):
                 upload(i % 2)
     pipeline(2)  # warm-up
     torch.cuda.synchronize()
+    copies["h2d"].clear()
+    copies["d2h"].clear()
     t0 = time.perf_counter()
     pipeline(args.steps)
     torch.cuda.synchronize()
     el = (time.perf_counter() - t0) * 1e3
+    # the host link's rate as each copy saw it (the copies overlap compute)
+    rate = {k: statistics.mean(N * amp / (a.elapsed_time(z) * 1e-3) / 1e9 for a, z in v) if v else None
+            for k, v in copies.items()}
     tmax, wsum = aggregate(el, float(ops_per_step) * N * args.steps)
     st2.close()
     del host_in, host_out
     return {"value": wsum / (tmax / 1e3), "unit": UNIT, "h2d_bytes_per_step": N * amp + 8 * 8,
             "d2h_bytes_per_step": N * amp + 8 * 1000, "ms_per_step": tmax / args.steps,
+            "h2d_GBps_seen": rate["h2d"], "d2h_GBps_seen": rate["d2h"],
             "note": "host state in pinned memory -> device, full step, final state and samples -> host; "
                     "two device states in turn, uploads and downloads on their own streams overlap compute"}
 
