@@ -132,7 +132,7 @@ def test_hall_and_layer(qc, dt, n):
 
 
 @pytest.mark.parametrize("dt", [0, 1])
-@pytest.mark.parametrize("n", [1, 2, 3, 5, 9, 10, 11, 12, 13, 16, 19])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7, 8, 9, 10, 11, 12, 13, 16, 19])
 def test_qft_vs_oracle(qc, dt, n):
     s, v = mk(qc, n, dt, seed=50 + n)
     ref = O.qft(as_dt(v, dt).copy(), n)
