@@ -192,6 +192,16 @@ FF_HD ff ff_add(ff a, ff b) {
 }
 FF_HD ff ff_neg(ff a) { return ff_make(-a.hi, -a.lo); }
 FF_HD ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+// a + b without the final renormalisation: hi = fl(a.hi + b.hi), lo = its
+// exact rounding error plus the low parts, so hi + lo holds the sum to the
+// same accuracy; only for a value that goes straight into another ff_add
+// (whose two-sum of the high parts is exact for any inputs).
+FF_HD ff ff_add_u(ff a, ff b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return ff_make(s, ff_add_rn(e, ff_add_rn(a.lo, b.lo)));
+}
+FF_HD ff ff_sub_u(ff a, ff b) { return ff_add_u(a, ff_neg(b)); }
 
 FF_HD ff ff_mul(ff a, ff b) {
   const float p = ff_mul_rn(a.hi, b.hi);
@@ -231,6 +241,8 @@ FF_HD ffc ffc_make(ff re, ff im) {
 }
 FF_HD ffc ffc_add(ffc a, ffc b) { return ffc_make(ff_add(a.re, b.re), ff_add(a.im, b.im)); }
 FF_HD ffc ffc_sub(ffc a, ffc b) { return ffc_make(ff_sub(a.re, b.re), ff_sub(a.im, b.im)); }
+FF_HD ffc ffc_add_u(ffc a, ffc b) { return ffc_make(ff_add_u(a.re, b.re), ff_add_u(a.im, b.im)); }
+FF_HD ffc ffc_sub_u(ffc a, ffc b) { return ffc_make(ff_sub_u(a.re, b.re), ff_sub_u(a.im, b.im)); }
 FF_HD ffc ffc_mul(ffc a, ffc b) {
   return ffc_make(ff_dot2m(a.re, b.re, a.im, b.im), ff_dot2p(a.re, b.im, a.im, b.re));
 }

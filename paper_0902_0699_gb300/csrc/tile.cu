@@ -52,6 +52,9 @@ template <> struct TA<float> {
   __device__ static V2 to(E z) { return make_float2(z.re, z.im); }
   __device__ static E add(E a, E b) { return cmake<float>(a.re + b.re, a.im + b.im); }
   __device__ static E sub(E a, E b) { return cmake<float>(a.re - b.re, a.im - b.im); }
+  // first level of a radix-4 step (no renormalisation to skip in FP32)
+  __device__ static E add_u(E a, E b) { return add(a, b); }
+  __device__ static E sub_u(E a, E b) { return sub(a, b); }
   __device__ static E mul(E a, E b) { return cmul(a, b); }
   __device__ static E times_i(E a) { return cmake<float>(-a.im, a.re); }
   __device__ static E neg(E a) { return cmake<float>(-a.re, -a.im); }
@@ -91,6 +94,10 @@ template <> struct TA<double> {
   __device__ static V2 to(E z) { return make_double2(ff_to_d(z.re), ff_to_d(z.im)); }
   __device__ static E add(E a, E b) { return ffc_add(a, b); }
   __device__ static E sub(E a, E b) { return ffc_sub(a, b); }
+  // first level of a radix-4 step: its sums feed the second level's adds
+  // directly, so their renormalisation is left to those
+  __device__ static E add_u(E a, E b) { return ffc_add_u(a, b); }
+  __device__ static E sub_u(E a, E b) { return ffc_sub_u(a, b); }
   __device__ static E mul(E a, E b) { return ffc_mul(a, b); }
   __device__ static E times_i(E a) { return ffc_make(ff_neg(a.im), a.re); }
   __device__ static E neg(E a) { return ffc_make(ff_neg(a.re), ff_neg(a.im)); }
@@ -337,8 +344,8 @@ __global__ void __launch_bounds__(512, QREG ? 1 : 2) k_tile(typename CT<R>::V2* 
           const int e01 = e00 | (1 << bl), e10 = e00 | (1 << bh), e11 = e01 | (1 << bh);
           const E a00 = sm[e00], a01 = sm[e01], a10 = sm[e10], a11 = sm[e11];
           // level jh on bit bh: pairs (e00, e10), (e01, e11)
-          const E s0 = A::add(a00, a10), d0 = A::sub(a00, a10);
-          const E s1 = A::add(a01, a11), d1 = A::sub(a01, a11);
+          const E s0 = A::add_u(a00, a10), d0 = A::sub_u(a00, a10);
+          const E s1 = A::add_u(a01, a11), d1 = A::sub_u(a01, a11);
           E t0, u0, t1, u1;
           if (lad) {
             // With L(y) = e^{2 pi i y / 2^{jh+1}} and x = group bits below jl:

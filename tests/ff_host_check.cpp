@@ -70,6 +70,20 @@ int main() {
     // joins of arithmetic results stay within the same bound
     const double j = ff_to_d(ff_add(A, B));
     if (std::fabs(j - ((long double)a + b)) > std::ldexp(sc, -44)) return fail("join add", a, b, j - (a + b));
+    // unnormalised first-level sums (radix-4 butterflies) carry the value, and
+    // a normalising second level over them keeps the bound
+    err = std::fabs(val(ff_add_u(A, B)) - ((long double)a + b));
+    if (err > std::ldexp(sc, -45)) return fail("add_u", a, b, err);
+    err = std::fabs(val(ff_sub_u(A, B)) - ((long double)a - b));
+    if (err > std::ldexp(sc, -45)) return fail("sub_u", a, b, err);
+    const long double sc4 = sc + std::fabs(c) + std::fabs(d);
+    const ff S0 = ff_add_u(A, B), S1 = ff_add_u(C, D), D0 = ff_sub_u(A, B), D1 = ff_sub_u(C, D);
+    err = std::fabs(val(ff_add(S0, S1)) - (((long double)a + b) + ((long double)c + d)));
+    if (err > std::ldexp(sc4, -44)) return fail("radix4 t0", a, c, err);
+    err = std::fabs(val(ff_sub(D0, D1)) - (((long double)a - b) - ((long double)c - d)));
+    if (err > std::ldexp(sc4, -44)) return fail("radix4 u1", a, c, err);
+    const ff T = ff_add(S0, S1);
+    if (std::fabs(T.lo) > std::fabs(T.hi) * std::ldexp(1.0, -23)) return fail("radix4 norm", a, c, T.lo);
   }
   printf("ok\n");
   return 0;
