@@ -45,6 +45,26 @@ def test_tensor_core_block_c64(qc, n, qubits):
     assert run(qc, n, 1, qubits, U, seed=n) <= 1e-5
 
 
+@pytest.mark.parametrize("qubits", [[0, 1, 2, 3, 4], [5, 6, 7, 8, 9], [19, 3, 14, 9, 11]])
+def test_tensor_core_block_c64_relative_accuracy(qc, qubits):
+    # 3xTF32 keeps a block at FP32-class accuracy: relative to the state
+    # (not to 1e-5 absolute, which plain TF32 would also meet at small n).
+    # The tensor cores' FP32 accumulation leaves a uniform shrink of about
+    # 7e-7 per block; anything near TF32's 2^-11 would fail here.
+    n = 20
+    U = unitary(W.rng(900 + sum(qubits)), 32)
+    s = qc.State(n, 1)
+    v = W.random_state(W.rng(901), n)
+    s.load(v)
+    x = v.astype(np.complex64).astype(np.complex128)
+    qc.qc_apply_dense(s.h, qubits, U)
+    got = s.numpy().astype(np.complex128)
+    ref = O.apply_dense(x, n, list(qubits), U)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 2e-6
+    scale = np.vdot(ref, got) / np.vdot(ref, ref) - 1
+    assert abs(scale) <= 2e-6
+
+
 @pytest.mark.parametrize("dt", [0, 1])
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
 def test_cuda_core_block(qc, dt, k):
