@@ -55,6 +55,7 @@ template <> struct TA<float> {
   // first level of a radix-4 step (no renormalisation to skip in FP32)
   __device__ static E add_u(E a, E b) { return add(a, b); }
   __device__ static E sub_u(E a, E b) { return sub(a, b); }
+  __device__ static E norm(E a) { return a; }
   __device__ static E mul(E a, E b) { return cmul(a, b); }
   __device__ static E times_i(E a) { return cmake<float>(-a.im, a.re); }
   __device__ static E neg(E a) { return cmake<float>(-a.re, -a.im); }
@@ -98,6 +99,17 @@ template <> struct TA<double> {
   // directly, so their renormalisation is left to those
   __device__ static E add_u(E a, E b) { return ffc_add_u(a, b); }
   __device__ static E sub_u(E a, E b) { return ffc_sub_u(a, b); }
+  // the closing renormalisation of an unnormalised sum (fast two-sum per
+  // component), for a value stored without passing through a product
+  __device__ static E norm(E a) {
+    float h, l;
+    ffc r;
+    fast_two_sum(a.re.hi, a.re.lo, h, l);
+    r.re = ff_make(h, l);
+    fast_two_sum(a.im.hi, a.im.lo, h, l);
+    r.im = ff_make(h, l);
+    return r;
+  }
   __device__ static E mul(E a, E b) { return ffc_mul(a, b); }
   __device__ static E times_i(E a) { return ffc_make(ff_neg(a.im), a.re); }
   __device__ static E neg(E a) { return ffc_make(ff_neg(a.re), ff_neg(a.im)); }
@@ -357,15 +369,21 @@ __global__ void __launch_bounds__(512, QREG ? 1 : 2) k_tile(typename CT<R>::V2* 
             const int x = (e00 >> c) & ((1 << jl) - 1);
             const E id1 = A::times_i(d1);
             t0 = A::add(s0, s1);
-            u0 = A::sub(s0, s1);
-            t1 = A::add(d0, id1);
-            u1 = A::sub(d0, id1);
+            // the products renormalise u0, t1, u1; without one (x = 0) the
+            // closing fast two-sum does
+            u0 = A::sub_u(s0, s1);
+            t1 = A::add_u(d0, id1);
+            u1 = A::sub_u(d0, id1);
             if (x) {
               u0 = A::mul(ladder(jh, 2 * x), u0);
               t1 = A::mul(ladder(jh, x), t1);
               const int x3 = 3 * x;  // < 1.5 2^jh; L(y + 2^jh) = -L(y)
               u1 = A::mul(ladder(jh, x3 & ((1 << jh) - 1)), u1);
               if (x3 >> jh) u1 = A::neg(u1);
+            } else {
+              u0 = A::norm(u0);
+              t1 = A::norm(t1);
+              u1 = A::norm(u1);
             }
           } else {  // plain butterflies on both bits
             t0 = A::add(s0, s1);

@@ -84,6 +84,12 @@ int main() {
     if (err > std::ldexp(sc4, -44)) return fail("radix4 u1", a, c, err);
     const ff T = ff_add(S0, S1);
     if (std::fabs(T.lo) > std::fabs(T.hi) * std::ldexp(1.0, -23)) return fail("radix4 norm", a, c, T.lo);
+    // a product over an unnormalised sum (the twiddle after a radix-4 step)
+    const long double pm = (long double)c * ((long double)a - b);
+    err = std::fabs(val(ff_mul(C, D0)) - pm);
+    if (err > std::ldexp(std::fabs(c) * sc, -43)) return fail("mul over sub_u", a, c, err);
+    err = std::fabs(val(ff_dot2m(C, D0, D, S0)) - (pm - (long double)d * ((long double)a + b)));
+    if (err > std::ldexp((std::fabs(c) + std::fabs(d)) * sc, -43)) return fail("dot2m over add_u", a, c, err);
   }
   printf("ok\n");
   return 0;
