@@ -430,6 +430,118 @@ def qc_probs_sample(h, probs_dev_ptr: int, seed: int, shots: int, out_dev_ptr: i
 
 # --------------------------------------------------- torch-facing helpers ----
 
+# ---- the remaining entry points under their C names (argument marshalling
+# only; the classes below wrap the same calls for everyday use) ----
+
+def qc_version() -> str:
+    return lib().qc_version().decode()
+
+
+def qc_last_error() -> str:
+    return last_error()
+
+
+def qc_kernel_launches() -> int:
+    return int(lib().qc_kernel_launches())
+
+
+def qc_state_info(h):
+    """(device pointer, n, dtype) of a state handle."""
+    p, n, dt = _VP(), _I(), _I()
+    _check(lib().qc_state_info(h, ctypes.byref(p), ctypes.byref(n), ctypes.byref(dt)))
+    return p.value, n.value, dt.value
+
+
+def qc_sample_noalloc(psi_dev_ptr: int, n: int, dt: int, seed: int, shots: int, out_dev_ptr: int, stream=None):
+    _check(lib().qc_sample_noalloc(_VP(psi_dev_ptr), n, dt, seed, shots, _VP(out_dev_ptr), _stream_handle(stream)))
+
+
+def _gate_array(gates):
+    if isinstance(gates, ctypes.Array):
+        return gates, len(gates)
+    gl = [tuple(int(v) for v in g) for g in gates]
+    return (Gate * max(1, len(gl)))(*[Gate(*g) for g in gl]), len(gl)
+
+
+def _term_array(terms):
+    if isinstance(terms, ctypes.Array):
+        return terms, len(terms)
+    tl = [(int(x), int(z), float(c)) for (x, z, c) in terms]
+    return (PauliTerm * max(1, len(tl)))(*[PauliTerm(*t) for t in tl]), len(tl)
+
+
+def qc_circuit_forward(n: int, dt: int, B: int, gates, theta_dev_ptr: int, theta_stride: int, psi_dev_ptr: int,
+                       stream=None):
+    """gates: (kind, q0, q1, param) tuples or a Gate array."""
+    ga, ng = _gate_array(gates)
+    _check(lib().qc_circuit_forward(n, dt, B, ga, ng, _VP(theta_dev_ptr), theta_stride, _VP(psi_dev_ptr),
+                                    _stream_handle(stream)))
+
+
+def qc_adjoint_grad(n: int, dt: int, B: int, gates, theta_dev_ptr: int, theta_stride: int, n_params: int, terms,
+                    psi_dev_ptr: int, lam_dev_ptr: int, energy_dev_ptr: int, grad_dev_ptr: int, stream=None):
+    """gates as for qc_circuit_forward; terms: (xmask, zmask, coeff) tuples or
+    a PauliTerm array."""
+    ga, ng = _gate_array(gates)
+    ta, nt = _term_array(terms)
+    _check(lib().qc_adjoint_grad(n, dt, B, ga, ng, _VP(theta_dev_ptr), theta_stride, n_params, ta, nt,
+                                 _VP(psi_dev_ptr), _VP(lam_dev_ptr), _VP(energy_dev_ptr), _VP(grad_dev_ptr),
+                                 _stream_handle(stream)))
+
+
+def qc_fused_plan_create(n: int, ops, kmax: int = 5, pad: bool = True):
+    """A plan handle for ops as FusedPlan takes them; free with
+    qc_fused_plan_free."""
+    plan = FusedPlan(n, ops, kmax=kmax, pad=pad)
+    h, plan.h = plan.h, None  # hand the handle over
+    return h
+
+
+def qc_fused_plan_info(plan):
+    nb, km = _I(), _I()
+    _check(lib().qc_fused_plan_info(plan, ctypes.byref(nb), ctypes.byref(km)))
+    return nb.value, km.value
+
+
+def qc_fused_plan_block(plan, i: int):
+    """(qubits, U) of block i."""
+    k = _I()
+    qs = (_I * 6)()
+    _check(lib().qc_fused_plan_block(plan, i, ctypes.byref(k), qs, None))
+    U = np.zeros(2 << (2 * k.value))
+    _check(lib().qc_fused_plan_block(plan, i, None, None, _dptr(U)))
+    d = 1 << k.value
+    return [qs[j] for j in range(k.value)], (U[0::2] + 1j * U[1::2]).reshape(d, d)
+
+
+def qc_fused_plan_run(state_h, plan):
+    _check(lib().qc_fused_plan_run(state_h, plan))
+
+
+def qc_fused_plan_free(plan):
+    _check(lib().qc_fused_plan_free(plan))
+
+
+def qc_traj_plan_create(desc: "TrajDesc", stream=None, autotune: bool = True):
+    h = _VP()
+    _check(lib().qc_traj_plan_create(ctypes.byref(desc), _stream_handle(stream), int(bool(autotune)), ctypes.byref(h)))
+    return h
+
+
+def qc_traj_plan_run(plan, out: "TrajOut"):
+    _check(lib().qc_traj_plan_run(plan, ctypes.byref(out)))
+
+
+def qc_traj_plan_info(plan):
+    v = [_I(), _I(), _I()]
+    _check(lib().qc_traj_plan_info(plan, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def qc_traj_plan_free(plan):
+    _check(lib().qc_traj_plan_free(plan))
+
+
 def torch_dtype(dt: int):
     import torch
     return torch.complex128 if dt == QC_C128 else torch.complex64

@@ -32,6 +32,13 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
 
 
+def test_binding_has_every_declared_name():
+    # the Python binding offers each C entry point under its own name
+    import paper_0902_0699_gb300 as qc
+    missing = [n for n in header_functions() if not callable(getattr(qc, n, None))]
+    assert not missing, missing
+
+
 def test_binding_loads_without_gpu():
     import paper_0902_0699_gb300 as qc
     assert "sm_103a" in qc.version()
