@@ -2,10 +2,13 @@
 """Benchmark of the state-vector gate engine on GB300.
 
 One step = one pass of the hot path over the 30-qubit complex128 workload:
-  HALL|0..0> (uniform fill), 100 Grover iterations with 8 seeded marked
-  items (oracle + diffusion, one fused pass each), the QFT, the Born-rule
-  probabilities and 1000 seeded samples, then the per-gate sweep H(t),
-  CNOT((t+1) mod n, t), CPHASE((t+1) mod n, t, k=1) for t = 0..n-1.
+  HALL on |0..0> (the step's input state; qc_hall, n Hadamards in fused
+  tile passes), 100 Grover iterations with 8 seeded marked items (oracle +
+  diffusion, one fused pass each), the QFT, the Born-rule probabilities and
+  1000 seeded samples, then the per-gate sweep H(t), CNOT((t+1) mod n, t),
+  CPHASE((t+1) mod n, t, k=1) for t = 0..n-1.  In the device-timed loop
+  each step first writes its input |0..0> (qc_state_reset, inside the timed
+  region); the end-to-end loop uploads it from host memory instead.
 Metric: amplitude-updates/s = 2^n x (operators applied per step) / step
 time, where HALL, each Grover operator G, the QFT and each swept gate count
 as one operator acting on all 2^n amplitudes (192 operators per step at
@@ -199,10 +202,14 @@ def run_ours(args, ws, rank, local):
     ops_per_step = 1 + iters + 1 + 3 * n
 
     def step(ev: Events | None, sweep_ev=None, state=None):
+        # state: an uploaded |0..0> (end-to-end loop); else write it here
         st_ = state if state is not None else st
         if ev: ev.mark("start")
-        st_.uniform()
-        if ev: ev.mark("hall_uniform")
+        if state is None:
+            st_.reset(0)
+        if ev: ev.mark("input_reset")
+        st_.hall()
+        if ev: ev.mark("hall")
         for _ in range(iters):
             st_.grover_step(marked)
         if ev: ev.mark("grover")
@@ -276,7 +283,8 @@ def run_ours(args, ws, rank, local):
     kernels = {
         "grover_step (prep+pass+fix)": {"ms": grover_ms, "alg_bytes": 2 * S, "GB/s": gb(2 * S, grover_ms),
                                         "launches_per_step": iters * 3},
-        "hall_uniform_fill": {"ms": comp["hall_uniform"], "alg_bytes": S, "GB/s": gb(S, comp["hall_uniform"])},
+        "input_reset (|0..0>)": {"ms": comp["input_reset"], "alg_bytes": S, "GB/s": gb(S, comp["input_reset"])},
+        "hall": {"ms": comp["hall"], "alg_bytes": hall_bytes(n, amp), "GB/s": gb(hall_bytes(n, amp), comp["hall"])},
         "qft": {"ms": comp["qft"], "alg_bytes": qft_bytes(n, amp), "GB/s": gb(qft_bytes(n, amp), comp["qft"])},
     }
     sweep_table = {}
@@ -294,6 +302,15 @@ def run_ours(args, ws, rank, local):
                 "frac": round(achieved / hbm, 4), "traffic": traffic,
                 "kernel": "k_grover_pass_%s (one fused oracle+diffusion read/write pass)" % args.dtype,
                 "alg_bytes_per_launch": 2 * S, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    # accuracy of this workload, outside the timed region: HALL, the Grover
+    # iterations and the QFT once more, against the closed form
+    st.reset(0)
+    st.hall()
+    for _ in range(iters):
+        st.grover_step(marked)
+    st.qft()
+    accuracy = error_vs_closed_form(st, n, marked, iters)
+    accuracy["tolerance_abs"] = 1e-12 if args.dtype == "c128" else 1e-5
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True,
@@ -305,10 +322,59 @@ def run_ours(args, ws, rank, local):
                    "operators_per_step": ops_per_step,
                    "l2": "inputs larger than L2 (%.1f GiB state)" % (S / 2 ** 30) if S > 2 ** 27 else "state fits in L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches),
+        "roofline": roofline, "clocks": clocks, "gpu_launches": int(launches), "accuracy": accuracy,
         "kernels": kernels, "sweep": sweep_table, "component_ms_per_step": comp,
     }
     return out, st, step, ops_per_step, N
+
+
+def hall_bytes(n, amp):
+    """Algorithmic bytes of HALL as built: one read+write pass per tile
+    group (csrc/tile.cu plan_groups)."""
+    BOT, K = (12, 9) if amp == 16 else (13, 10)
+    g0 = min(n, BOT)
+    rest = n - g0
+    passes = 1 + (-(-rest // K) if rest > 0 else 0)
+    return passes * 2 * (1 << n) * amp
+
+
+def grover_qft_closed_form(n, marked, k, idx):
+    """Amplitudes of QFT(G^k HALL|0..0>) at indices idx, from the closed form
+    (sec. 5.1 and the DFT identity of App. A): with theta = asin(sqrt(M/N)),
+    a = sin((2k+1) theta)/sqrt(M) on the marked items and
+    b = cos((2k+1) theta)/sqrt(N-M) elsewhere,
+    QFT[j] = b sqrt(N) [j = 0] + (a - b)/sqrt(N) sum_m e^{2 pi i m j / N}."""
+    import numpy as np
+    N = 1 << n
+    M = len(marked)
+    th = math.asin(math.sqrt(M / N))
+    a = math.sin((2 * k + 1) * th) / math.sqrt(M)
+    b = math.cos((2 * k + 1) * th) / math.sqrt(N - M)
+    out = np.zeros(len(idx), dtype=np.complex128)
+    for i, j in enumerate(idx):
+        acc = 0j
+        for m in marked:
+            ang = 2.0 * math.pi * ((int(m) * int(j)) % N) / N
+            acc += complex(math.cos(ang), math.sin(ang))
+        out[i] = (a - b) / math.sqrt(N) * acc + (b * math.sqrt(N) if int(j) == 0 else 0.0)
+    return out
+
+
+def error_vs_closed_form(st, n, marked, k, seed=7, samples=4096):
+    """max |d amp| and max |d amp| / |amp| of st (after HALL, k Grover
+    iterations and the QFT) against the closed form, on the zero index, the
+    marked items and seeded random indices."""
+    import numpy as np
+    import torch
+    g = np.random.default_rng(seed)
+    idx = np.unique(np.concatenate([[0], np.asarray(marked, dtype=np.int64),
+                                    g.integers(0, 1 << n, samples, dtype=np.int64)]))
+    got = st.tensor[torch.as_tensor(idx, device=st.tensor.device)].cpu().numpy().astype(np.complex128)
+    ref = grover_qft_closed_form(n, marked, k, idx)
+    d = np.abs(got - ref)
+    return {"max_abs": float(d.max()), "max_rel": float((d / np.abs(ref)).max()),
+            "median_abs_amp": float(np.median(np.abs(ref))), "indices": int(len(idx)),
+            "against": "closed form of QFT(G^%d HALL|0..0>) (sec. 5.1, App. A)" % k}
 
 
 def qft_bytes(n, amp):
@@ -330,6 +396,85 @@ def read_peaks():
     return {"hbm_gbs": 6800.0, "src": "fallback"}
 
 
+def gpu_numa_node(dev):
+    """NUMA node of the host memory next to GPU `dev`, from the GPU's PCI
+    device in sysfs (None if unknown)."""
+    import torch
+    p = torch.cuda.get_device_properties(dev)
+    addrs = []
+    if hasattr(p, "pci_bus_id"):
+        addrs.append("%04x:%02x:%02x.0" % (getattr(p, "pci_domain_id", 0), p.pci_bus_id, getattr(p, "pci_device_id", 0)))
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(dev), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        if out:  # e.g. 00000009:01:00.0
+            dom, rest = out.split(":", 1)
+            addrs.append(("%04x" % int(dom, 16)) + ":" + rest.lower())
+    except Exception:
+        pass
+    for a in addrs:
+        try:
+            node = int(open("/sys/bus/pci/devices/%s/numa_node" % a).read().strip())
+            if node >= 0:
+                return node, a
+        except Exception:
+            continue
+    return None, (addrs[0] if addrs else None)
+
+
+class HostBuffer:
+    """Page-locked host memory for the end-to-end copies, placed on the GPU's
+    local NUMA node: an anonymous mapping bound to that node (mbind), first
+    touched there, then registered with CUDA.  Falls back to torch's pinned
+    allocator (placement left to the kernel) if any step is unavailable."""
+
+    def __init__(self, nbytes, node):
+        import ctypes
+        import mmap
+        import platform
+        import torch
+        self.nbytes, self.node, self.buf, self.addr, self.registered = nbytes, node, None, None, False
+        self.method = "torch pinned allocator (default placement)"
+        sysno = {"aarch64": 235, "x86_64": 237}.get(platform.machine())
+        if node is not None and sysno is not None and node < 64:
+            try:
+                libc = ctypes.CDLL(None, use_errno=True)
+                buf = mmap.mmap(-1, nbytes, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+                addr = ctypes.addressof(ctypes.c_char.from_buffer(buf))
+                mask = ctypes.c_ulong(1 << node)
+                rc = libc.syscall(ctypes.c_long(sysno), ctypes.c_void_p(addr), ctypes.c_ulong(nbytes), ctypes.c_int(2),
+                                  ctypes.byref(mask), ctypes.c_ulong(65), ctypes.c_uint(0))  # MPOL_BIND
+                if rc != 0:
+                    raise OSError(ctypes.get_errno(), "mbind")
+                # first touch (pages land on the bound node), in parallel chunks
+                chunk = 1 << 28
+                from concurrent.futures import ThreadPoolExecutor
+                with ThreadPoolExecutor(max_workers=8) as ex:
+                    list(ex.map(lambda o: libc.memset(ctypes.c_void_p(addr + o), 0,
+                                                      ctypes.c_size_t(min(chunk, nbytes - o))),
+                                range(0, nbytes, chunk)))
+                err = torch.cuda.cudart().cudaHostRegister(addr, nbytes, 0)
+                if int(err) != 0:
+                    raise OSError(int(err), "cudaHostRegister")
+                self.buf, self.addr, self.registered = buf, addr, True
+                self.method = "mbind(MPOL_BIND) to node %d + first touch + cudaHostRegister" % node
+            except Exception as e:
+                self.method = "torch pinned allocator (default placement; node binding failed: %r)" % (e,)
+                self.buf = None
+
+    def tensor(self, dtype, numel):
+        import torch
+        if self.buf is not None:
+            return torch.frombuffer(self.buf, dtype=torch.uint8, count=self.nbytes).view(dtype)[:numel]
+        return torch.zeros(numel, dtype=dtype, pin_memory=True)
+
+    def close(self):
+        import torch
+        if self.registered:
+            torch.cuda.cudart().cudaHostUnregister(self.addr)
+            self.registered = False
+
+
 def run_e2e(args, st, step_fn, ops_per_step, N):
     """Same workload through the public API with the state in pinned host
     memory: every step copies its input state host->device, runs the step
@@ -343,9 +488,11 @@ def run_e2e(args, st, step_fn, ops_per_step, N):
     n = args.n
     cdt = st.tensor.dtype
     amp = st.tensor.element_size()
-    host_in = torch.zeros(N, dtype=cdt, pin_memory=True)
-    host_in[0] = 1.0
-    host_out = torch.empty(N, dtype=cdt, pin_memory=True)
+    node, pci = gpu_numa_node(torch.cuda.current_device())
+    hb_in, hb_out = HostBuffer(N * amp, node), HostBuffer(N * amp, node)
+    host_in = hb_in.tensor(cdt, N)
+    host_in[0] = 1.0  # the step's input |0..0>
+    host_out = hb_out.tensor(cdt, N)
     host_shots = torch.empty(1000, dtype=torch.int64, pin_memory=True)
     comp = torch.cuda.current_stream()
     st2 = qc.State(n, st.dt)
@@ -405,10 +552,14 @@ def run_e2e(args, st, step_fn, ops_per_step, N):
             for k, v in copies.items()}
     tmax, wsum = aggregate(el, float(ops_per_step) * N * args.steps)
     st2.close()
+    pinned = {"gpu_pci": pci, "gpu_numa_node": node, "host_in": hb_in.method, "host_out": hb_out.method,
+              "host_in_is_pinned": bool(host_in.is_pinned()), "host_out_is_pinned": bool(host_out.is_pinned())}
     del host_in, host_out
-    return {"value": wsum / (tmax / 1e3), "unit": UNIT, "h2d_bytes_per_step": N * amp + 8 * 8,
+    hb_in.close()
+    hb_out.close()
+    return {"value": wsum / (tmax / 1e3), "unit": UNIT, "h2d_bytes_per_step": N * amp,
             "d2h_bytes_per_step": N * amp + 8 * 1000, "ms_per_step": tmax / args.steps,
-            "h2d_GBps_seen": rate["h2d"], "d2h_GBps_seen": rate["d2h"],
+            "h2d_GBps_seen": rate["h2d"], "d2h_GBps_seen": rate["d2h"], "host_buffers": pinned,
             "note": "host state in pinned memory -> device, full step, final state and samples -> host; "
                     "two device states in turn, uploads and downloads on their own streams overlap compute"}
 
@@ -430,13 +581,19 @@ def extra_c64(n=32, iters=100):
     def run(timed):
         ev = Events(torch)
         ev.mark("start")
-        st.uniform()
-        ev.mark("hall_uniform")
+        st.reset(0)
+        ev.mark("input_reset")
+        st.hall()
+        ev.mark("hall")
         for _ in range(iters):
             st.grover_step(marked)
         ev.mark("grover")
         st.qft()
         ev.mark("qft")
+        if timed:
+            res["accuracy"] = error_vs_closed_form(st, n, marked, iters)
+            res["accuracy"]["tolerance_abs"] = 1e-5
+            ev.mark("accuracy")
         hs = []
         for t in range(n):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -453,14 +610,57 @@ def extra_c64(n=32, iters=100):
     spans, hs = run(True)
     gb = lambda b, ms: b / (ms * 1e-3) / 1e9
     ms = [[x[0].elapsed_time(x[1]) for x in h] for h in hs]
+    spans.pop("accuracy", None)
     total = sum(spans.values())
-    res = {"qubits": n, "state_bytes": S, "ms_total": total,
+    res.update({"qubits": n, "state_bytes": S, "ms_total": total,
            "amp_updates_per_s": (1 + iters + 1 + 3 * n) * N / (total * 1e-3),
            "grover_step_ms": spans["grover"] / iters, "grover_GB/s": gb(2 * S, spans["grover"] / iters),
            "qft_ms": spans["qft"], "qft_GB/s": gb(qft_bytes(n, 8), spans["qft"]),
+           "hall_ms": spans["hall"], "hall_GB/s": gb(hall_bytes(n, 8), spans["hall"]),
            "h_GB/s_mean": statistics.mean(gb(2 * S, m[0]) for m in ms),
            "cnot_GB/s_mean": statistics.mean(gb(S, m[1]) for m in ms),
-           "cphase_GB/s_mean": statistics.mean(gb(S / 2, m[2]) for m in ms)}
+           "cphase_GB/s_mean": statistics.mean(gb(S / 2, m[2]) for m in ms)})
+    st.close()
+    del st
+    torch.cuda.empty_cache()
+    return res
+
+
+def extra_u2_sweep(n=30, dtype="c128", reps=1):
+    """General one-qubit operators on every target t = 0..n-1 of an n-qubit
+    state: a Haar-random U(2) (the general complex kind) and RY (the real
+    kind).  One read+write pass each (2S algorithmic bytes)."""
+    import numpy as np
+    import torch
+    import paper_0902_0699_gb300 as qc
+    import workloads as W
+    dt = qc.QC_C128 if dtype == "c128" else qc.QC_C64
+    S = (1 << n) * (16 if dt == qc.QC_C128 else 8)
+    st = qc.State(n, dt)
+    st.uniform()
+    U = W.haar_u2(W.rng(2), n)
+    c, s_ = math.cos(0.3), math.sin(0.3)
+    RY = np.array([[c, -s_], [s_, c]], dtype=np.complex128)
+    hbm = read_peaks()["hbm_gbs"]
+    res = {}
+    for name, mats in (("haar_u2", U), ("ry", [RY] * n)):
+        st.apply_1q(0, mats[0])  # warm-up
+        torch.cuda.synchronize()
+        evs = []
+        for t in range(n):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                st.apply_1q(t, mats[t])
+            b.record()
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) / reps for a, b in evs]
+        gbs = [2 * S / (m * 1e-3) / 1e9 for m in ms]
+        res[name] = {"ms_mean": statistics.mean(ms), "GB/s_per_t": [round(x, 1) for x in gbs],
+                     "frac_of_measured_min": round(min(gbs) / hbm, 3), "frac_of_measured_max": round(max(gbs) / hbm, 3),
+                     "frac_of_measured_mean": round(statistics.mean(gbs) / hbm, 3)}
+    res["state"] = {"qubits": n, "dtype": dtype, "state_bytes": S}
     st.close()
     del st
     torch.cuda.empty_cache()
@@ -909,7 +1109,8 @@ def main():
         fn = {"c64": extra_c64, "c1": extra_c1, "c2": extra_c2, "c4": extra_c4, "c5": extra_c5,
               # a small trajectory batch (96 instances, 16..18 qubits) for profiling
               "c4s": lambda: extra_c4(96, 16, 18, seed=7, autotune=0), "f3": extra_f3,
-              "dense": extra_dense, "dense26": lambda: extra_dense(26, 2), "red": extra_red}[args.only]
+              "dense": extra_dense, "dense26": lambda: extra_dense(26, 2), "red": extra_red,
+              "u2": extra_u2_sweep, "u2_26": lambda: extra_u2_sweep(26)}[args.only]
         print(json.dumps({args.only: fn()}), flush=True)
         return 0
     out, st, step_fn, ops, N = run_ours(args, ws, rank, local)
@@ -927,7 +1128,8 @@ def main():
                                "sample": "25-qubit complex128: HALL, 3 literal Grover operators, literal QFT, probs + 1000 samples, H/CNOT/CPHASE sweep (%d operators, %.1f s)" % (nops, el)}
     if rank == 0 and not args.no_extras:
         extras = {}
-        for name, fn in (("c64_n32", extra_c64), ("grover_n10", extra_c1), ("random_n24", extra_c2),
+        for name, fn in (("c64_n32", extra_c64), ("u2_sweep_n30_c128", extra_u2_sweep),
+                         ("grover_n10", extra_c1), ("random_n24", extra_c2),
                          ("trajectories_4096", extra_c4), ("adjoint_n20", extra_c5),
                          ("multiverse_density_n14", extra_f3), ("dense_block_k5_n30_c64", extra_dense)):
             try:

@@ -155,6 +155,23 @@ qc_status qc_grover_step(qc_state* s, const uint64_t* marked, int n_marked);
  * QC_C64) the whole run is one kernel with the state in shared memory. */
 qc_status qc_grover_run(qc_state* s, const uint64_t* marked, int n_marked, int iters);
 
+/* Grover step of a state split over several devices (sec. 5.1's G; the
+ * split is the paper's distribution of amplitudes over processes, sec.
+ * 3.1-3.3, with the high index bits choosing the device).  `s` is one
+ * shard; `marked` (host, n_marked = 0 .. QC_MAX_MARKED distinct indices <
+ * 2^n of the shard) are the marked items that fall in it, in shard-local
+ * indices.  qc_grover_partial writes out[2] = S_r - 2 sum_{marked} C (S_r
+ * the shard's amplitude sum; synchronises the shard's stream) and saves the
+ * marked amplitudes; the caller adds the shards' values (one complex
+ * all-reduce) into P and calls qc_grover_apply_mean with the same marked
+ * list and mean[2] = P / 2^{n_total}, which applies C -> 2m - C (unmarked),
+ * 2m + C (marked) in one read+write pass.  The diffusion 2|s><s| - I does
+ * not depend on how qubits are ordered over the shards.  QC_EINVAL if the
+ * apply call does not follow a partial call with the same list, with no
+ * other mutation between them. */
+qc_status qc_grover_partial(qc_state* s, const uint64_t* marked, int n_marked, double out[2]);
+qc_status qc_grover_apply_mean(qc_state* s, const uint64_t* marked, int n_marked, const double mean[2]);
+
 /* Quantum Fourier transform (Appendix A): the Hadamard / CPHASEK ladder
  * followed by the qubit-order reversal swaps, i.e.
  *   C~_{n'} = 2^{-n/2} sum_n e^{+2 pi i n n' / 2^n} C_n.
@@ -176,10 +193,24 @@ qc_status qc_apply_2q(qc_state* s, int t1, int t2, const double V[32]);
  * other qubits, C[g|offs(l)] <- sum_l' U[l][l'] C[g|offs(l')].  U: host,
  * 2 * 4^k doubles, row-major, (re, im) interleaved.  k = 2 with qubits
  * {t2, t1} is qc_apply_2q(t1, t2).  complex64 with k = 5 runs on the
- * tensor cores (TF32 operands split hi + lo, FP32 accumulation; synchronises
- * the stream to read a status word, QC_ETIMEOUT if a device wait gave up);
- * other cases on CUDA cores (complex128 in double-float). */
+ * tensor cores: each group of 32 amplitudes and the operator are cut into
+ * bf16 fixed-point digits from their largest magnitude (rows whose largest
+ * magnitude is below 2^-120 keep 8 significant bits), the leading digit
+ * products accumulate exactly in FP32, and the result is rounded once
+ * (FP32-class accuracy, no bias); the call synchronises the stream to read
+ * a status word and returns QC_ETIMEOUT if a device wait gave up.  Other
+ * cases run on CUDA cores (complex128 in double-float). */
 qc_status qc_apply_dense(qc_state* s, int k, const int* qubits, const double* U);
+
+/* Self-test of the tensor-core block's timeout path (no paper counterpart).
+ * Launches qc_apply_dense's tensor-core kernel on qubits 0..4 of a complex64
+ * state (n >= 5) with its MMA issue switched off and each mbarrier wait
+ * bounded by spin_limit polls (1 .. 2^20), so the first wait runs out while
+ * nothing asynchronous is in flight: the kernel records the timeout in its
+ * status word, releases its tensor memory and returns.  The state is not
+ * modified.  Returns QC_ETIMEOUT when the path works (anything else is a
+ * failure of the path); QC_EINVAL for a bad state or limit. */
+qc_status qc_dense_timeout_selftest(qc_state* s, uint32_t spin_limit);
 
 /* ------------------------------------------------------- gate fusion -- */
 /* A circuit operator for gate fusion: kind QC_OP_1Q applies m (a U(2),
@@ -336,15 +367,18 @@ qc_status qc_probs_sample(const qc_state* s, double* probs_dev, uint64_t seed, i
  * states return QC_EINVAL with a message.  The scratch is a fixed array of
  * 2^20 + 512 + 32 uint64 (about 8 MiB) in the library's own device memory,
  * held on every GPU that loads the library until the process exits.  The
- * first call on a device looks up that array's device address, so make the
- * first call on each device before any stream capture.  The array keeps the
- * last call's contents (each call resets what must start at zero); calls
- * whose work overlaps on the GPU -- on different streams or threads -- race
- * on it and must be serialised by the caller.
+ * first call on a device looks up that array's device address (once per
+ * device, kept for later calls); make that first call before any stream
+ * capture begins, and do not call this entry point again on a device after
+ * cudaDeviceReset there.  The array keeps the last call's contents (each
+ * call resets what must start at zero); calls whose work overlaps on the
+ * GPU -- on different streams or threads -- race on it and must be
+ * serialised by the caller.
  *
  * Validation: every |C_i|^2 must lie in [0, 2] and
- * 0 < sum_i trunc(p_i 2^62) <= 2^63; otherwise QC_EINVAL (checked on the
- * device; the call synchronises `stream` once to read the verdict). */
+ * 0 < sum_i trunc(p_i 2^62) <= 2^63; otherwise QC_EINVAL.  The check runs on
+ * the device, and every call synchronises `stream` once to read its verdict
+ * back to the host before it draws the samples. */
 #define QC_SAMPLE_NOALLOC_MAX_QUBITS 20
 qc_status qc_sample_noalloc(const void* psi_dev, int n, qc_dtype dt, uint64_t seed, int64_t shots,
                             uint64_t* out_dev, void* stream);
@@ -398,6 +432,16 @@ qc_status qc_traj_plan_create(const qc_traj_desc* d, void* stream, int autotune,
  * stream.  Returns QC_ETIMEOUT (after synchronising) if a device-side
  * bounded wait gave up. */
 qc_status qc_traj_plan_run(qc_traj_plan* p, const qc_traj_out* out);
+
+/* qc_traj_plan_run, and also each selected instance's final complex64 state:
+ * the 2^nq[i] amplitudes its read-out is drawn from (after its last pass;
+ * squared norm Q, the value p_success divides by), written to
+ * states_dev + state_off_dev[i] (device array of n_inst amplitude offsets,
+ * ~0 = skip the instance; the caller makes the ranges disjoint and large
+ * enough).  For replaying an instance's seeded read-out from the very
+ * weights the kernel used.  QC_EINVAL if either pointer is NULL. */
+qc_status qc_traj_plan_run_states(qc_traj_plan* p, const qc_traj_out* out, const uint64_t* state_off_dev,
+                                  void* states_dev);
 
 /* Chosen launch shape: clusters of `ctas_per_inst` CTAs, `threads` threads. */
 qc_status qc_traj_plan_info(const qc_traj_plan* p, int* ctas_per_inst, int* threads, int* grid);

@@ -430,11 +430,22 @@ def readout_success(p: np.ndarray, n: int, marked: int, p_ro: float) -> float:
     return float(np.sum(p * w))
 
 
-def trajectory_measure(p: np.ndarray, n: int, seed: int, inst: int, thr_ro: int) -> int:
-    """One seeded measurement of the instance (integer-CDF sampler with counter
-    (inst, 0xFFFFFFFF, 0, 'MEAS')), then each bit q flips when the Philox draw
-    (inst, 0xFFFFFFFF, q, 'READ') has word 0 < thr_ro."""
-    cdf = integer_cdf(p)
+def readout_weights_c64(psi64: np.ndarray) -> np.ndarray:
+    """Integer read-out weights of a complex64 state, the rule the batched
+    trajectories measure with: w_j = trunc(re_j^2 2^62) + trunc(im_j^2 2^62).
+    Every step is exact in binary64 (a float's square has at most 48
+    significant bits, and 2^62 only shifts the exponent)."""
+    re = np.ascontiguousarray(psi64).real.astype(np.float64)
+    im = np.ascontiguousarray(psi64).imag.astype(np.float64)
+    return (re * re * TWO62).astype(np.uint64) + (im * im * TWO62).astype(np.uint64)
+
+
+def trajectory_measure_weights(w: np.ndarray, n: int, seed: int, inst: int, thr_ro: int) -> int:
+    """One seeded measurement of the instance from integer weights w (the
+    integer-CDF rule of the sampler with counter (inst, 0xFFFFFFFF, 0,
+    'MEAS')), then each bit q flips when the Philox draw (inst, 0xFFFFFFFF,
+    q, 'READ') has word 0 < thr_ro."""
+    cdf = np.cumsum(np.asarray(w, dtype=np.uint64), dtype=np.uint64)
     total = int(cdf[-1])
     key = (seed & 0xFFFFFFFF, seed >> 32)
     x = philox4x32_10((inst, 0xFFFFFFFF, 0, TAG_MEAS), key)
@@ -446,6 +457,13 @@ def trajectory_measure(p: np.ndarray, n: int, seed: int, inst: int, thr_ro: int)
         if y[0] < thr_ro:
             out ^= 1 << q
     return out
+
+
+def trajectory_measure(p: np.ndarray, n: int, seed: int, inst: int, thr_ro: int) -> int:
+    """trajectory_measure_weights with the weights trunc(p_j 2^62) of the
+    probabilities p (the sampler's rule)."""
+    integer_cdf(p)  # validates p
+    return trajectory_measure_weights((p * TWO62).astype(np.uint64), n, seed, inst, thr_ro)
 
 
 # ------------------------------------------------------ adjoint gradient ----

@@ -82,6 +82,8 @@ _SIGS = {
     "qc_apply_1q_layer": [_VP, _DP, _U64],
     "qc_grover_step": [_VP, _U64P, _I],
     "qc_grover_run": [_VP, _U64P, _I, _I],
+    "qc_grover_partial": [_VP, _U64P, _I, _DP],
+    "qc_grover_apply_mean": [_VP, _U64P, _I, _DP],
     "qc_qft": [_VP],
     "qc_apply_2q": [_VP, _I, _I, _DP],
     "qc_shor_prepare": [_VP, _I, _U64, _U64],
@@ -96,6 +98,7 @@ _SIGS = {
     "qc_sample_noalloc": [_VP, _I, _I, _U64, _I64, _VP, _VP],
     "qc_traj_plan_create": [ctypes.POINTER(TrajDesc), _VP, _I, ctypes.POINTER(_VP)],
     "qc_traj_plan_run": [_VP, ctypes.POINTER(TrajOut)],
+    "qc_traj_plan_run_states": [_VP, ctypes.POINTER(TrajOut), _VP, _VP],
     "qc_traj_plan_info": [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "qc_traj_plan_free": [_VP],
     "qc_circuit_forward": [_I, _I, _I, ctypes.POINTER(Gate), _I, _VP, _I64, _VP, _VP],
@@ -103,6 +106,7 @@ _SIGS = {
                         ctypes.POINTER(PauliTerm), _I, _VP, _VP, _VP, _VP, _VP],
     "qc_wigner_d": [_I, ctypes.c_double, ctypes.c_double, ctypes.c_double, _DP],
     "qc_apply_dense": [_VP, _I, ctypes.POINTER(_I), _DP],
+    "qc_dense_timeout_selftest": [_VP, ctypes.c_uint32],
     "qc_hamiltonian_step": [_VP, ctypes.c_double, _VP, _I],
     "qc_fused_plan_create": [_I, _VP, _I, _I, _I, ctypes.POINTER(_VP)],
     "qc_fused_plan_info": [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)],
@@ -231,8 +235,21 @@ def qc_hall(h):
     _check(lib().qc_hall(h))
 
 
+def _layer_ops(U, n: int) -> np.ndarray:
+    """n one-qubit operators as the 8 n doubles the C call reads: either
+    complex (n, 2, 2) matrices or (n, 8) interleaved (re, im) rows."""
+    U = np.asarray(U)
+    if U.dtype.kind == "c":
+        U = np.stack([U.real, U.imag], axis=-1)
+    a = np.ascontiguousarray(U, dtype=np.float64).reshape(-1)
+    if a.size != 8 * n:
+        raise ValueError("a layer on %d qubits needs %d operators (8 doubles each), got %d doubles" % (n, n, a.size))
+    return a
+
+
 def qc_apply_1q_layer(h, U, mask: int):
-    a = np.ascontiguousarray(np.asarray(U, dtype=np.float64).reshape(-1))
+    _, n, _ = qc_state_info(h)
+    a = _layer_ops(U, n)
     _check(lib().qc_apply_1q_layer(h, _dptr(a), mask))
 
 
@@ -248,6 +265,24 @@ def qc_grover_step(h, marked):
 def qc_grover_run(h, marked, iters: int):
     m = _marked(marked)
     _check(lib().qc_grover_run(h, m.ctypes.data_as(_U64P), len(m), iters))
+
+
+def _marked0(marked) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(marked, dtype=np.uint64).reshape(-1))
+
+
+def qc_grover_partial(h, marked_local) -> complex:
+    """S_r - 2 sum_{marked} C of one shard (qc_grover_partial)."""
+    m = _marked0(marked_local)
+    out = np.zeros(2)
+    _check(lib().qc_grover_partial(h, m.ctypes.data_as(_U64P) if m.size else None, int(m.size), _dptr(out)))
+    return complex(out[0], out[1])
+
+
+def qc_grover_apply_mean(h, marked_local, mean: complex):
+    m = _marked0(marked_local)
+    mv = np.array([mean.real, mean.imag])
+    _check(lib().qc_grover_apply_mean(h, m.ctypes.data_as(_U64P) if m.size else None, int(m.size), _dptr(mv)))
 
 
 def qc_qft(h):
@@ -337,6 +372,12 @@ class FusedPlan:
 
 class HTerm(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("qubits", ctypes.c_int32 * 2), ("h", ctypes.c_double * 32)]
+
+
+def qc_dense_timeout_selftest(h, spin_limit: int) -> int:
+    """Runs the tensor-core block's timeout path; returns the status code
+    (QC_ETIMEOUT when the path works) instead of raising."""
+    return int(lib().qc_dense_timeout_selftest(h, int(spin_limit)))
 
 
 def qc_hamiltonian_step(h, dt: float, terms):
@@ -530,6 +571,10 @@ def qc_traj_plan_create(desc: "TrajDesc", stream=None, autotune: bool = True):
 
 def qc_traj_plan_run(plan, out: "TrajOut"):
     _check(lib().qc_traj_plan_run(plan, ctypes.byref(out)))
+
+
+def qc_traj_plan_run_states(plan, out: "TrajOut", state_off_dev_ptr: int, states_dev_ptr: int):
+    _check(lib().qc_traj_plan_run_states(plan, ctypes.byref(out), _VP(state_off_dev_ptr), _VP(states_dev_ptr)))
 
 
 def qc_traj_plan_info(plan):
@@ -804,7 +849,10 @@ class TrajectoryPlan:
         _check(lib().qc_traj_plan_info(self.h, *[ctypes.byref(x) for x in v]))
         return tuple(x.value for x in v)
 
-    def run(self):
+    def run(self, keep=()):
+        """Runs every instance.  keep: instance indices whose final complex64
+        states (the ones their read-outs are drawn from) are returned too,
+        as out["states"][i]."""
         import torch
         dev = torch.device("cuda", torch.cuda.current_device())
         out = {"p_success": torch.empty(self.n_inst, dtype=torch.float64, device=dev),
@@ -813,7 +861,21 @@ class TrajectoryPlan:
                "n_errors": torch.empty(self.n_inst, dtype=torch.int32, device=dev)}
         o = TrajOut(out["p_success"].data_ptr(), out["p_readout"].data_ptr(), out["outcome"].data_ptr(),
                     out["n_errors"].data_ptr())
-        _check(lib().qc_traj_plan_run(self.h, ctypes.byref(o)))
+        keep = sorted(set(int(i) for i in keep))
+        if not keep:
+            _check(lib().qc_traj_plan_run(self.h, ctypes.byref(o)))
+            return out
+        off = np.full(self.n_inst, np.iinfo(np.uint64).max, dtype=np.uint64)
+        pos = 0
+        for i in keep:
+            off[i] = pos
+            pos += 1 << int(self._nq[i])
+        states = torch.empty(pos, dtype=torch.complex64, device=dev)
+        off_d = torch.from_numpy(off.view(np.int64)).to(dev)
+        _check(lib().qc_traj_plan_run_states(self.h, ctypes.byref(o), _VP(off_d.data_ptr()),
+                                             _VP(states.data_ptr())))
+        out["states"] = {i: states[int(off[i]):int(off[i]) + (1 << int(self._nq[i]))] for i in keep}
+        out["_state_offsets"] = off_d  # kept alive until the run has finished
         return out
 
     def close(self):

@@ -42,16 +42,18 @@ qc_status check_launch(const char* what, int nkernels) {
 }
 
 int sm_count() {
-  static int cache[64] = {0};
+  static std::atomic<int> cache[64];  // zero-initialised; threads may fill a slot concurrently (same value)
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
-  if (cache[dev] == 0) {
+  int c = cache[dev].load(std::memory_order_relaxed);
+  if (c == 0) {
     int v = 0;
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    cache[dev] = v > 0 ? v : 1;
+    c = v > 0 ? v : 1;
+    cache[dev].store(c, std::memory_order_relaxed);
   }
-  return cache[dev];
+  return c;
 }
 
 int resident_blocks(const void* kernel, int threads, size_t smem) {
@@ -143,6 +145,7 @@ static qc_status new_state(void* data, int n, qc_dtype dt, void* stream, bool ow
   cudaGetDevice(&s->device);
   s->scratch = nullptr;
   s->marked_dev = nullptr;
+  s->grover_partial_ready = false;
   cudaError_t e = cudaMalloc(&s->scratch, QC_SCRATCH_DOUBLES * sizeof(double));
   if (e != cudaSuccess) {
     delete s;
@@ -372,9 +375,9 @@ QC_API qc_status qc_apply_1q_layer(qc_state* s, const double* U, uint64_t mask) 
   return launch_layer(s, U, mask);
 }
 
-static qc_status check_marked(const qc_state* s, const uint64_t* marked, int m) {
-  if (!marked || m < 1 || m > QC_MAX_MARKED) {
-    set_error("need 1..%d marked items (got %d, ptr %p)", QC_MAX_MARKED, m, (const void*)marked);
+static qc_status check_marked(const qc_state* s, const uint64_t* marked, int m, int min_m = 1) {
+  if ((m > 0 && !marked) || m < min_m || m > QC_MAX_MARKED) {
+    set_error("need %d..%d marked items (got %d, ptr %p)", min_m, QC_MAX_MARKED, m, (const void*)marked);
     return QC_EINVAL;
   }
   const uint64_t N = 1ull << s->n;
@@ -403,6 +406,30 @@ QC_API qc_status qc_grover_step(qc_state* s, const uint64_t* marked, int m) {
     return QC_EINVAL;
   }
   return launch_grover_step(s, marked, m);
+}
+
+QC_API qc_status qc_grover_partial(qc_state* s, const uint64_t* marked, int m, double out[2]) {
+  clear_error();
+  qc_status st = check_state(s);
+  if (!st) st = check_marked(s, marked, m, 0);
+  if (st) return st;
+  if (!out) {
+    set_error("qc_grover_partial: out is NULL");
+    return QC_EINVAL;
+  }
+  return launch_grover_partial(s, marked, m, out);
+}
+
+QC_API qc_status qc_grover_apply_mean(qc_state* s, const uint64_t* marked, int m, const double mean[2]) {
+  clear_error();
+  qc_status st = check_state(s);
+  if (!st) st = check_marked(s, marked, m, 0);
+  if (st) return st;
+  if (!mean || !std::isfinite(mean[0]) || !std::isfinite(mean[1])) {
+    set_error("qc_grover_apply_mean: mean is NULL or not finite");
+    return QC_EINVAL;
+  }
+  return launch_grover_apply(s, marked, m, mean);
 }
 
 QC_API qc_status qc_grover_run(qc_state* s, const uint64_t* marked, int m, int iters) {

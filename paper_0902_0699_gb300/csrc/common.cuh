@@ -38,6 +38,7 @@ struct qc_state {
   double* scratch;  // device, QC_SCRATCH_DOUBLES
   void* marked_dev;  // device copy of the last Grover marked list (lazy)
   std::vector<uint64_t> marked_host;  // what marked_dev holds
+  bool grover_partial_ready;  // qc_grover_partial saved the marked amplitudes and P_r
 };
 
 // ------------------------------------------------------------ errors -----
@@ -320,9 +321,15 @@ qc_status launch_fill_basis(qc_state* s, uint64_t idx);
 qc_status launch_fill_uniform(qc_state* s);
 qc_status launch_hall(qc_state* s);
 qc_status launch_layer(qc_state* s, const double* U, uint64_t mask);
+// Hadamard layers as Walsh-Hadamard tile passes (wht.cu), for n >= the
+// returned minimum
+int hadamard_layer_min_qubits(qc_dtype dt);
+qc_status launch_hadamard_layer(qc_state* s, uint64_t mask);
 qc_status launch_qft(qc_state* s);
 qc_status launch_grover_step(qc_state* s, const uint64_t* marked, int m);
 qc_status launch_grover_run(qc_state* s, const uint64_t* marked, int m, int iters);
+qc_status launch_grover_partial(qc_state* s, const uint64_t* marked, int m, double* out_host);
+qc_status launch_grover_apply(qc_state* s, const uint64_t* marked, int m, const double* mean);
 qc_status launch_sum(qc_state* s);  // refreshes scratch[QC_SCR_SUM]
 qc_status reduce_norm(const qc_state* s, double* out_host);
 qc_status launch_probs(const qc_state* s, double* out);
@@ -344,6 +351,11 @@ qc_status dense_map(int n, int k, const int* qubits, DenseMap* M);
 bool dense_uses_tc(qc_dtype dt, int k);
 size_t dense_op_bytes(qc_dtype dt, int k);
 void dense_pack(qc_dtype dt, int k, const double* U, void* host_out);
-qc_status dense_launch(qc_state* s, const DenseMap& M, const void* dev_op, int* status);
+// spin_limit bounds each of the tensor-core kernel's mbarrier waits (polls);
+// no_mma = 1 is the timeout self-test (no MMA is issued, so the first wait
+// runs out with nothing asynchronous in flight).
+#define QC_TC_SPIN_LIMIT (1u << 20)
+qc_status dense_launch(qc_state* s, const DenseMap& M, const void* dev_op, int* status,
+                       uint32_t spin_limit = QC_TC_SPIN_LIMIT, int no_mma = 0);
 
 }  // namespace qc

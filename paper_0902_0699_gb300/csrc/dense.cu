@@ -22,7 +22,10 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
+#include "slices.cuh"
 
 namespace qc {
 
@@ -115,31 +118,45 @@ __global__ void __launch_bounds__(DENSE_T) k_dense(typename DenseT<R>::V* __rest
 }
 
 // ----------------------------------------------------- tensor cores ------
-// complex64, k = 5: rows of K = 64 reals, N = 64, tiles of M = 128 rows.
+// complex64, k = 5: rows of K = 64 reals, N = 64, tiles of M = 128 rows, on
+// tcgen05 kind::f16 with bf16 digit slices (slices.cuh).  Row r of a tile
+// (one group) is scaled by 2^(134 - E_r) from its largest magnitude and cut
+// into digits a0, a1, a2; W^T into b0, b1, b2 with one scale per operator.
+// With y = a0 + 2^-8 (a1 + a2) and v = b0 + 2^-8 (b1 + b2),
+//   y v = a0 b0 + 2^-8 (a0 b1 + a1 b0)
+//         + 2^-8 (a0 b2 + a2 b0 + a1 (2^-8 b1) + a1 (2^-8 b2) + a2 (2^-8 b1))
+//         + 2^-16 a2 b2,
+// and three FP32 accumulators in tensor memory hold
+//   acc0 = sum a0 b0,  acc1 = sum a0 b1 + a1 b0   (exact integers below 2^24)
+//   acc2 = the fractional terms (2^-8 b1 and 2^-8 b2 are extra W digits),
+// so the output is (acc0 + 2^-8 (acc1 + acc2)) 2^(E_r - 134) 2^(E_w - 134).
+// acc0 and acc1 are exact, so the tensor cores' truncating accumulation
+// leaves no bias in them; acc2 is about 2^-8 of acc1 and enters 2^-8 lower
+// still.  The one omitted term, 2^-16 a2 b2 (|a2|, |b2| <= 1/2), is below
+// 2^-18 of a unit of y v, far under the final rounding.
+//
 // Shared-memory operands use the canonical K-major layout without swizzle:
-// 8-row x 16-byte core matrices, 128 contiguous bytes each; core matrices
-// adjacent in K are 128 B apart (leading byte offset), 8-row groups are
-// 16 * 128 = 2048 B apart (stride byte offset).
+// 8-row x 16-byte core matrices (8 bf16 along K), 128 contiguous bytes
+// each; core matrices adjacent in K are 128 B apart (leading byte offset),
+// 8-row groups are 8 * 128 = 1024 B apart (stride byte offset).
 #define TC_M 128
 #define TC_T 256  // threads: two per tile row (halves of 16 amplitudes)
 #define TC_K 64
 #define TC_N 64
 #define TC_LBO 128
-#define TC_SBO 2048
-#define TC_A_BYTES (TC_M * TC_K * 4)  // 32 KiB
-#define TC_B_BYTES (TC_N * TC_K * 4)  // 16 KiB
-#define TC_SMEM (2 * TC_A_BYTES + 2 * TC_B_BYTES + 64)
-#define TC_SPIN_LIMIT (1u << 20)  // polls of try_wait; a tile takes microseconds
+#define TC_SBO 1024
+#define TC_A_SLICE (TC_M * TC_K * 2)  // 16 KiB per A digit
+#define TC_B_SLICE (TC_N * TC_K * 2)  // 8 KiB per W digit
+#define TC_NA 3                       // a0, a1, a2
+#define TC_NB 5                       // b0, b1, b2, 2^-8 b1, 2^-8 b2
+#define TC_OP_BYTES (TC_NB * TC_B_SLICE)  // device operator: the W digits, then the W scale (float)
+// Two CTAs per SM (a third does not fit: 3 x 89 KiB > 227 KiB), 256 TMEM
+// columns each (three 64-column accumulators; allocations are powers of two).
+#define TC_SMEM (TC_NA * TC_A_SLICE + TC_NB * TC_B_SLICE + TC_M * 4 + 64)
+#define TC_TMEM_COLS 256
 
-__device__ __forceinline__ uint32_t canon_off(int r, int k) {  // byte offset of (row r, column k)
-  return (uint32_t)((r >> 3) * TC_SBO + (k >> 2) * TC_LBO + (r & 7) * 16 + (k & 3) * 4);
-}
-
-// hi = x rounded to TF32 (11 significant bits, ties away from zero, by
-// integer arithmetic on the pattern); lo = x - hi exactly
-__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
-  hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
-  lo = x - hi;
+__device__ __forceinline__ uint32_t canon_off(int r, int k) {  // byte offset of bf16 (row r, column k)
+  return (uint32_t)((r >> 3) * TC_SBO + (k >> 3) * TC_LBO + (r & 7) * 16 + (k & 7) * 2);
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
@@ -147,18 +164,18 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
          (1ull << 46);  // descriptor version 1, no swizzle (layout 0)
 }
 
-// kind::tf32, D = F32, A = B = TF32, both K-major, N = 64, M = 128
-#define TC_IDESC ((1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24))
+// kind::f16, D = F32, A = B = BF16, both K-major, N = 64, M = 128
+#define TC_IDESC ((1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24))
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
       "l"(da), "l"(db), "r"(TC_IDESC), "r"(acc));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (uint32_t it = 0; it < TC_SPIN_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -171,63 +188,93 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
-// 32 consecutive accumulator columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
+// 16 consecutive accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// One persistent CTA of 128 threads per tile stream.  Thread t stages row
-// t of each 128-group tile (split into TF32 hi and lo), thread 0 issues the
-// 3 x 8 MMAs of the tile into a 128 x 64 FP32 accumulator in tensor memory
-// and commits them to an mbarrier, every warp reads its 32 accumulator
-// lanes back and writes its rows.  Wt holds W^T (N x K) split hi, lo.
-// status: set to 1 if an mbarrier wait ran out (the kernel then stops).
+__device__ __forceinline__ uint32_t abs_bits(float x) { return __float_as_uint(x) & 0x7FFFFFFFu; }
+__device__ __forceinline__ uint32_t max4_bits(const float4& v) {
+  return max(max(abs_bits(v.x), abs_bits(v.y)), max(abs_bits(v.z), abs_bits(v.w)));
+}
+
+// Two reals into their three digits, each pair packed as bf16x2 (element
+// k in the low half, at the lower address).
+__device__ __forceinline__ void digits2(float x, float y, float scale, uint32_t& w0, uint32_t& w1, uint32_t& w2) {
+  float a0, a1, a2, b0, b1, b2;
+  slice_digits(x, scale, a0, a1, a2);
+  slice_digits(y, scale, b0, b1, b2);
+  __nv_bfloat162 t = __floats2bfloat162_rn(a0, b0);
+  w0 = *reinterpret_cast<const uint32_t*>(&t);
+  t = __floats2bfloat162_rn(a1, b1);
+  w1 = *reinterpret_cast<const uint32_t*>(&t);
+  t = __floats2bfloat162_rn(a2, b2);
+  w2 = *reinterpret_cast<const uint32_t*>(&t);
+}
+
+// Four reals of one row into their three digit slices (8 bytes each).
+__device__ __forceinline__ void stage4(const float4& v, float scale, unsigned char* A, uint32_t off) {
+  uint2 d0, d1, d2;
+  digits2(v.x, v.y, scale, d0.x, d1.x, d2.x);
+  digits2(v.z, v.w, scale, d0.y, d1.y, d2.y);
+  *reinterpret_cast<uint2*>(A + off) = d0;
+  *reinterpret_cast<uint2*>(A + TC_A_SLICE + off) = d1;
+  *reinterpret_cast<uint2*>(A + 2 * TC_A_SLICE + off) = d2;
+}
+
+// Persistent CTAs of 256 threads.  Per tile of 128 groups: the row maxima
+// (shared-memory atomics), the digit slices of every row, 32 MMAs issued by
+// thread 0 into three 128 x 64 FP32 accumulators and committed to an
+// mbarrier, then every warp reads its 32 accumulator lanes back and writes
+// its rows.  Wd holds the W^T digits (b0, b1, b2, 2^-8 b1, 2^-8 b2; N x K each) and
+// then the W scale.  status: set to 1 if an mbarrier wait ran out (the
+// kernel then stops).  spin_limit bounds each wait; no_mma = 1 issues no MMA
+// and no commit, so the first wait runs out with nothing asynchronous in
+// flight (the self-test of the timeout path).
 __global__ void __launch_bounds__(TC_T, 2) k_dense_tc(float2* __restrict__ psi, uint64_t ngroups,
-                                                   const float* __restrict__ Wt_hi, const float* __restrict__ Wt_lo,
-                                                   DenseMap M, int* __restrict__ status,
-                                                   const __grid_constant__ CUtensorMap out_map, int use_tma) {
+                                                   const uint16_t* __restrict__ Wd, DenseMap M,
+                                                   int* __restrict__ status,
+                                                   const __grid_constant__ CUtensorMap out_map, int use_tma,
+                                                   uint32_t spin_limit, int no_mma) {
   extern __shared__ __align__(1024) unsigned char tsm[];
-  unsigned char* A_hi = tsm;
-  unsigned char* A_lo = tsm + TC_A_BYTES;
-  unsigned char* B_hi = tsm + 2 * TC_A_BYTES;
-  unsigned char* B_lo = B_hi + TC_B_BYTES;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(B_lo + TC_B_BYTES);
+  unsigned char* A = tsm;                          // TC_NA digit slices of the tile
+  unsigned char* B = tsm + TC_NA * TC_A_SLICE;     // TC_NB digit slices of W^T
+  uint32_t* rowmax = reinterpret_cast<uint32_t*>(B + TC_NB * TC_B_SLICE);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(rowmax + TC_M);
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mbar + 1);
   __shared__ int stop;
   const int tid = threadIdx.x, warp = tid >> 5;
-  // W^T into the canonical layout (once per CTA)
-  for (int e = tid; e < TC_N * TC_K; e += TC_T) {
-    const int r = e / TC_K, c = e % TC_K;
-    *reinterpret_cast<float*>(B_hi + canon_off(r, c)) = Wt_hi[e];
-    *reinterpret_cast<float*>(B_lo + canon_off(r, c)) = Wt_lo[e];
+  // W^T digits into the canonical layout (once per CTA)
+  for (int e = tid; e < TC_NB * TC_N * TC_K; e += TC_T) {
+    const int s = e / (TC_N * TC_K), rc = e % (TC_N * TC_K), r = rc / TC_K, c = rc % TC_K;
+    *reinterpret_cast<uint16_t*>(B + s * TC_B_SLICE + canon_off(r, c)) = Wd[e];
   }
+  const float wscale = *reinterpret_cast<const float*>(Wd + TC_NB * TC_N * TC_K);
+  for (int r = tid; r < TC_M; r += TC_T) rowmax[r] = 0u;
   const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(mbar);
   if (tid == 0) {
     stop = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar_a));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  if (warp == 0) {  // 64 TMEM columns: the 128 x 64 FP32 accumulator
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;\n" ::"r"(
-        (uint32_t)__cvta_generic_to_shared(tmem_holder)));
+  if (warp == 0) {  // 256 TMEM columns: the three 128 x 64 FP32 accumulators
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(tmem_holder)),
+                 "n"(TC_TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_holder;
-  const uint32_t a_hi = (uint32_t)__cvta_generic_to_shared(A_hi), a_lo = (uint32_t)__cvta_generic_to_shared(A_lo);
-  const uint32_t b_hi = (uint32_t)__cvta_generic_to_shared(B_hi), b_lo = (uint32_t)__cvta_generic_to_shared(B_lo);
+  const uint32_t a_s = (uint32_t)__cvta_generic_to_shared(A), b_s = (uint32_t)__cvta_generic_to_shared(B);
   bool contig = true;
   for (int l = 0; l < 32; ++l) contig &= (M.offs[l] == (uint64_t)l);
   uint32_t phase = 0;
@@ -239,8 +286,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_dense_tc(float2* __restrict__ psi, 
   // moved by all threads together.  Chunk i of thread tid is row
   // 8 (8 hf + i) + (tid & 7), 16-byte segment 4 ((tid & 127) >> 5) +
   // ((tid >> 3) & 3): a warp reads 8 rows x 64 contiguous bytes (whole
-  // sectors) and a quarter-warp writes one contiguous 128-byte run of the
-  // K-major layout.
+  // sectors).
   const int crow = tid & 7, cseg = 4 * (row >> 5) + ((tid >> 3) & 3);
   // A thread's 8 float4 of a tile in registers from its load to its
   // staging; two register buffers, so tile t+2's loads are in flight during
@@ -276,42 +322,52 @@ __global__ void __launch_bounds__(TC_T, 2) k_dense_tc(float2* __restrict__ psi, 
   auto body = [&](uint64_t tile, float4 (&R)[8], bool& rlive, uint64_t& rbase) -> bool {
     const bool live = rlive;
     const uint64_t base = rbase;
-    if (tma_out) {  // the previous tile's output store has read A_hi
+    if (tma_out) {  // the previous tile's output store has read the A slices
       if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
       __syncthreads();
     }
+    // row maxima (|x| bit patterns order like the values)
+    if (contig) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {  // two amplitudes (4 reals) per core-matrix row
-      const float4 v = R[i];
-      float4 h, lo;
-      tf32_split(v.x, h.x, lo.x);
-      tf32_split(v.y, h.y, lo.y);
-      tf32_split(v.z, h.z, lo.z);
-      tf32_split(v.w, h.w, lo.w);
-      const uint32_t off =
-          contig ? canon_off(8 * (8 * hf + i) + crow, 4 * cseg) : canon_off(row, 4 * (8 * hf + i));
-      *reinterpret_cast<float4*>(A_hi + off) = h;
-      *reinterpret_cast<float4*>(A_lo + off) = lo;
+      for (int i = 0; i < 8; ++i) atomicMax(&rowmax[8 * (8 * hf + i) + crow], max4_bits(R[i]));
+    } else {
+      uint32_t mx = 0u;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) mx = max(mx, max4_bits(R[i]));
+      atomicMax(&rowmax[row], mx);
+    }
+    __syncthreads();
+    const uint32_t Ee = slice_exp(rowmax[row]);  // the exponent of this thread's output row
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {  // digits of two amplitudes (4 reals) per 8-byte piece of a row
+      const int r = contig ? 8 * (8 * hf + i) + crow : row;
+      const int k = contig ? 4 * cseg : 4 * (8 * hf + i);
+      stage4(R[i], slice_scale(slice_exp(rowmax[r])), A, canon_off(r, k));
     }
     // the tensor core reads shared memory through the async proxy
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
-    if (tid == 0) {
+    if (tid < TC_M) rowmax[tid] = 0u;  // read by every thread above; the next tile's atomics follow the last barrier
+    if (tid == 0 && !no_mma) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t as[3] = {a_hi, a_hi, a_lo}, bs[3] = {b_hi, b_lo, b_hi};
-      uint32_t acc = 0;
-      for (int t = 0; t < 3; ++t)
-        for (int s = 0; s < TC_K / 8; ++s) {  // K = 8 TF32 per MMA: two core matrices along K
-          mma_tf32(tmem, smem_desc(as[t] + s * 2 * TC_LBO), smem_desc(bs[t] + s * 2 * TC_LBO), acc);
-          acc = 1;
-        }
+      // acc0 = a0 b0; acc1 = a0 b1 + a1 b0;
+      // acc2 = a0 b2 + a2 b0 + a1 (2^-8 b1) + a1 (2^-8 b2) + a2 (2^-8 b1)
+      const int pa[8] = {0, 0, 1, 0, 2, 1, 1, 2}, pb[8] = {0, 1, 0, 2, 0, 3, 4, 3};
+      const int acc_of[8] = {0, 1, 1, 2, 2, 2, 2, 2};
+      for (int t = 0; t < 8; ++t) {
+        const uint32_t d = tmem + acc_of[t] * TC_N;
+        const bool first = (t == 0 || t == 1 || t == 3);  // first term of its accumulator
+        for (int s = 0; s < TC_K / 16; ++s)  // K = 16 bf16 per MMA: two core matrices along K
+          mma_bf16(d, smem_desc(a_s + pa[t] * TC_A_SLICE + s * 2 * TC_LBO),
+                   smem_desc(b_s + pb[t] * TC_B_SLICE + s * 2 * TC_LBO), (first && s == 0) ? 0u : 1u);
+      }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar_a)
                    : "memory");
     }
     // tile + 2 grid's loads overlap this tile's MMAs and epilogue and the next tile
     if (tile + 2ull * gridDim.x < ntiles) fetch(tile + 2ull * gridDim.x, R, rlive, rbase);
-    if (!mbar_wait(mbar_a, phase)) {
+    if (!mbar_wait(mbar_a, phase, spin_limit)) {
       if (tid == 0) atomicExch(status, 1);
       stop = 1;
     }
@@ -319,48 +375,68 @@ __global__ void __launch_bounds__(TC_T, 2) k_dense_tc(float2* __restrict__ psi, 
     __syncthreads();
     if (stop) return false;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    // lanes 32 (warp & 3) .. hold this warp's rows; columns 32 hf .. 32 hf + 31
-    float out[32];
-    tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 32 * hf, out);
+    // lanes 32 (warp & 3) .. hold this warp's rows; columns 32 hf .. 32 hf + 31,
+    // read and combined 16 at a time
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 32 * hf;
+    const float us = slice_unscale(Ee);
+    float4* stg = reinterpret_cast<float4*>(A);  // contiguous fallback: 128 rows x 16 float4, chunk c of row r at c ^ (r & 15)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float out[16], acc1[16];
+      tmem_ld16(lane_base + TC_N + 16 * h, out);
+      tmem_ld16(lane_base + 2 * TC_N + 16 * h, acc1);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc1[j] = __fadd_rn(out[j], acc1[j]);  // acc1 + acc2
+      tmem_ld16(lane_base + 16 * h, out);  // acc0
+#pragma unroll
+      for (int j = 0; j < 16; ++j) out[j] = __fmul_rn(__fmul_rn(__fmaf_rn(acc1[j], 0.00390625f, out[j]), wscale), us);
+      if (tma_out) {
+        // rows into two 128 x 32-float boxes (the A slices are free: the
+        // MMAs are done) in the tensor map's 128-byte swizzle (16-byte chunk
+        // c of row r at chunk c ^ (r & 7), so a warp's 32 rows hit every
+        // bank)
+        unsigned char* box = A + hf * (TC_M * 128);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = 4 * h + j;
+          *reinterpret_cast<float4*>(box + row * 128 + ((c ^ (row & 7)) << 4)) =
+              make_float4(out[4 * j], out[4 * j + 1], out[4 * j + 2], out[4 * j + 3]);
+        }
+      } else if (contig) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = 8 * hf + 4 * h + j;
+          stg[row * 16 + (c ^ (row & 15))] = make_float4(out[4 * j], out[4 * j + 1], out[4 * j + 2], out[4 * j + 3]);
+        }
+      } else if (live) {
+#pragma unroll
+        for (int l = 0; l < 8; ++l)
+          psi[base | M.offs[16 * hf + 8 * h + l]] = make_float2(out[2 * l], out[2 * l + 1]);
+      }
+    }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     if (tma_out) {
-      // rows into two 128 x 32-float boxes (A_hi is free: the MMAs are done)
-      // in the tensor map's 128-byte swizzle (16-byte chunk c of row r at
-      // chunk c ^ (r & 7), so a warp's 32 rows hit every bank), then one
-      // tensor store per box writes them back as plain rows (rows past the
-      // state are clipped by the map)
-      unsigned char* box = A_hi + hf * (TC_M * 128);
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        *reinterpret_cast<float4*>(box + row * 128 + ((j ^ (row & 7)) << 4)) =
-            make_float4(out[4 * j], out[4 * j + 1], out[4 * j + 2], out[4 * j + 3]);
+      // one tensor store per box writes the rows back (rows past the state
+      // are clipped by the map)
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       __syncthreads();
       if (tid == 0) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+        for (int hb = 0; hb < 2; ++hb)
           asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(
                            reinterpret_cast<uint64_t>(&out_map)),
-                       "r"(32 * h), "r"((int)(tile * TC_M)), "r"(a_hi + (uint32_t)(h * TC_M * 128))
+                       "r"(32 * hb), "r"((int)(tile * TC_M)), "r"(a_s + (uint32_t)(hb * TC_M * 128))
                        : "memory");
         asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
       }
-    } else if (contig) {  // rows through shared memory (A_hi is free: the MMAs are done)
-#pragma unroll
-      for (int l4 = 0; l4 < 8; ++l4)
-        *reinterpret_cast<float4*>(A_hi + canon_off(row, 4 * (8 * hf + l4))) =
-            make_float4(out[4 * l4], out[4 * l4 + 1], out[4 * l4 + 2], out[4 * l4 + 3]);
+    } else if (contig) {  // rows through shared memory
       __syncthreads();
       float4* dst = reinterpret_cast<float4*>(psi) + tile * TC_M * 16;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int ii = 8 * hf + i;
-        if (tile * TC_M + 8 * ii + crow < ngroups)
-          dst[(8 * ii + crow) * 16 + cseg] = *reinterpret_cast<const float4*>(A_hi + canon_off(8 * ii + crow, 4 * cseg));
+        const int r = 8 * (8 * hf + i) + crow;
+        if (tile * TC_M + r < ngroups) dst[r * 16 + cseg] = stg[r * 16 + (cseg ^ (r & 15))];
       }
-    } else if (live) {
-#pragma unroll
-      for (int l = 0; l < 16; ++l) psi[base | M.offs[16 * hf + l]] = make_float2(out[2 * l], out[2 * l + 1]);
     }
     __syncthreads();  // every lane is read before the next tile's MMAs overwrite TMEM
     return true;
@@ -375,12 +451,13 @@ __global__ void __launch_bounds__(TC_T, 2) k_dense_tc(float2* __restrict__ psi, 
     if (tile + gridDim.x < ntiles && !body(tile + gridDim.x, RB, lb, bb)) break;
   }
   // an MMA that a timed-out wait left in flight: one more bounded wait
-  if (stop && tid == 0) mbar_wait(mbar_a, phase ^ 1u);
+  if (stop && tid == 0 && !no_mma) mbar_wait(mbar_a, phase ^ 1u, spin_limit);
   // output stores in flight finish before the CTA (and its shared memory) ends
   if (tma_out && tid == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;\n" ::"r"(tmem));
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(TC_TMEM_COLS));
 }
 
 }  // namespace qc
@@ -389,12 +466,6 @@ using namespace qc;
 
 // -------------------------------------------------------------- host ----
 namespace qc {
-
-static uint32_t tf32_hi_bits(float x) {
-  uint32_t b;
-  memcpy(&b, &x, 4);
-  return (b + 0x1000u) & 0xFFFFE000u;
-}
 
 qc_status dense_map(int n, int k, const int* qubits, DenseMap* M) {
   if (k < 1 || k > DENSE_MAX_K || k > n || !qubits) {
@@ -425,34 +496,45 @@ qc_status dense_map(int n, int k, const int* qubits, DenseMap* M) {
 bool dense_uses_tc(qc_dtype dt, int k) { return dt == QC_C64 && k == 5; }
 
 size_t dense_op_bytes(qc_dtype dt, int k) {
-  return dense_uses_tc(dt, k) ? 2 * sizeof(float) * TC_N * TC_K : sizeof(double) * 2 * (size_t)(1 << k) * (1 << k);
+  return dense_uses_tc(dt, k) ? TC_OP_BYTES + 16 : sizeof(double) * 2 * (size_t)(1 << k) * (1 << k);
 }
 
-// The device form of U: W^T split into TF32 hi and lo for the tensor cores
-// (W^T[n][kk], n the output real 2j or 2j+1, kk the input real 2l or
-// 2l+1), else U itself.
+// The device form of U.  For the tensor cores: W^T (W^T[nn][kk], nn the
+// output real 2j or 2j+1, kk the input real 2l or 2l+1) as float, cut into
+// the digit slices b0, b1, b2, 2^-8 b1, 2^-8 b2 (bf16, N x K each) with one scale
+// 2^(134 - E_w) from the largest |entry|, followed by 2^(E_w - 134) as a
+// float.  Otherwise U itself.
 void dense_pack(qc_dtype dt, int k, const double* U, void* host_out) {
   const int dim = 1 << k;
   if (!dense_uses_tc(dt, k)) {
     memcpy(host_out, U, sizeof(double) * 2 * dim * dim);
     return;
   }
-  float* hi = reinterpret_cast<float*>(host_out);
-  float* lo = hi + TC_N * TC_K;
+  std::vector<float> wt((size_t)TC_N * TC_K);
   for (int j = 0; j < dim; ++j)
     for (int l = 0; l < dim; ++l) {
       const double ur = U[2 * (j * dim + l)], ui = U[2 * (j * dim + l) + 1];
       const float vals[4] = {(float)ur, (float)-ui, (float)ui, (float)ur};  // (2j,2l) (2j,2l+1) (2j+1,2l) (2j+1,2l+1)
       const int rr[4] = {2 * j, 2 * j, 2 * j + 1, 2 * j + 1}, cc[4] = {2 * l, 2 * l + 1, 2 * l, 2 * l + 1};
-      for (int q = 0; q < 4; ++q) {
-        const float x = vals[q];
-        const uint32_t hb = tf32_hi_bits(x);
-        float h;
-        memcpy(&h, &hb, 4);
-        hi[rr[q] * TC_K + cc[q]] = h;
-        lo[rr[q] * TC_K + cc[q]] = x - h;
-      }
+      for (int q = 0; q < 4; ++q) wt[rr[q] * TC_K + cc[q]] = vals[q];
     }
+  uint32_t mx = 0;
+  for (float w : wt) mx = std::max(mx, ff_fbits(w) & 0x7FFFFFFFu);
+  const uint32_t Ew = slice_exp(mx);
+  const float sc = slice_scale(Ew);
+  uint16_t* out = reinterpret_cast<uint16_t*>(host_out);
+  const size_t S = (size_t)TC_N * TC_K;
+  for (size_t e = 0; e < S; ++e) {
+    float b0, b1, b2;
+    slice_digits(wt[e], sc, b0, b1, b2);
+    out[e] = bf16_bits_rn(b0);
+    out[S + e] = bf16_bits_rn(b1);
+    out[2 * S + e] = bf16_bits_rn(b2);
+    out[3 * S + e] = bf16_bits_rn(b1 * 0.00390625f);  // exact: b1 is a small integer
+    out[4 * S + e] = bf16_bits_rn(bf16_value(out[2 * S + e]) * 0.00390625f);  // exact: a power-of-two scaling
+  }
+  const float ws = slice_unscale(Ew);
+  memcpy(reinterpret_cast<unsigned char*>(host_out) + TC_OP_BYTES, &ws, sizeof ws);
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (looked up
@@ -492,7 +574,8 @@ static bool dense_out_map(const qc_state* s, uint64_t ngroups, CUtensorMap* tm) 
 // Launches one block on the state's stream (no allocation, no sync);
 // dev_op holds dense_pack's output; status (tensor cores) is a device word
 // that a timed-out wait sets to 1.
-qc_status dense_launch(qc_state* s, const DenseMap& M, const void* dev_op, int* status) {
+qc_status dense_launch(qc_state* s, const DenseMap& M, const void* dev_op, int* status, uint32_t spin_limit,
+                       int no_mma) {
   const int k = M.k, dim = 1 << k;
   const uint64_t ngroups = 1ull << (s->n - k);
   if (dense_uses_tc(s->dt, k)) {
@@ -509,9 +592,8 @@ qc_status dense_launch(qc_state* s, const DenseMap& M, const void* dev_op, int* 
     memset(&tm, 0, sizeof tm);
     const int use_tma = contig && dense_out_map(s, ngroups, &tm);
     k_dense_tc<<<grid, TC_T, TC_SMEM, s->stream>>>(reinterpret_cast<float2*>(s->data), ngroups,
-                                                     reinterpret_cast<const float*>(dev_op),
-                                                     reinterpret_cast<const float*>(dev_op) + TC_N * TC_K, M, status,
-                                                     tm, use_tma);
+                                                     reinterpret_cast<const uint16_t*>(dev_op), M, status, tm,
+                                                     use_tma, spin_limit, no_mma);
   } else if (s->dt == QC_C64) {
     const size_t smem = sizeof(float2) * ((size_t)dim * dim + DENSE_AMPS);
     static bool attr = false;
@@ -543,8 +625,10 @@ qc_status dense_launch(qc_state* s, const DenseMap& M, const void* dev_op, int* 
 
 }  // namespace qc
 
-QC_API qc_status qc_apply_dense(qc_state* s, int k, const int* qubits, const double* U) {
-  clear_error();
+// One dense block, synchronous for the tensor cores (to read the status
+// word); spin_limit and no_mma as in dense_launch.
+static qc_status apply_dense_impl(qc_state* s, int k, const int* qubits, const double* U, uint32_t spin_limit,
+                                  int no_mma) {
   qc_status st = check_state(s);
   if (st) return st;
   if (!U) {
@@ -573,7 +657,7 @@ QC_API qc_status qc_apply_dense(qc_state* s, int k, const int* qubits, const dou
     cudaFreeAsync(dbuf, s->stream);
     return cuda_fail(e, "dense operator upload");
   }
-  dense_launch(s, M, dbuf, status);
+  dense_launch(s, M, dbuf, status, spin_limit, no_mma);
   st = check_launch(dense_uses_tc(s->dt, k) ? "dense block (tensor cores)" : "dense block", 1);
   if (!st && dense_uses_tc(s->dt, k)) {
     int hstat = 0;
@@ -587,6 +671,27 @@ QC_API qc_status qc_apply_dense(qc_state* s, int k, const int* qubits, const dou
   }
   cudaFreeAsync(dbuf, s->stream);
   return st;
+}
+
+QC_API qc_status qc_apply_dense(qc_state* s, int k, const int* qubits, const double* U) {
+  clear_error();
+  return apply_dense_impl(s, k, qubits, U, QC_TC_SPIN_LIMIT, 0);
+}
+
+QC_API qc_status qc_dense_timeout_selftest(qc_state* s, uint32_t spin_limit) {
+  clear_error();
+  qc_status st = check_state(s);
+  if (st) return st;
+  if (s->dt != QC_C64 || s->n < 5 || spin_limit < 1 || spin_limit > QC_TC_SPIN_LIMIT) {
+    set_error("qc_dense_timeout_selftest: needs a complex64 state of >= 5 qubits and 1 <= spin_limit <= %u",
+              QC_TC_SPIN_LIMIT);
+    return QC_EINVAL;
+  }
+  // identity block on qubits 0..4: any operator would do, none is applied
+  std::vector<double> I(2 * 32 * 32, 0.0);
+  for (int d = 0; d < 32; ++d) I[2 * (d * 32 + d)] = 1.0;
+  const int q[5] = {0, 1, 2, 3, 4};
+  return apply_dense_impl(s, 5, q, I.data(), spin_limit, 1);
 }
 
 // ------------------------------------------------- Hamiltonian step ------

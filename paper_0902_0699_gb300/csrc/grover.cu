@@ -175,7 +175,104 @@ qc_status launch_grover_step(qc_state* s, const uint64_t* marked, int m) {
   MarkedList* dml = nullptr;
   st = upload_marked(s, marked, m, &dml);
   if (st) return st;
+  s->grover_partial_ready = false;  // the saved marked amplitudes are overwritten
   st = step_with(s, dml);
+  s->sum_valid = (st == QC_OK);
+  return st;
+}
+
+// ------------------------------------------ a state split over devices ----
+// For a state split over several devices (one shard per device, the high
+// index bits selecting the shard), the Grover mean needs the sum over all
+// shards: each shard contributes P_r = S_r - 2 sum_{marked in r} C, the
+// caller adds them (one scalar all-reduce) and hands back m = sum_r P_r / N.
+// The pass itself is the single-device one.
+template <typename R>
+__global__ void k_grover_partial(const typename CT<R>::V2* __restrict__ s, const MarkedList* __restrict__ ML,
+                                 double* __restrict__ scr) {
+  __shared__ double red[2][256];
+  double ar = 0.0, ai = 0.0;
+  for (int i = threadIdx.x; i < ML->m; i += blockDim.x) {
+    const auto v = s[ML->idx[i]];
+    scr[QC_SCR_MARKED + 2 * i] = (double)v.x;
+    scr[QC_SCR_MARKED + 2 * i + 1] = (double)v.y;
+    ar += (double)v.x;
+    ai += (double)v.y;
+  }
+  red[0][threadIdx.x] = ar;
+  red[1][threadIdx.x] = ai;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + w];
+      red[1][threadIdx.x] += red[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {  // P_r in the misc slots
+    scr[QC_SCR_MISC] = scr[QC_SCR_SUM] - 2.0 * red[0][0];
+    scr[QC_SCR_MISC + 1] = scr[QC_SCR_SUM + 1] - 2.0 * red[1][0];
+  }
+}
+
+// The given mean into the scratch, and the shard's next running sum
+// S_r' = N_r (2m) - P_r (2m rounded as the pass rounds it).
+template <typename R>
+__global__ void k_grover_set_mean(double* __restrict__ scr, uint64_t N, double mr, double mi) {
+  scr[QC_SCR_MEAN] = mr;
+  scr[QC_SCR_MEAN + 1] = mi;
+  const double tr = (double)(R)(2.0 * mr), ti = (double)(R)(2.0 * mi);
+  scr[QC_SCR_SUM] = (double)N * tr - scr[QC_SCR_MISC];
+  scr[QC_SCR_SUM + 1] = (double)N * ti - scr[QC_SCR_MISC + 1];
+}
+
+qc_status launch_grover_partial(qc_state* s, const uint64_t* marked, int m, double* out_host) {
+  qc_status st = QC_OK;
+  if (!s->sum_valid) {
+    st = launch_sum(s);
+    if (st) return st;
+  }
+  MarkedList* dml = nullptr;
+  st = upload_marked(s, marked, m, &dml);
+  if (st) return st;
+  if (s->dt == QC_C128)
+    k_grover_partial<double><<<1, 256, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), dml, s->scratch);
+  else
+    k_grover_partial<float><<<1, 256, 0, s->stream>>>(reinterpret_cast<const float2*>(s->data), dml, s->scratch);
+  st = check_launch("grover partial sum");
+  if (st) return st;
+  cudaError_t e = cudaMemcpyAsync(out_host, s->scratch + QC_SCR_MISC, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                  s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "grover partial readback");
+  s->grover_partial_ready = true;
+  return QC_OK;
+}
+
+qc_status launch_grover_apply(qc_state* s, const uint64_t* marked, int m, const double* mean) {
+  if (!s->grover_partial_ready || !s->sum_valid || (int)s->marked_host.size() != m ||
+      !std::equal(s->marked_host.begin(), s->marked_host.end(), marked)) {
+    set_error("qc_grover_apply_mean: call qc_grover_partial with the same marked list first");
+    return QC_EINVAL;
+  }
+  s->grover_partial_ready = false;
+  const uint64_t N = 1ull << s->n;
+  const int T = 256;
+  const MarkedList* dml = reinterpret_cast<const MarkedList*>(s->marked_dev);
+  if (s->dt == QC_C128) {
+    k_grover_set_mean<double><<<1, 1, 0, s->stream>>>(s->scratch, N, mean[0], mean[1]);
+    const unsigned g = std::min<unsigned>(resident_grid(k_grover_pass_c128, T, N, GROVER_UNR * T), 3u * (unsigned)sm_count());
+    k_grover_pass_c128<<<g, T, 0, s->stream>>>(reinterpret_cast<double2*>(s->data), N, s->scratch);
+    k_grover_fix<double><<<1, 256, 0, s->stream>>>(reinterpret_cast<double2*>(s->data), dml, s->scratch);
+  } else {
+    k_grover_set_mean<float><<<1, 1, 0, s->stream>>>(s->scratch, N, mean[0], mean[1]);
+    const uint64_t N2 = N / 2;
+    if (N2 > 0)
+      k_grover_pass_c64<<<resident_grid(k_grover_pass_c64, T, N2, 2 * T), T, 0, s->stream>>>(
+          reinterpret_cast<float4*>(s->data), N2, s->scratch);
+    k_grover_fix<float><<<1, 256, 0, s->stream>>>(reinterpret_cast<float2*>(s->data), dml, s->scratch);
+  }
+  qc_status st = check_launch("grover pass (given mean)", 3);
   s->sum_valid = (st == QC_OK);
   return st;
 }

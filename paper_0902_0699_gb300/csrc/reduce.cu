@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <atomic>
+
 #include "common.cuh"
 
 namespace qc {
@@ -823,7 +825,9 @@ static __device__ __align__(256) uint64_t g_noalloc_scratch[NA_CDF + NA_BSUM + 3
 
 // Device address of the scratch per device (host code only sees a host-side
 // stand-in for the symbol, so the address is looked up once per device).
-static uint64_t* g_noalloc_ptr[64] = {nullptr};
+// Atomic slots: first calls from several host threads may race to fill one;
+// they store the same value.
+static std::atomic<uint64_t*> g_noalloc_ptr[64];
 
 // Status bits: 1 = some p_i outside [0, 2] (or NaN, from k_wsum), 2 = total
 // weight zero or above 2^63.
@@ -860,13 +864,14 @@ QC_API qc_status qc_sample_noalloc(const void* psi_dev, int n, qc_dtype dt, uint
     set_error("qc_sample_noalloc: device ordinal %d not supported", dev);
     return QC_EINVAL;
   }
-  if (!g_noalloc_ptr[dev]) {  // first call on this device: look up the scratch address
+  uint64_t* cdf = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+  if (!cdf) {  // first call on this device: look up the scratch address
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "qc_sample_noalloc: scratch address");
-    g_noalloc_ptr[dev] = reinterpret_cast<uint64_t*>(ptr);
+    cdf = reinterpret_cast<uint64_t*>(ptr);
+    g_noalloc_ptr[dev].store(cdf, std::memory_order_release);
   }
-  uint64_t* cdf = g_noalloc_ptr[dev];
   uint64_t* bsum = cdf + NA_CDF;
   uint64_t* status = bsum + NA_BSUM;
   cudaStream_t st = (cudaStream_t)stream;

@@ -624,6 +624,11 @@ static qc_status layer_impl(qc_state* s, const double* U, uint64_t mask) {
 
 qc_status launch_layer(qc_state* s, const double* U, uint64_t mask) {
   s->sum_valid = false;
+  // a layer of Hadamards only (HALL among them): Walsh-Hadamard passes
+  bool all_h = mask != 0;
+  for (int q = 0; q < s->n && all_h; ++q)
+    if ((mask >> q) & 1) all_h = is_exact_hadamard(U + 8 * q);
+  if (all_h && s->n >= hadamard_layer_min_qubits(s->dt)) return launch_hadamard_layer(s, mask);
   return s->dt == QC_C128 ? layer_impl<double>(s, U, mask) : layer_impl<float>(s, U, mask);
 }
 

@@ -66,6 +66,10 @@ struct TrajParams {
   double* p_readout;
   uint64_t* outcome;
   uint32_t* n_errors;
+  // optional: instance i's final state goes to states + state_off[i]
+  // (amplitudes; ~0 skips the instance)
+  float2* states;
+  const uint64_t* state_off;
 };
 
 // Pauli string i^a X^x Z^z.
@@ -734,9 +738,15 @@ __global__ void __launch_bounds__(512, MINB) k_traj(TrajParams P) {
     __syncthreads();
     float roh = 0.f, rol = 0.f;
     unsigned long long wt = 0;
+    const uint64_t soff = P.states ? P.state_off[I.id] : ~0ull;
+    float2* sdst = soff != ~0ull ? P.states + soff : nullptr;
     for (uint32_t v = (lo >> 1) + tid; v < (hi >> 1); v += T) {
       const float4 u = p4[v];
       const float2 v0 = make_float2(u.x, u.y), v1 = make_float2(u.z, u.w);
+      if (sdst) {  // the state the read-out is drawn from
+        sdst[2 * v] = v0;
+        sdst[2 * v + 1] = v1;
+      }
       const float p0 = fmaf(v0.x, v0.x, v0.y * v0.y), p1 = fmaf(v1.x, v1.x, v1.y * v1.y);
       ff_add(roh, rol, fmaf(p0, wtab[__popc((2 * v) ^ m)], p1 * wtab[__popc((2 * v + 1) ^ m)]));
       wt += ro_weight(v0) + ro_weight(v1);
@@ -838,6 +848,8 @@ struct qc_traj_plan {
   int G, T, grid, minb;
   cudaGraphExec_t gexec;
   qc_traj_out last_out;
+  float2* last_states;
+  const uint64_t* last_state_off;
   bool have_graph;
 };
 
@@ -1062,14 +1074,15 @@ QC_API qc_status qc_traj_plan_create(const qc_traj_desc* d, void* stream, int au
   return check_launch("trajectory plan", autotune ? 2 * (int)cands.size() : 0);
 }
 
-QC_API qc_status qc_traj_plan_run(qc_traj_plan* p, const qc_traj_out* o) {
-  clear_error();
-  if (!p || !o || !o->p_success || !o->p_readout || !o->outcome || !o->n_errors) {
+static qc_status traj_run(qc_traj_plan* p, const qc_traj_out* o, const uint64_t* state_off, void* states) {
+  if (!p || !o || !o->p_success || !o->p_readout || !o->outcome || !o->n_errors || (!state_off) != (!states)) {
     set_error("bad plan or output pointers");
     return QC_EINVAL;
   }
+  float2* st = reinterpret_cast<float2*>(states);
   const bool same = p->have_graph && o->p_success == p->last_out.p_success && o->p_readout == p->last_out.p_readout &&
-                    o->outcome == p->last_out.outcome && o->n_errors == p->last_out.n_errors;
+                    o->outcome == p->last_out.outcome && o->n_errors == p->last_out.n_errors &&
+                    st == p->last_states && state_off == p->last_state_off;
   if (!same) {
     if (p->have_graph) {
       cudaGraphExecDestroy(p->gexec);
@@ -1080,19 +1093,23 @@ QC_API qc_status qc_traj_plan_run(qc_traj_plan* p, const qc_traj_out* o) {
     prm.p_readout = o->p_readout;
     prm.outcome = o->outcome;
     prm.n_errors = o->n_errors;
+    prm.states = st;
+    prm.state_off = state_off;
     cudaGraph_t g;
     cudaError_t e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "graph capture");
     cudaMemsetAsync(p->queue, 0, sizeof(unsigned) + sizeof(int), p->stream);
-    qc_status st = traj_launch(p, p->G, p->T, p->grid, p->minb, prm);
+    qc_status rs = traj_launch(p, p->G, p->T, p->grid, p->minb, prm);
     e = cudaStreamEndCapture(p->stream, &g);
-    if (st) return st;
+    if (rs) return rs;
     if (e != cudaSuccess) return cuda_fail(e, "graph capture end");
     e = cudaGraphInstantiate(&p->gexec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
     p->have_graph = true;
     p->last_out = *o;
+    p->last_states = st;
+    p->last_state_off = state_off;
   }
   // order: caller's stream -> plan stream (graph) -> caller's stream
   cudaError_t e = cudaEventRecord(p->ev_in, p->user);
@@ -1102,6 +1119,21 @@ QC_API qc_status qc_traj_plan_run(qc_traj_plan* p, const qc_traj_out* o) {
   if (e == cudaSuccess) e = cudaStreamWaitEvent(p->user, p->ev_out, 0);
   if (e != cudaSuccess) return cuda_fail(e, "graph launch");
   return check_launch("trajectory run", 1);
+}
+
+QC_API qc_status qc_traj_plan_run(qc_traj_plan* p, const qc_traj_out* o) {
+  clear_error();
+  return traj_run(p, o, nullptr, nullptr);
+}
+
+QC_API qc_status qc_traj_plan_run_states(qc_traj_plan* p, const qc_traj_out* o, const uint64_t* state_off_dev,
+                                         void* states_dev) {
+  clear_error();
+  if (!state_off_dev || !states_dev) {
+    set_error("qc_traj_plan_run_states: NULL offsets or state buffer");
+    return QC_EINVAL;
+  }
+  return traj_run(p, o, state_off_dev, states_dev);
 }
 
 QC_API qc_status qc_traj_plan_info(const qc_traj_plan* p, int* G, int* T, int* grid) {

@@ -15,3 +15,14 @@ def test_ff_layer_on_host():
                                os.path.join(HERE, "ff_host_check.cpp"), "-o", exe])
         out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
         assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
+
+
+def test_bf16_digit_slices_on_host():
+    # the tensor-core block's digit slices (slices.cuh) and its product
+    # formula, against long double references
+    with tempfile.TemporaryDirectory() as td:
+        exe = os.path.join(td, "slicecheck")
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
+                               os.path.join(HERE, "slices_host_check.cpp"), "-o", exe])
+        out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+        assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr

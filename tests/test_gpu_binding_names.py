@@ -96,6 +96,24 @@ def test_trajectory_plan_wrappers(qc):
     assert np.array_equal(outs["ps"].cpu().numpy(), got["p_success"].cpu().numpy())
     assert np.array_equal(outs["oc"].cpu().numpy(), got["outcome"].cpu().numpy())
     assert np.array_equal(outs["ne"].cpu().numpy(), got["n_errors"].cpu().numpy())
+    # final states: the same-name call and the wrapper's keep= give the same
+    h = qc.qc_traj_plan_create(d, None, False)
+    off = np.full(len(nq), np.iinfo(np.uint64).max, dtype=np.uint64)
+    off[5] = 0
+    off_d = torch.from_numpy(off.view(np.int64)).cuda()
+    st = torch.empty(1 << int(nq[5]), dtype=torch.complex64, device="cuda")
+    qc.qc_traj_plan_run_states(h, qc.TrajOut(outs["ps"].data_ptr(), outs["pr"].data_ptr(), outs["oc"].data_ptr(),
+                                             outs["ne"].data_ptr()), off_d.data_ptr(), st.data_ptr())
+    torch.cuda.synchronize()
+    qc.qc_traj_plan_free(h)
+    plan = qc.TrajectoryPlan(tb.nq, tb.marked, tb.iters, tb.seed, p_gate=0.01, p_readout=0.01, autotune=False)
+    got = plan.run(keep=[5])
+    torch.cuda.synchronize()
+    plan.close()
+    assert torch.equal(got["states"][5], st)
+    assert np.array_equal(outs["oc"].cpu().numpy(), got["outcome"].cpu().numpy())
+    w = O.readout_weights_c64(st.cpu().numpy())
+    assert int(got["outcome"][5]) == O.trajectory_measure_weights(w, int(nq[5]), tb.seed, 5, tb.thr_readout)
 
 
 @pytest.mark.parametrize("dt", [0, 1])

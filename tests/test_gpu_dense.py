@@ -47,10 +47,14 @@ def test_tensor_core_block_c64(qc, n, qubits):
 
 @pytest.mark.parametrize("qubits", [[0, 1, 2, 3, 4], [5, 6, 7, 8, 9], [19, 3, 14, 9, 11]])
 def test_tensor_core_block_c64_relative_accuracy(qc, qubits):
-    # 3xTF32 keeps a block at FP32-class accuracy: relative to the state
-    # (not to 1e-5 absolute, which plain TF32 would also meet at small n).
-    # The tensor cores' FP32 accumulation leaves a uniform shrink of about
-    # 7e-7 per block; anything near TF32's 2^-11 would fail here.
+    # The bf16 digit slices keep a block at FP32-class accuracy relative to
+    # the state (not to 1e-5 absolute, which a single bf16 or TF32 product
+    # would also meet at small n): every output is rounded once from sums
+    # that are exact or 2^-8 below the result, so the error is a few 2^-25
+    # of the row scale and has no sign preference.  The fitted scale
+    # <ref, got>/<ref, ref> - 1 then averages 2^20 independent errors; a
+    # truncating accumulation (what FP32 sums on the tensor cores do) would
+    # show here as a uniform shrink of about 1e-7 per chained product.
     n = 20
     U = unitary(W.rng(900 + sum(qubits)), 32)
     s = qc.State(n, 1)
@@ -60,9 +64,42 @@ def test_tensor_core_block_c64_relative_accuracy(qc, qubits):
     qc.qc_apply_dense(s.h, qubits, U)
     got = s.numpy().astype(np.complex128)
     ref = O.apply_dense(x, n, list(qubits), U)
-    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 2e-6
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1.5e-7
     scale = np.vdot(ref, got) / np.vdot(ref, ref) - 1
-    assert abs(scale) <= 2e-6
+    assert abs(scale) <= 2e-8
+
+
+def test_tensor_core_block_chain_keeps_the_norm(qc):
+    # 200 blocks in a row on one state: without a bias the norm drifts like a
+    # random walk of ~2^-25 steps, far below 1e-5
+    n = 16
+    s = qc.State(n, 1)
+    s.load(W.random_state(W.rng(77), n))
+    g = W.rng(78)
+    for i in range(200):
+        qs = [int(q) for q in g.permutation(n)[:5]]
+        qc.qc_apply_dense(s.h, qs, unitary(g, 32))
+    assert abs(s.norm() - 1.0) <= 1e-5
+
+
+def test_tensor_core_wait_timeout_selftest(qc):
+    # the bounded mbarrier wait runs out (no MMA issued, nothing asynchronous
+    # in flight): the call reports QC_ETIMEOUT, the state is untouched and
+    # the next block on the same stream is correct
+    n = 12
+    s = qc.State(n, 1)
+    v = W.random_state(W.rng(3), n)
+    s.load(v)
+    before = s.numpy()
+    assert qc.qc_dense_timeout_selftest(s.h, 1024) == qc.QC_ETIMEOUT
+    assert "timed out" in qc.last_error()
+    assert np.array_equal(s.numpy(), before)
+    U = unitary(W.rng(4), 32)
+    qc.qc_apply_dense(s.h, [0, 1, 2, 3, 4], U)
+    ref = O.apply_dense(before.astype(np.complex128), n, [0, 1, 2, 3, 4], U)
+    assert np.max(np.abs(s.numpy() - ref)) <= 1e-6
+    with pytest.raises(qc.QCError):  # the limit is validated
+        qc._check(qc.qc_dense_timeout_selftest(s.h, 0))
 
 
 @pytest.mark.parametrize("dt", [0, 1])

@@ -137,3 +137,37 @@ def test_readout_success_enumeration():
             if j ^ f == marked:
                 tot += p[j] * w
     assert abs(O.readout_success(p, n, marked, pr) - tot) < 1e-15
+
+
+def test_readout_weights_c64_exact():
+    # trunc(re^2 2^62) + trunc(im^2 2^62) of float32 parts, against exact
+    # rational arithmetic (Fraction) on random, tiny and edge values
+    from fractions import Fraction
+    g = np.random.default_rng(3)
+    re = np.concatenate([g.standard_normal(300) * 0.01, [0.0, -0.0, 1.0, -0.5, 2.0 ** -40, 3e-30, 1.0 - 2 ** -24]])
+    im = np.concatenate([g.standard_normal(300) * 0.003, [1.0, 0.25, 0.0, -0.75, 2.0 ** -31, 1e-20, 2 ** -12]])
+    psi = (re + 1j * im).astype(np.complex64)
+    w = O.readout_weights_c64(psi)
+    for j in range(len(psi)):
+        r, i = Fraction(float(psi[j].real)), Fraction(float(psi[j].imag))
+        ref = int(r * r * 2 ** 62) + int(i * i * 2 ** 62)  # int() truncates toward zero
+        assert int(w[j]) == ref
+
+
+def test_measure_from_weights_matches_probability_rule():
+    # the weight form of the read-out equals the probability form when the
+    # weights are trunc(p 2^62), and a weight moved across the target's
+    # boundary moves the outcome (the replay is sensitive to the weights)
+    g = np.random.default_rng(4)
+    n = 9
+    p = g.random(1 << n)
+    p /= p.sum()
+    for inst in range(20):
+        a = O.trajectory_measure(p, n, 77, inst, 0)
+        b = O.trajectory_measure_weights((p * O.TWO62).astype(np.uint64), n, 77, inst, 0)
+        assert a == b
+    w = (p * O.TWO62).astype(np.uint64)
+    out = O.trajectory_measure_weights(w, n, 77, 0, 0)
+    w2 = w.copy()
+    w2[out] = 0  # nothing left at the drawn outcome: the draw must land elsewhere
+    assert O.trajectory_measure_weights(w2, n, 77, 0, 0) != out
