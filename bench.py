@@ -477,11 +477,15 @@ class HostBuffer:
 
 def run_e2e(args, st, step_fn, ops_per_step, N):
     """Same workload through the public API with the state in pinned host
-    memory: every step copies its input state host->device, runs the step
-    and copies its final state and samples back.  Two device states are
-    used in turn, so step i+1's upload and step i-1's download (on their
-    own streams) overlap step i's compute, as a production pipeline would;
-    the timed region still holds every step's copies."""
+    memory: every step copies its input state (|0..0>) host->device, runs
+    the step and copies its final state and samples back.  Two device
+    states are used in turn.  The upload runs on the compute stream right
+    before its step, and the download of step i-1 is issued after it on its
+    own stream, where it overlaps step i: on this host link a host->device
+    copy that runs at the same time as a device->host copy crawls at 8-17
+    GB/s, against about 210 GB/s alone (the device->host copy keeps about
+    190 GB/s next to compute).  The timed region holds every step's
+    copies."""
     import numpy as np
     import torch
     import paper_0902_0699_gb300 as qc
@@ -497,8 +501,7 @@ def run_e2e(args, st, step_fn, ops_per_step, N):
     comp = torch.cuda.current_stream()
     st2 = qc.State(n, st.dt)
     states = [st, st2]
-    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-    ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+    s_out = torch.cuda.Stream()
     ev_done = [torch.cuda.Event(), torch.cuda.Event()]
     ev_free = [torch.cuda.Event(), torch.cuda.Event()]
     issued_free = [False, False]
@@ -512,33 +515,34 @@ def run_e2e(args, st, step_fn, ops_per_step, N):
         z.record(stream)
         copies[kind].append((a, z))
 
-    def upload(b):
-        with torch.cuda.stream(s_in):
-            if issued_free[b]:
-                s_in.wait_event(ev_free[b])  # the previous download of this buffer is done
-            timed_copy("h2d", s_in, lambda: states[b].tensor.copy_(host_in, non_blocking=True))
-            ev_in[b].record(s_in)
-
-    def run(b):
-        comp.wait_event(ev_in[b])
-        qc.qc_state_invalidate(states[b].h)
-        shots = step_fn(None, None, states[b])
-        ev_done[b].record(comp)
+    def download(b):
         with torch.cuda.stream(s_out):
             s_out.wait_event(ev_done[b])
             timed_copy("d2h", s_out, lambda: host_out.copy_(states[b].tensor, non_blocking=True))
-            host_shots.copy_(shots, non_blocking=True)
+            host_shots.copy_(shots_of[b], non_blocking=True)
             ev_free[b].record(s_out)
         issued_free[b] = True
 
+    shots_of = [None, None]
+
     def pipeline(k):
-        upload(0)
-        if k > 1:
-            upload(1)
+        # upload i (compute stream, alone on the host link), then download
+        # i-1 (its own stream, overlapping step i), then step i
         for i in range(k):
-            run(i % 2)
-            if i + 2 < k:
-                upload(i % 2)
+            b = i % 2
+            if issued_free[b]:
+                comp.wait_event(ev_free[b])  # the previous download of this buffer is done
+            timed_copy("h2d", comp, lambda: states[b].tensor.copy_(host_in, non_blocking=True))
+            ev_up.record(comp)
+            if i > 0:
+                s_out.wait_event(ev_up)
+                download(1 - b)
+            qc.qc_state_invalidate(states[b].h)
+            shots_of[b] = step_fn(None, None, states[b])
+            ev_done[b].record(comp)
+        download((k - 1) % 2)
+
+    ev_up = torch.cuda.Event()
     pipeline(2)  # warm-up
     torch.cuda.synchronize()
     copies["h2d"].clear()
@@ -547,7 +551,7 @@ def run_e2e(args, st, step_fn, ops_per_step, N):
     pipeline(args.steps)
     torch.cuda.synchronize()
     el = (time.perf_counter() - t0) * 1e3
-    # the host link's rate as each copy saw it (the copies overlap compute)
+    # the host link's rate as each copy saw it
     rate = {k: statistics.mean(N * amp / (a.elapsed_time(z) * 1e-3) / 1e9 for a, z in v) if v else None
             for k, v in copies.items()}
     tmax, wsum = aggregate(el, float(ops_per_step) * N * args.steps)
@@ -560,8 +564,9 @@ def run_e2e(args, st, step_fn, ops_per_step, N):
     return {"value": wsum / (tmax / 1e3), "unit": UNIT, "h2d_bytes_per_step": N * amp,
             "d2h_bytes_per_step": N * amp + 8 * 1000, "ms_per_step": tmax / args.steps,
             "h2d_GBps_seen": rate["h2d"], "d2h_GBps_seen": rate["d2h"], "host_buffers": pinned,
-            "note": "host state in pinned memory -> device, full step, final state and samples -> host; "
-                    "two device states in turn, uploads and downloads on their own streams overlap compute"}
+            "note": "host |0..0> in pinned memory -> device on the compute stream before each step (never next to "
+                    "a download), full step, final state and samples -> host on their own stream (overlapping the "
+                    "next step); two device states in turn"}
 
 
 # ---------------------------------------------------------------- extras ----
@@ -624,6 +629,36 @@ def extra_c64(n=32, iters=100):
     del st
     torch.cuda.empty_cache()
     return res
+
+
+def extra_rho64(n=13, B=64, reps=3):
+    """The ensemble density matrix of B random complex64 states on the
+    tensor cores (profiling helper): rho is 4^n x 8 bytes (512 MiB at
+    n = 13, larger than L2)."""
+    import numpy as np
+    import torch
+    import paper_0902_0699_gb300 as qc
+    g = torch.Generator(device="cuda")
+    g.manual_seed(13)
+    t = torch.randn(B << n, 2, dtype=torch.float32, device="cuda", generator=g)
+    t = torch.view_as_complex(t).reshape(B, 1 << n)
+    t /= t.abs().pow(2).sum(dim=1, keepdim=True).sqrt()
+    P = np.full(B, 1.0 / B)
+    N = 1 << n
+    rho = torch.empty(N * N, dtype=torch.complex64, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    qc.qc_density_matrix(t.data_ptr(), n, qc.QC_C64, B, P, rho.data_ptr(), s)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        qc.qc_density_matrix(t.data_ptr(), n, qc.QC_C64, B, P, rho.data_ptr(), s)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    tr = float(rho.view(N, N).diagonal().real.sum().item())
+    return {"qubits": n, "universes": B, "ms": ms, "GB/s_written": N * N * 8 / (ms * 1e6),
+            "trace_minus_1": tr - 1.0}
 
 
 def extra_u2_sweep(n=30, dtype="c128", reps=1):
@@ -985,13 +1020,29 @@ def extra_f3(n=14, B=64):
     torch.cuda.synchronize()
     t_rho = a.elapsed_time(b_)
     p_m = float(rho[m * N + m].real.item())
+    del rho
+    # the same ensemble in complex64: rho on the tensor cores
+    t64 = t.to(torch.complex64)
+    rho64 = torch.empty(N * N, dtype=torch.complex64, device="cuda")
+    qc.qc_density_matrix(t64.data_ptr(), n, qc.QC_C64, B, mv.P, rho64.data_ptr(), stream)
+    a.record()
+    for _ in range(3):
+        qc.qc_density_matrix(t64.data_ptr(), n, qc.QC_C64, B, mv.P, rho64.data_ptr(), stream)
+    b_.record()
+    torch.cuda.synchronize()
+    t_rho64 = a.elapsed_time(b_) / 3
+    rho64_mm = float(rho64[m * N + m].real.item())
+    del rho64, t64
     qc.qc_mixed_spectrum(t.data_ptr(), n, qc.QC_C128, B, mv.P)
     t0 = time.perf_counter()
     ev, (tr, pur, ent) = qc.qc_mixed_spectrum(t.data_ptr(), n, qc.QC_C128, B, mv.P)
     t_spec = time.perf_counter() - t0
-    del rho
     return {"qubits": n, "universes": B, "grover_iterations": k, "runs_ms": t_runs * 1e3,
             "rho_ms (complex128, 4^n entries)": t_rho, "rho_GB/s_written": N * N * 16 / (t_rho * 1e6),
+            "rho_ms (complex64, tensor cores, synchronous call)": t_rho64,
+            "rho64_GB/s_written": N * N * 8 / (t_rho64 * 1e6),
+            "rho64_tensor_TFLOP/s (bf16 digit products executed)": 2.0 * 8 * (2 * B) * (2 * N * N) / (t_rho64 * 1e9),
+            "rho64_mm_minus_rho128_mm": rho64_mm - p_m,
             "spectrum_ms (Gram + Jacobi, synchronous)": t_spec * 1e3, "trace": tr, "purity": pur,
             "entropy": ent, "p_success_rho_mm": p_m, "largest_eigenvalue": float(ev[0])}
 
@@ -1110,7 +1161,7 @@ def main():
               # a small trajectory batch (96 instances, 16..18 qubits) for profiling
               "c4s": lambda: extra_c4(96, 16, 18, seed=7, autotune=0), "f3": extra_f3,
               "dense": extra_dense, "dense26": lambda: extra_dense(26, 2), "red": extra_red,
-              "u2": extra_u2_sweep, "u2_26": lambda: extra_u2_sweep(26)}[args.only]
+              "u2": extra_u2_sweep, "u2_26": lambda: extra_u2_sweep(26), "rho64": extra_rho64}[args.only]
         print(json.dumps({args.only: fn()}), flush=True)
         return 0
     out, st, step_fn, ops, N = run_ours(args, ws, rank, local)

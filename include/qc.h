@@ -518,8 +518,12 @@ qc_status qc_wigner_d(int twoj, double alpha, double beta, double gamma, double*
 /* The ensemble density matrix (sec. 6.1):
  *   rho[n][n'] = sum_a P_a C_a(n) C_a(n')^*,
  * written row-major to rho_dev (device, 4^n amplitudes of dtype dt, owned by
- * the caller).  1 <= n <= QC_DM_MAX_QUBITS, B >= 1.  Stream-ordered; the
- * inner products run in double-float. */
+ * the caller).  1 <= n <= QC_DM_MAX_QUBITS, B >= 1.  complex64 with B <= 64
+ * runs on the tensor cores (the real GEMM of 128 x 32 tiles over K = 2B,
+ * operands in bf16 digit slices with exact leading sums; FP32-class
+ * accuracy) and synchronises the stream to read a status word (QC_ETIMEOUT
+ * if a device wait gave up); other cases are stream-ordered on CUDA cores
+ * (complex128 inner products in double-float). */
 qc_status qc_density_matrix(const void* psi_dev, int n, qc_dtype dt, int B, const double* P_host,
                             void* rho_dev, void* stream);
 

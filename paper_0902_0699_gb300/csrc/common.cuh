@@ -355,6 +355,10 @@ void dense_pack(qc_dtype dt, int k, const double* U, void* host_out);
 // no_mma = 1 is the timeout self-test (no MMA is issued, so the first wait
 // runs out with nothing asynchronous in flight).
 #define QC_TC_SPIN_LIMIT (1u << 20)
+// The ensemble density matrix of a complex64 batch (B <= 64) on the tensor
+// cores (rho_tc.cu); synchronous.
+qc_status rho_tc_c64(const float2* psi, int n, int B, const double* P_host, float2* rho, cudaStream_t s);
+
 qc_status dense_launch(qc_state* s, const DenseMap& M, const void* dev_op, int* status,
                        uint32_t spin_limit = QC_TC_SPIN_LIMIT, int no_mma = 0);
 

@@ -26,6 +26,7 @@
 
 #include "common.cuh"
 #include "slices.cuh"
+#include "tc5.cuh"
 
 namespace qc {
 
@@ -143,10 +144,8 @@ __global__ void __launch_bounds__(DENSE_T) k_dense(typename DenseT<R>::V* __rest
 #define TC_T 256  // threads: two per tile row (halves of 16 amplitudes)
 #define TC_K 64
 #define TC_N 64
-#define TC_LBO 128
-#define TC_SBO 1024
-#define TC_A_SLICE (TC_M * TC_K * 2)  // 16 KiB per A digit
-#define TC_B_SLICE (TC_N * TC_K * 2)  // 8 KiB per W digit
+#define TC_A_SLICE TC5_A_SLICE  // 16 KiB per A digit
+#define TC_B_SLICE TC5_B_SLICE  // 8 KiB per W digit
 #define TC_NA 3                       // a0, a1, a2
 #define TC_NB 5                       // b0, b1, b2, 2^-8 b1, 2^-8 b2
 #define TC_OP_BYTES (TC_NB * TC_B_SLICE)  // device operator: the W digits, then the W scale (float)
@@ -154,51 +153,6 @@ __global__ void __launch_bounds__(DENSE_T) k_dense(typename DenseT<R>::V* __rest
 // columns each (three 64-column accumulators; allocations are powers of two).
 #define TC_SMEM (TC_NA * TC_A_SLICE + TC_NB * TC_B_SLICE + TC_M * 4 + 64)
 #define TC_TMEM_COLS 256
-
-__device__ __forceinline__ uint32_t canon_off(int r, int k) {  // byte offset of bf16 (row r, column k)
-  return (uint32_t)((r >> 3) * TC_SBO + (k >> 3) * TC_LBO + (r & 7) * 16 + (k & 7) * 2);
-}
-
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(TC_LBO >> 4) << 16) | ((uint64_t)(TC_SBO >> 4) << 32) |
-         (1ull << 46);  // descriptor version 1, no swizzle (layout 0)
-}
-
-// kind::f16, D = F32, A = B = BF16, both K-major, N = 64, M = 128
-#define TC_IDESC ((1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24))
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(da), "l"(db), "r"(TC_IDESC), "r"(acc));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit) {
-  for (uint32_t it = 0; it < limit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-// 16 consecutive accumulator columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 __device__ __forceinline__ uint32_t abs_bits(float x) { return __float_as_uint(x) & 0x7FFFFFFFu; }
 __device__ __forceinline__ uint32_t max4_bits(const float4& v) {
@@ -254,7 +208,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_dense_tc(float2* __restrict__ psi, 
   // W^T digits into the canonical layout (once per CTA)
   for (int e = tid; e < TC_NB * TC_N * TC_K; e += TC_T) {
     const int s = e / (TC_N * TC_K), rc = e % (TC_N * TC_K), r = rc / TC_K, c = rc % TC_K;
-    *reinterpret_cast<uint16_t*>(B + s * TC_B_SLICE + canon_off(r, c)) = Wd[e];
+    *reinterpret_cast<uint16_t*>(B + s * TC_B_SLICE + tc5_canon_off(r, c)) = Wd[e];
   }
   const float wscale = *reinterpret_cast<const float*>(Wd + TC_NB * TC_N * TC_K);
   for (int r = tid; r < TC_M; r += TC_T) rowmax[r] = 0u;
@@ -342,7 +296,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_dense_tc(float2* __restrict__ psi, 
     for (int i = 0; i < 8; ++i) {  // digits of two amplitudes (4 reals) per 8-byte piece of a row
       const int r = contig ? 8 * (8 * hf + i) + crow : row;
       const int k = contig ? 4 * cseg : 4 * (8 * hf + i);
-      stage4(R[i], slice_scale(slice_exp(rowmax[r])), A, canon_off(r, k));
+      stage4(R[i], slice_scale(slice_exp(rowmax[r])), A, tc5_canon_off(r, k));
     }
     // the tensor core reads shared memory through the async proxy
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -359,15 +313,15 @@ __global__ void __launch_bounds__(TC_T, 2) k_dense_tc(float2* __restrict__ psi, 
         const uint32_t d = tmem + acc_of[t] * TC_N;
         const bool first = (t == 0 || t == 1 || t == 3);  // first term of its accumulator
         for (int s = 0; s < TC_K / 16; ++s)  // K = 16 bf16 per MMA: two core matrices along K
-          mma_bf16(d, smem_desc(a_s + pa[t] * TC_A_SLICE + s * 2 * TC_LBO),
-                   smem_desc(b_s + pb[t] * TC_B_SLICE + s * 2 * TC_LBO), (first && s == 0) ? 0u : 1u);
+          tc5_mma_bf16(d, tc5_smem_desc(a_s + pa[t] * TC_A_SLICE + s * 2 * TC5_LBO),
+                   tc5_smem_desc(b_s + pb[t] * TC_B_SLICE + s * 2 * TC5_LBO), (first && s == 0) ? 0u : 1u);
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar_a)
                    : "memory");
     }
     // tile + 2 grid's loads overlap this tile's MMAs and epilogue and the next tile
     if (tile + 2ull * gridDim.x < ntiles) fetch(tile + 2ull * gridDim.x, R, rlive, rbase);
-    if (!mbar_wait(mbar_a, phase, spin_limit)) {
+    if (!tc5_mbar_wait(mbar_a, phase, spin_limit)) {
       if (tid == 0) atomicExch(status, 1);
       stop = 1;
     }
@@ -383,11 +337,11 @@ __global__ void __launch_bounds__(TC_T, 2) k_dense_tc(float2* __restrict__ psi, 
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       float out[16], acc1[16];
-      tmem_ld16(lane_base + TC_N + 16 * h, out);
-      tmem_ld16(lane_base + 2 * TC_N + 16 * h, acc1);
+      tc5_tmem_ld16(lane_base + TC_N + 16 * h, out);
+      tc5_tmem_ld16(lane_base + 2 * TC_N + 16 * h, acc1);
 #pragma unroll
       for (int j = 0; j < 16; ++j) acc1[j] = __fadd_rn(out[j], acc1[j]);  // acc1 + acc2
-      tmem_ld16(lane_base + 16 * h, out);  // acc0
+      tc5_tmem_ld16(lane_base + 16 * h, out);  // acc0
 #pragma unroll
       for (int j = 0; j < 16; ++j) out[j] = __fmul_rn(__fmul_rn(__fmaf_rn(acc1[j], 0.00390625f, out[j]), wscale), us);
       if (tma_out) {
@@ -451,7 +405,7 @@ __global__ void __launch_bounds__(TC_T, 2) k_dense_tc(float2* __restrict__ psi, 
     if (tile + gridDim.x < ntiles && !body(tile + gridDim.x, RB, lb, bb)) break;
   }
   // an MMA that a timed-out wait left in flight: one more bounded wait
-  if (stop && tid == 0 && !no_mma) mbar_wait(mbar_a, phase ^ 1u, spin_limit);
+  if (stop && tid == 0 && !no_mma) tc5_mbar_wait(mbar_a, phase ^ 1u, spin_limit);
   // output stores in flight finish before the CTA (and its shared memory) ends
   if (tma_out && tid == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");

@@ -424,6 +424,10 @@ QC_API qc_status qc_density_matrix(const void* psi_dev, int n, qc_dtype dt, int 
     if (P) cudaFreeAsync(P, s);
     return cuda_fail(e, "density matrix weights");
   }
+  if (dt == QC_C64 && B <= 64) {  // tensor cores (rho_tc.cu)
+    cudaFreeAsync(P, s);
+    return rho_tc_c64(reinterpret_cast<const float2*>(psi_dev), n, B, P_host, reinterpret_cast<float2*>(rho_dev), s);
+  }
   const unsigned nt = (unsigned)((N + RHO_TILE - 1) / RHO_TILE);
   const dim3 grid(nt, nt);
   if (dt == QC_C128)

@@ -6,11 +6,11 @@
 // 2^{-|B|/2}.  Only additions are needed, so:
 //  - complex128 tiles run in exact 64-bit fixed point.  The tile's largest
 //    exponent fixes the binary point so that |B| doublings cannot overflow
-//    (|v| < 2^62); the conversion rounds every value to nearest at
-//    2^-51 of the tile's largest magnitude or better, the butterflies are
-//    exact integer additions, and the result is rounded once, to nearest,
-//    back to binary64 (odd |B|: one fixed-point product by 1/sqrt 2 before
-//    that).  No FP64 instruction is issued; GB300's FP64 pipe would
+//    (|v| < 2^62); the conversion rounds every value to nearest (half away
+//    from zero) at 2^-51 of the tile's largest magnitude or better, the
+//    butterflies are exact integer additions, and the result is rounded
+//    once, to nearest, back to binary64 (odd |B|: one fixed-point product
+//    by 1/sqrt 2 before that).  No FP64 instruction is issued; GB300's FP64 pipe would
 //    otherwise bound the pass, and double-float butterflies cost about 20
 //    FP32 operations per addition.
 //  - complex64 tiles run in FP32.
@@ -47,8 +47,9 @@ __device__ __forceinline__ uint64_t wht_global(uint64_t e, uint64_t T, int lo, i
 
 // ---------------------------------------------------------- complex128 --
 // binary64 -> fixed point round(x 2^(1075 - G)) for the tile's G (see
-// k_wht_c128), rounding to nearest even.  x = m 2^(ex - 1075), so the value
-// is m 2^(ex - G).
+// k_wht_c128), rounding half away from zero (symmetric, so unbiased; exact
+// values need no rounding at all).  x = m 2^(ex - 1075), so the value is
+// m 2^(ex - G).
 __device__ __forceinline__ long long d2fix(double x, int G) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((b >> 52) & 0x7FFu);
@@ -60,23 +61,19 @@ __device__ __forceinline__ long long d2fix(double x, int G) {
     v = m << sh;  // sh <= 9 - |B|: no overflow
   } else {
     const int r = -sh;
-    if (r > 54) return 0;
-    v = (m + (1ull << (r - 1)) - 1ull + ((m >> r) & 1ull)) >> r;
+    v = r > 54 ? 0ull : ((m >> (r - 1)) + 1ull) >> 1;
   }
   return (b >> 63) ? -(long long)v : (long long)v;
 }
 
-// fixed point v 2^-F -> binary64, rounded to nearest even (results below
-// 2^-1022 flush to zero)
+// fixed point v 2^-F -> binary64, rounded half away from zero (results
+// below 2^-1022 flush to zero)
 __device__ __forceinline__ double fix2d(long long v, int F) {
   if (v == 0) return 0.0;
   const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
   const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
   const int lz = __clzll((long long)a);
-  const unsigned long long mant = a << lz;  // bit 63 set
-  unsigned long long keep = mant >> 11;
-  const unsigned long long rem = mant & 0x7FFull;
-  keep += (rem > 0x400ull || (rem == 0x400ull && (keep & 1ull))) ? 1ull : 0ull;
+  unsigned long long keep = (((a << lz) >> 10) + 1ull) >> 1;  // 53 bits, rounded
   int e = 63 - lz - F + 1023;
   if (keep >> 53) {
     keep >>= 1;

@@ -52,6 +52,31 @@ def test_density_matrix_vs_oracle(qc, dt, n, B):
     assert np.max(np.abs(got - got.conj().T)) <= TOL[dt]
 
 
+@pytest.mark.parametrize("n,B", [(1, 1), (4, 2), (8, 33), (11, 64), (12, 7)])
+def test_density_matrix_tensor_cores_c64(qc, n, B):
+    # complex64 rho on the tensor cores: 128 x 32 tiles over K = 2B (one or
+    # two 64-wide chunks, padded), bf16 digit slices with exact leading sums.
+    # Against the oracle on the same complex64 inputs: FP32-class error
+    # relative to the largest entry, Hermitian to that level, and a trace
+    # with no drift (a truncating accumulation would shrink it)
+    import torch
+    g = W.rng(n * 31 + B)
+    states = np.stack([W.random_state(g, n) for _ in range(B)])
+    P = g.random(B)
+    P /= P.sum()
+    t = batch(qc, states, 1)
+    N = 1 << n
+    rho = torch.empty(N * N, dtype=torch.complex64, device="cuda")
+    qc.qc_density_matrix(t.data_ptr(), n, 1, B, P, rho.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = rho.cpu().numpy().astype(np.complex128).reshape(N, N)
+    ref = D.density_matrix(as_dt(states, 1), P)
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)) <= 3e-7 * scale
+    assert np.max(np.abs(got - got.conj().T)) <= 3e-7 * scale
+    assert abs(np.trace(got).real - np.trace(ref).real) <= 1e-6
+
+
 @pytest.mark.parametrize("dt", [0, 1])
 @pytest.mark.parametrize("n,B", [(1, 2), (6, 7), (10, 16), (12, 64)])
 def test_mixed_spectrum_vs_oracle(qc, dt, n, B):
