@@ -233,6 +233,35 @@ FF_HD ff ff_dot2m(ff a, ff b, ff c, ff d) {
 // a*b + c*d
 FF_HD ff ff_dot2p(ff a, ff b, ff c, ff d) { return ff_dot2m(a, b, ff_neg(c), d); }
 
+// a*b + c*d + e*f + g*h with one closing renormalisation: the high
+// products' rounding errors are exact (fma), their sum is carried by
+// two-sums, and the low-part cross terms and the errors are summed in the
+// low word.
+FF_HD ff ff_dot4(ff a, ff b, ff c, ff d, ff e, ff f, ff g, ff h) {
+  const float p1 = ff_mul_rn(a.hi, b.hi), p2 = ff_mul_rn(c.hi, d.hi);
+  const float p3 = ff_mul_rn(e.hi, f.hi), p4 = ff_mul_rn(g.hi, h.hi);
+  float t = ff_fma(a.hi, b.hi, -p1);
+  t = ff_add_rn(t, ff_fma(c.hi, d.hi, -p2));
+  t = ff_add_rn(t, ff_fma(e.hi, f.hi, -p3));
+  t = ff_add_rn(t, ff_fma(g.hi, h.hi, -p4));
+  float s, e1, e2, e3;
+  two_sum(p1, p2, s, e1);
+  two_sum(s, p3, s, e2);
+  two_sum(s, p4, s, e3);
+  t = ff_add_rn(t, ff_add_rn(e1, ff_add_rn(e2, e3)));
+  t = ff_fma(a.hi, b.lo, t);
+  t = ff_fma(a.lo, b.hi, t);
+  t = ff_fma(c.hi, d.lo, t);
+  t = ff_fma(c.lo, d.hi, t);
+  t = ff_fma(e.hi, f.lo, t);
+  t = ff_fma(e.lo, f.hi, t);
+  t = ff_fma(g.hi, h.lo, t);
+  t = ff_fma(g.lo, h.hi, t);
+  float hh, ll;
+  fast_two_sum(s, t, hh, ll);
+  return ff_make(hh, ll);
+}
+
 FF_HD ffc ffc_make(ff re, ff im) {
   ffc z;
   z.re = re;

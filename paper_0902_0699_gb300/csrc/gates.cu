@@ -5,7 +5,8 @@
 // grid-stride loops sized to the resident blocks.
 //
 // complex64 operators compute in FP32.  complex128 operators with real
-// arithmetic (general, real, diagonal, anti-diagonal, Hadamard) compute in
+// arithmetic (general, real, diagonal, anti-diagonal, Hadamard) split their
+// products between the FP64 pipe (a few operations per pair) and
 // double-float on the FP32 pipe (ff.cuh): on GB300 the FP64 pipe does 0.5
 // Top/s, fewer than 2.5 FP64 operations per amplitude in the time one HBM
 // pass takes at 30 qubits.  Exchanges (X, CNOT, SWAP) and the phases -1, +i,
@@ -29,9 +30,57 @@ template <> struct GateArg<double> {
   Mat2ff F;
 };
 
+// complex128 operators with products on both pipes: 4 FP64 operations per
+// pair (GB300's FP64 pipe completes about 6 per pair in the time a 30-qubit
+// read+write pass takes at 0.8 of HBM), the rest in double-float on the FP32
+// pipe.  The FP64 part is one output component (general: Re b0) or the
+// real parts (real operators) or one output (diagonal, anti-diagonal).
+__device__ __forceinline__ void apply_general_c128(const GateArg<double>& G, Cx<double>& a0, Cx<double>& a1) {
+  const Mat2<double>& U = G.U;
+  double r0 = U.m[0].re * a0.re;
+  r0 = fma(-U.m[0].im, a0.im, r0);
+  r0 = fma(U.m[1].re, a1.re, r0);
+  r0 = fma(-U.m[1].im, a1.im, r0);
+  const ff x0r = ff_from_d(a0.re), x0i = ff_from_d(a0.im), x1r = ff_from_d(a1.re), x1i = ff_from_d(a1.im);
+  const Mat2ff& F = G.F;
+  const ff i0 = ff_dot4(F.m[0].re, x0i, F.m[0].im, x0r, F.m[1].re, x1i, F.m[1].im, x1r);
+  const ff r1 = ff_dot4(F.m[2].re, x0r, ff_neg(F.m[2].im), x0i, F.m[3].re, x1r, ff_neg(F.m[3].im), x1i);
+  const ff i1 = ff_dot4(F.m[2].re, x0i, F.m[2].im, x0r, F.m[3].re, x1i, F.m[3].im, x1r);
+  a0 = cmake<double>(r0, ff_to_d(i0));
+  a1 = cmake<double>(ff_to_d(r1), ff_to_d(i1));
+}
+__device__ __forceinline__ void apply_real_c128(const GateArg<double>& G, Cx<double>& a0, Cx<double>& a1) {
+  const double u00 = G.U.m[0].re, u01 = G.U.m[1].re, u10 = G.U.m[2].re, u11 = G.U.m[3].re;
+  const double r0 = fma(u01, a1.re, u00 * a0.re), r1 = fma(u11, a1.re, u10 * a0.re);
+  const ff x0i = ff_from_d(a0.im), x1i = ff_from_d(a1.im);
+  const Mat2ff& F = G.F;
+  const ff i0 = ff_dot2p(F.m[0].re, x0i, F.m[1].re, x1i), i1 = ff_dot2p(F.m[2].re, x0i, F.m[3].re, x1i);
+  a0 = cmake<double>(r0, ff_to_d(i0));
+  a1 = cmake<double>(r1, ff_to_d(i1));
+}
+// one complex product in FP64 (u a), the other in double-float
+__device__ __forceinline__ Cx<double> cmul_fp64(Cx<double> u, Cx<double> a) {
+  return cmake<double>(fma(-u.im, a.im, u.re * a.re), fma(u.im, a.re, u.re * a.im));
+}
+__device__ __forceinline__ Cx<double> cmul_ffd(const ffc& u, Cx<double> a) {
+  const ffc z = ffc_mul(u, ffc_from_d(a.re, a.im));
+  return cmake<double>(ff_to_d(z.re), ff_to_d(z.im));
+}
+
 template <typename R, int KIND>
 __device__ __forceinline__ void apply_gate(const GateArg<R>& G, Cx<R>& a0, Cx<R>& a1) {
-  if constexpr (sizeof(R) == 8 && KIND == MK_HAD) {
+  if constexpr (sizeof(R) == 8 && KIND == MK_GENERAL) {
+    apply_general_c128(G, a0, a1);
+  } else if constexpr (sizeof(R) == 8 && KIND == MK_REAL) {
+    apply_real_c128(G, a0, a1);
+  } else if constexpr (sizeof(R) == 8 && KIND == MK_DIAG) {
+    a0 = cmul_fp64(G.U.m[0], a0);
+    a1 = cmul_ffd(G.F.m[3], a1);
+  } else if constexpr (sizeof(R) == 8 && KIND == MK_ANTI) {
+    const Cx<double> b0 = cmul_fp64(G.U.m[1], a1);
+    a1 = cmul_ffd(G.F.m[2], a0);
+    a0 = b0;
+  } else if constexpr (sizeof(R) == 8 && KIND == MK_HAD) {
     // both pipes: real parts in FP64 (1.5 FP64 operations per amplitude),
     // imaginary parts in double-float on the FP32 pipe
     const double h = G.U.m[0].re;
@@ -66,9 +115,19 @@ __device__ __forceinline__ uint64_t pair_base(uint64_t p, int p0, int p1, uint64
 // of four blocks per SM is declared: with it the complex128 exchange (CNOT)
 // streams at 0.93-0.95 of copy bandwidth on GB300, without it at 0.82-0.86
 // (same register count, different schedule).
+// Register budget: four blocks per SM (64 registers), except the complex128
+// kinds whose products are split between FP64 and double-float (general,
+// diagonal, anti-diagonal), which declare three (85 registers) -- the
+// launcher runs three per SM for complex128 anyway, and under 64 registers
+// they spill 100+ bytes.
+template <typename R, int KIND>
+struct PairBlocks {
+  static constexpr int value =
+      (sizeof(R) == 8 && (KIND == MK_GENERAL || KIND == MK_DIAG || KIND == MK_ANTI)) ? 3 : 4;
+};
 template <typename R, int KIND, int NINS>
-__global__ void __launch_bounds__(256, 4) k_pairs(typename CT<R>::V2* __restrict__ s, uint64_t npairs, int p0,
-                                               int p1, uint64_t setm, int t, GateArg<R> G) {
+__global__ void __launch_bounds__(256, PairBlocks<R, KIND>::value)
+    k_pairs(typename CT<R>::V2* __restrict__ s, uint64_t npairs, int p0, int p1, uint64_t setm, int t, GateArg<R> G) {
   using IO = AmpIO<R>;
   constexpr bool B1 = touches_bit1_only(KIND);
   constexpr int UNR = sizeof(R) == 8 ? 4 : 2;

@@ -90,6 +90,14 @@ int main() {
     if (err > std::ldexp(std::fabs(c) * sc, -43)) return fail("mul over sub_u", a, c, err);
     err = std::fabs(val(ff_dot2m(C, D0, D, S0)) - (pm - (long double)d * ((long double)a + b)));
     if (err > std::ldexp((std::fabs(c) + std::fabs(d)) * sc, -43)) return fail("dot2m over add_u", a, c, err);
+    // the four-term dot of the general one-qubit operator (one renormalisation)
+    const long double r4 = (long double)a * b + (long double)c * d + (long double)b * c - (long double)a * d;
+    err = std::fabs(val(ff_dot4(A, B, C, D, B, C, ff_neg(A), D)) - r4);
+    const long double s4 = std::fabs(a * b) + std::fabs(c * d) + std::fabs(b * c) + std::fabs(a * d);
+    if (err > std::ldexp(s4, -43)) return fail("dot4", a, c, err);  // four products, ~12 low-word roundings
+    const ff R4 = ff_dot4(A, B, C, D, B, C, ff_neg(A), D);
+    if (std::fabs(R4.lo) > std::fabs(R4.hi) * std::ldexp(1.0, -23) + std::ldexp(s4, -70))
+      return fail("dot4 norm", a, c, R4.lo);
   }
   printf("ok\n");
   return 0;
