@@ -423,69 +423,64 @@ def gpu_numa_node(dev):
 
 
 class HostBuffer:
-    """Page-locked host memory for the end-to-end copies, placed on the GPU's
-    local NUMA node: an anonymous mapping bound to that node (mbind), first
-    touched there, then registered with CUDA.  Falls back to torch's pinned
-    allocator (placement left to the kernel) if any step is unavailable."""
+    """Page-locked host memory for the end-to-end copies, allocated by
+    cudaHostAlloc (torch's pinned allocator) from a thread bound to the CPUs
+    of the GPU's NUMA node, so that the pages are placed next to the GPU.
+    (An anonymous mapping bound with mbind and registered with
+    cudaHostRegister was tried as well: on the GB300 machines its host->device
+    rate dropped to about 10 GB/s for good once two copies had overlapped on
+    it, while cudaHostAlloc memory keeps about 210 GB/s.)"""
 
     def __init__(self, nbytes, node):
-        import ctypes
-        import mmap
-        import platform
         import torch
-        self.nbytes, self.node, self.buf, self.addr, self.registered = nbytes, node, None, None, False
-        self.method = "torch pinned allocator (default placement)"
-        sysno = {"aarch64": 235, "x86_64": 237}.get(platform.machine())
-        if node is not None and sysno is not None and node < 64:
+        self.nbytes, self.node = nbytes, node
+        cpus = None
+        if node is not None:
             try:
-                libc = ctypes.CDLL(None, use_errno=True)
-                buf = mmap.mmap(-1, nbytes, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
-                addr = ctypes.addressof(ctypes.c_char.from_buffer(buf))
-                mask = ctypes.c_ulong(1 << node)
-                rc = libc.syscall(ctypes.c_long(sysno), ctypes.c_void_p(addr), ctypes.c_ulong(nbytes), ctypes.c_int(2),
-                                  ctypes.byref(mask), ctypes.c_ulong(65), ctypes.c_uint(0))  # MPOL_BIND
-                if rc != 0:
-                    raise OSError(ctypes.get_errno(), "mbind")
-                # first touch (pages land on the bound node), in parallel chunks
-                chunk = 1 << 28
-                from concurrent.futures import ThreadPoolExecutor
-                with ThreadPoolExecutor(max_workers=8) as ex:
-                    list(ex.map(lambda o: libc.memset(ctypes.c_void_p(addr + o), 0,
-                                                      ctypes.c_size_t(min(chunk, nbytes - o))),
-                                range(0, nbytes, chunk)))
-                err = torch.cuda.cudart().cudaHostRegister(addr, nbytes, 0)
-                if int(err) != 0:
-                    raise OSError(int(err), "cudaHostRegister")
-                self.buf, self.addr, self.registered = buf, addr, True
-                self.method = "mbind(MPOL_BIND) to node %d + first touch + cudaHostRegister" % node
-            except Exception as e:
-                self.method = "torch pinned allocator (default placement; node binding failed: %r)" % (e,)
-                self.buf = None
+                cpus = parse_cpulist(open("/sys/devices/system/node/node%d/cpulist" % node).read())
+            except Exception:
+                cpus = None
+        old = os.sched_getaffinity(0)
+        bound = False
+        if cpus and cpus & old:
+            os.sched_setaffinity(0, cpus & old)
+            bound = True
+        try:
+            self.t = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+            self.t.zero_()  # first touch from the bound thread (pages are placed at pinning already)
+        finally:
+            if bound:
+                os.sched_setaffinity(0, old)
+        self.method = ("cudaHostAlloc from a thread bound to node %d's CPUs" % node) if bound else \
+            "cudaHostAlloc (NUMA node unknown: default placement)"
 
     def tensor(self, dtype, numel):
-        import torch
-        if self.buf is not None:
-            return torch.frombuffer(self.buf, dtype=torch.uint8, count=self.nbytes).view(dtype)[:numel]
-        return torch.zeros(numel, dtype=dtype, pin_memory=True)
+        return self.t.view(dtype)[:numel]
 
     def close(self):
-        import torch
-        if self.registered:
-            torch.cuda.cudart().cudaHostUnregister(self.addr)
-            self.registered = False
+        self.t = None
+
+
+def parse_cpulist(txt):
+    cpus = set()
+    for part in txt.strip().split(","):
+        if "-" in part:
+            lo, hi = part.split("-")
+            cpus.update(range(int(lo), int(hi) + 1))
+        elif part:
+            cpus.add(int(part))
+    return cpus
 
 
 def run_e2e(args, st, step_fn, ops_per_step, N):
     """Same workload through the public API with the state in pinned host
     memory: every step copies its input state (|0..0>) host->device, runs
     the step and copies its final state and samples back.  Two device
-    states are used in turn.  The upload runs on the compute stream right
-    before its step, and the download of step i-1 is issued after it on its
-    own stream, where it overlaps step i: on this host link a host->device
-    copy that runs at the same time as a device->host copy crawls at 8-17
-    GB/s, against about 210 GB/s alone (the device->host copy keeps about
-    190 GB/s next to compute).  The timed region holds every step's
-    copies."""
+    states are used in turn.  All copies go through one copy stream, one
+    at a time, and overlap the other state's step: on the GB300 machines' host
+    link a single copy runs at about 210 GB/s (H2D) or 193 GB/s (D2H), while
+    two copies at the same time collapse to about 10 GB/s.  The timed
+    region holds every step's copies."""
     import numpy as np
     import torch
     import paper_0902_0699_gb300 as qc
@@ -501,48 +496,44 @@ def run_e2e(args, st, step_fn, ops_per_step, N):
     comp = torch.cuda.current_stream()
     st2 = qc.State(n, st.dt)
     states = [st, st2]
-    s_out = torch.cuda.Stream()
+    s_copy = torch.cuda.Stream()
+    ev_in = [torch.cuda.Event(), torch.cuda.Event()]
     ev_done = [torch.cuda.Event(), torch.cuda.Event()]
-    ev_free = [torch.cuda.Event(), torch.cuda.Event()]
-    issued_free = [False, False]
 
-    copies = {"h2d": [], "d2h": []}  # (start, end) events per copy, on the copy's own stream
+    copies = {"h2d": [], "d2h": []}  # (start, end) events per copy, on the copy stream
 
-    def timed_copy(kind, stream, fn):
+    def timed_copy(kind, fn):
         a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
+        a.record(s_copy)
         fn()
-        z.record(stream)
+        z.record(s_copy)
         copies[kind].append((a, z))
 
-    def download(b):
-        with torch.cuda.stream(s_out):
-            s_out.wait_event(ev_done[b])
-            timed_copy("d2h", s_out, lambda: host_out.copy_(states[b].tensor, non_blocking=True))
-            host_shots.copy_(shots_of[b], non_blocking=True)
-            ev_free[b].record(s_out)
-        issued_free[b] = True
-
-    shots_of = [None, None]
+    def upload(b):
+        with torch.cuda.stream(s_copy):
+            timed_copy("h2d", lambda: states[b].tensor.copy_(host_in, non_blocking=True))
+            ev_in[b].record(s_copy)
 
     def pipeline(k):
-        # upload i (compute stream, alone on the host link), then download
-        # i-1 (its own stream, overlapping step i), then step i
+        # copy stream: upload 0, upload 1, then per step i: download i, upload
+        # i + 2 (into the state download i has just freed); all of it
+        # overlaps the other state's step on the compute stream
+        upload(0)
+        if k > 1:
+            upload(1)
         for i in range(k):
             b = i % 2
-            if issued_free[b]:
-                comp.wait_event(ev_free[b])  # the previous download of this buffer is done
-            timed_copy("h2d", comp, lambda: states[b].tensor.copy_(host_in, non_blocking=True))
-            ev_up.record(comp)
-            if i > 0:
-                s_out.wait_event(ev_up)
-                download(1 - b)
+            comp.wait_event(ev_in[b])
             qc.qc_state_invalidate(states[b].h)
-            shots_of[b] = step_fn(None, None, states[b])
+            shots = step_fn(None, None, states[b])
             ev_done[b].record(comp)
-        download((k - 1) % 2)
-
-    ev_up = torch.cuda.Event()
+            with torch.cuda.stream(s_copy):
+                s_copy.wait_event(ev_done[b])
+                timed_copy("d2h", lambda: host_out.copy_(states[b].tensor, non_blocking=True))
+                host_shots.copy_(shots, non_blocking=True)
+                shots.record_stream(s_copy)
+            if i + 2 < k:
+                upload(b)
     pipeline(2)  # warm-up
     torch.cuda.synchronize()
     copies["h2d"].clear()
@@ -564,9 +555,8 @@ def run_e2e(args, st, step_fn, ops_per_step, N):
     return {"value": wsum / (tmax / 1e3), "unit": UNIT, "h2d_bytes_per_step": N * amp,
             "d2h_bytes_per_step": N * amp + 8 * 1000, "ms_per_step": tmax / args.steps,
             "h2d_GBps_seen": rate["h2d"], "d2h_GBps_seen": rate["d2h"], "host_buffers": pinned,
-            "note": "host |0..0> in pinned memory -> device on the compute stream before each step (never next to "
-                    "a download), full step, final state and samples -> host on their own stream (overlapping the "
-                    "next step); two device states in turn"}
+            "note": "host |0..0> in pinned memory -> device, full step, final state and samples -> host; two "
+                    "device states in turn; one copy stream (one copy at a time) overlapping the other state's step"}
 
 
 # ---------------------------------------------------------------- extras ----
@@ -1049,9 +1039,10 @@ def extra_f3(n=14, B=64):
 
 def extra_dense(n=30, reps=5):
     """The dense k-qubit block on the tensor cores: a random 32 x 32 unitary
-    on 5 qubits of an n-qubit complex64 state (tcgen05, 3xTF32), on the
-    lowest five qubits and on five scattered ones.  Bound: HBM (2S per
-    launch); the tensor work is 3 x 256 flops per amplitude."""
+    on 5 qubits of an n-qubit complex64 state (tcgen05 kind::f16, bf16 digit
+    slices), on the lowest five qubits, on qubits 5..9 and on five scattered
+    ones.  Bound: HBM (2S per launch); the tensor work executed is 8 digit
+    products x 256 flops per amplitude."""
     import json as _json
     import numpy as np
     import torch
@@ -1062,7 +1053,7 @@ def extra_dense(n=30, reps=5):
     peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
-    tf32 = peaks.get("bf16_tflops", 1900.0) * 1.1 / 2.25  # nominal TF32 / bf16 ratio
+    bf16 = peaks.get("bf16_tflops", 1900.0)
     res = {}
     s = qc.State(n, qc.QC_C64)
     s.uniform()
@@ -1079,12 +1070,12 @@ def extra_dense(n=30, reps=5):
         ms = a.elapsed_time(b) / reps
         S = (1 << n) * 8
         gbs = 2 * S / ms / 1e6
-        tflops = 3 * 256 * (1 << n) / ms / 1e9
+        tflops = 8 * 256 * (1 << n) / ms / 1e9
         res[name] = {"qubits": qs, "ms": ms, "GB/s": gbs, "frac_of_measured_hbm": gbs / hbm,
-                     "tensor_TFLOP/s (3xTF32 executed)": tflops, "frac_of_tf32_peak": tflops / tf32}
+                     "tensor_TFLOP/s (bf16 executed)": tflops, "frac_of_bf16_peak": tflops / bf16}
     s.close()
-    res["note"] = ("per launch: %d-qubit complex64, one tile of 128 groups per MMA round (tcgen05 kind::tf32, "
-                   "M128 N64 K64 x 3 terms); tf32 peak = measured bf16 x 1.1/2.25 = %.0f TFLOP/s" % (n, tf32))
+    res["note"] = ("per launch: %d-qubit complex64, one tile of 128 groups per MMA round (tcgen05 kind::f16 bf16, "
+                   "M128 N64 K64 x 8 digit products = 32 MMAs of K16); bf16 peak = measured %.0f TFLOP/s" % (n, bf16))
     return res
 
 

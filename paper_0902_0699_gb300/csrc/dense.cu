@@ -10,10 +10,14 @@
 //   W[2l][2j+1] = Im U[j][l], W[2l+1][2j+1] = Re U[j][l]   (K = N = 2^{k+1}).
 // At k = 5 that is 256 flops per amplitude, more than the FP32 pipe can
 // feed at HBM speed, so complex64 k = 5 runs on the 5th-generation tensor
-// cores (tcgen05, TF32 inputs, FP32 accumulator in tensor memory) with the
-// operands split hi + lo ("3xTF32": A_hi B_hi + A_hi B_lo + A_lo B_hi), which
-// keeps FP32-level accuracy.  Other k and complex128 run on CUDA cores
-// (complex128 in double-float).
+// cores (tcgen05 kind::f16 with bf16 inputs, FP32 accumulators in tensor
+// memory).  Each operand is scaled by a power of two and cut into three
+// integer-valued bf16 digits, x = 2^-s (a0 + 2^-8 a1 + 2^-16 a2); the eight
+// digit products down to weight 2^-16 go to three accumulators, the first
+// two of which sum integers exactly, so no product or partial sum is
+// rounded toward zero and the result keeps FP32-level accuracy without
+// drift.  Other k and complex128 run on CUDA cores (complex128 in
+// double-float).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
