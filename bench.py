@@ -380,8 +380,8 @@ def error_vs_closed_form(st, n, marked, k, seed=7, samples=4096):
 def qft_bytes(n, amp):
     """Algorithmic bytes of the QFT as built: one read+write pass per tile
     group plus the bit-reversal pass."""
-    # lowest group up to BOT qubits, the others up to K (csrc/tile.cu TileCfg)
-    BOT, K = (12, 9) if amp == 16 else (13, 10)
+    # lowest group up to BOT qubits, the others up to K (the QFT group plans of csrc/tile.cu)
+    BOT, K = (12, 9) if amp == 16 else (13, 9)
     g0 = min(n, BOT)
     rest = n - g0
     passes = 1 + (-(-rest // K) if rest > 0 else 0)

@@ -238,13 +238,211 @@ __device__ __forceinline__ void qft_levels_regs(typename TA<R>::E* sm, int NE, i
   }
 }
 
-// QREG: complex64 QFT programs apply four levels at a time in registers
-// (127 registers a thread, one CTA per SM); every other program keeps two
-// CTAs per SM (64 registers), which small tiles need to hide latency.
+// L_j(y) = e^{2 pi i y / 2^{j+1}}, y < 2^j, from the ladder table (levels
+// below kl) or, for level kl, from level kl - 1 and the extra entry.
+template <typename R>
+__device__ __forceinline__ typename TA<R>::E ladder_at(const typename TA<R>::E* LAD, int kl, int j, int y) {
+  if (j < kl) return LAD[(1 << j) - 1 + y];
+  const typename TA<R>::E m = LAD[(1 << (j - 1)) - 1 + (y >> 1)];
+  return (y & 1) ? TA<R>::mul(m, LAD[(1 << kl) - 1]) : m;
+}
+
+// Shared tables of a pass: the ladders (QFT programs) and the twiddle
+// remainder tables TWA, TWB (QFT programs with a twiddle).
+template <typename R>
+__device__ __forceinline__ void tile_tables(const TileProg<R>& P, typename TA<R>::E* LAD, typename TA<R>::E* TWA,
+                                            typename TA<R>::E* TWB, int kl) {
+  using A = TA<R>;
+  const int k = P.k, hi = P.lo + P.k - 1;
+  if (!P.qft) return;
+  // ladder tables, one per level: LAD[2^j - 1 + x] = e^{2 pi i x / 2^{j+1}}
+  for (int a = threadIdx.x; a < (1 << kl) - 1; a += blockDim.x) {
+    const int j = 31 - __clz(a + 1);
+    LAD[a] = A::root((uint64_t)(a + 1 - (1 << j)), j + 1);
+  }
+  if (k > kl && threadIdx.x == 0) LAD[(1 << kl) - 1] = A::root(1, k);  // e^{2 pi i / 2^k}
+  // twiddle remainder: Omega_{hi+1}^x = TWA[x & 127] * TWB[x >> 7], x < 2^{c+k}
+  if (P.twiddle)
+    for (int i = threadIdx.x; i < TS_TWA + TS_TWB; i += blockDim.x) {
+      if (i < TS_TWA) TWA[i] = A::root((uint64_t)i, hi + 1);
+      else TWB[i - TS_TWA] = A::root((uint64_t)(i - TS_TWA) << 7, hi + 1);
+    }
+}
+
+// V[f] = 2^{-p/2} Omega_{hi+1}^{Ltile f} for tile T (Ltile = the tile's bits
+// between c and lo).
+template <typename R>
+__device__ __forceinline__ void tile_twiddle_v(const TileProg<R>& P, uint64_t T, typename TA<R>::E* V,
+                                               const typename CT<R>::V2* __restrict__ tlo,
+                                               const typename CT<R>::V2* __restrict__ thi, typename TA<R>::S sc) {
+  const int lo = P.lo, k = P.k, c = P.c, hi = lo + k - 1;
+  const uint64_t Lt = (T & ((1ull << (lo - c)) - 1ull)) << c;
+  for (int f = threadIdx.x; f < (1 << k); f += blockDim.x) {
+    const uint64_t r = (Lt * (uint64_t)f) & ((2ull << hi) - 1ull);
+    V[f] = TA<R>::scale_by(omega<R>(tlo, thi, r << (P.n - hi - 1), P.nl), sc);
+  }
+}
+
+// The program's operators on the staged tile sm (2^{k+c} elements), with a
+// barrier after each shared-memory round trip.  QREG: four descending QFT
+// levels at a time in registers.
 template <typename R, bool QREG>
-__global__ void __launch_bounds__(512, QREG ? 1 : 2) k_tile(typename CT<R>::V2* __restrict__ s, uint64_t ntiles,
-                                              const TileProg<R> P, const typename CT<R>::V2* __restrict__ tlo,
-                                              const typename CT<R>::V2* __restrict__ thi) {
+__device__ __forceinline__ void tile_ops(typename TA<R>::E* sm, const TileProg<R>& P, const typename TA<R>::E* LAD,
+                                         int kl) {
+  using A = TA<R>;
+  using E = typename A::E;
+  const int c = P.c;
+  const int NE = 1 << (P.k + c);
+  for (int o = 0; o < P.nops; ++o) {
+    const int b = c + P.q[o];
+    const int kind = P.kind[o];
+    // four descending QFT levels in registers (complex64: the passes are
+    // bound by shared-memory traffic)
+    if (QREG && kind == TOP_QFTLEVEL && o + 3 < P.nops && P.kind[o + 1] == kind &&
+        P.kind[o + 2] == kind && P.kind[o + 3] == kind && P.q[o + 1] == P.q[o] - 1 &&
+        P.q[o + 2] == P.q[o] - 2 && P.q[o + 3] == P.q[o] - 3) {
+      qft_levels_regs<R, 4>(sm, NE, c, P.q[o], LAD);
+      __syncthreads();
+      o += 3;
+      continue;
+    }
+    // two butterfly levels on neighbouring qubits: one shared-memory round
+    // trip (radix 4).  QFT levels come in descending order j, j-1; plain
+    // Hadamard butterflies commute, so any neighbouring pair qualifies.
+    if (kind != TOP_U2 && o + 1 < P.nops && P.kind[o + 1] == kind &&
+        (P.q[o + 1] == P.q[o] - 1 || (kind == TOP_HB && P.q[o + 1] == P.q[o] + 1))) {
+      const int jh = max(P.q[o], P.q[o + 1]), jl = jh - 1;  // levels jh then jl
+      const int bh = c + jh, bl = c + jl;
+      const bool lad = (kind == TOP_QFTLEVEL);
+      for (int p = threadIdx.x; p < (NE >> 2); p += blockDim.x) {
+        const int e00 = (int)insert0(insert0((uint64_t)p, bl), bh);
+        const int e01 = e00 | (1 << bl), e10 = e00 | (1 << bh), e11 = e01 | (1 << bh);
+        const E a00 = sm[e00], a01 = sm[e01], a10 = sm[e10], a11 = sm[e11];
+        // level jh on bit bh: pairs (e00, e10), (e01, e11)
+        const E s0 = A::add_u(a00, a10), d0 = A::sub_u(a00, a10);
+        const E s1 = A::add_u(a01, a11), d1 = A::sub_u(a01, a11);
+        E t0, u0, t1, u1;
+        if (lad) {
+          // With L(y) = e^{2 pi i y / 2^{jh+1}} and x = group bits below jl:
+          // level jh multiplies d0 by L(x) and d1 by L(x + 2^jl) = i L(x);
+          // level jl multiplies its bit-1 outputs by L(2x).  So
+          //   t0 = s0 + s1,  u0 = L(2x) (s0 - s1),
+          //   t1 = L(x) (d0 + i d1),  u1 = L(3x) (d0 - i d1):
+          // three multiplications per four amplitudes instead of four.
+          const int x = (e00 >> c) & ((1 << jl) - 1);
+          const E id1 = A::times_i(d1);
+          t0 = A::add(s0, s1);
+          // the products renormalise u0, t1, u1; without one (x = 0) the
+          // closing fast two-sum does
+          u0 = A::sub_u(s0, s1);
+          t1 = A::add_u(d0, id1);
+          u1 = A::sub_u(d0, id1);
+          if (x) {
+            u0 = A::mul(ladder_at<R>(LAD, kl, jh, 2 * x), u0);
+            t1 = A::mul(ladder_at<R>(LAD, kl, jh, x), t1);
+            const int x3 = 3 * x;  // < 1.5 2^jh; L(y + 2^jh) = -L(y)
+            u1 = A::mul(ladder_at<R>(LAD, kl, jh, x3 & ((1 << jh) - 1)), u1);
+            if (x3 >> jh) u1 = A::neg(u1);
+          } else {
+            u0 = A::norm(u0);
+            t1 = A::norm(t1);
+            u1 = A::norm(u1);
+          }
+        } else {  // plain butterflies on both bits
+          t0 = A::add(s0, s1);
+          u0 = A::sub(s0, s1);
+          t1 = A::add(d0, d1);
+          u1 = A::sub(d0, d1);
+        }
+        sm[e00] = t0;
+        sm[e01] = u0;
+        sm[e10] = t1;
+        sm[e11] = u1;
+      }
+      __syncthreads();
+      ++o;
+      continue;
+    }
+    if (kind == TOP_U2) {
+      const int mk = P.mk[o];
+      for (int p = threadIdx.x; p < (NE >> 1); p += blockDim.x) {
+        const int e0 = (int)insert0((uint64_t)p, b), e1 = e0 | (1 << b);
+        E a0 = sm[e0], a1 = sm[e1];
+        A::u2(mk, P.U[o], a0, a1);
+        sm[e0] = a0;
+        sm[e1] = a1;
+      }
+    } else {
+      // unnormalised butterfly (a0 + a1, a0 - a1); for a QFT level the
+      // bit-1 half then takes the ladder phase e^{2 pi i x / 2^{j+1}}
+      // = omega_k^{x 2^{k-j-1}}, x = group bits below group qubit j
+      const int j = P.q[o];
+      const bool lad = (kind == TOP_QFTLEVEL);
+      for (int p = threadIdx.x; p < (NE >> 1); p += blockDim.x) {
+        const int e0 = (int)insert0((uint64_t)p, b), e1 = e0 | (1 << b);
+        const E a0 = sm[e0], a1 = sm[e1];
+        sm[e0] = A::add(a0, a1);
+        E d = A::sub(a0, a1);
+        if (lad) {
+          const int x = (e0 >> c) & ((1 << j) - 1);
+          if (x) d = A::mul(ladder_at<R>(LAD, kl, j, x), d);
+        }
+        sm[e1] = d;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// The tile back to the state: twiddle (which carries the 2^{-p/2} scale) or
+// the bare scale.
+template <typename R>
+__device__ __forceinline__ void tile_store(typename CT<R>::V2* __restrict__ s, uint64_t T, const typename TA<R>::E* sm,
+                                           const TileProg<R>& P, const typename TA<R>::E* V,
+                                           const typename TA<R>::E* TWA, const typename TA<R>::E* TWB,
+                                           typename TA<R>::S sc) {
+  using A = TA<R>;
+  using E = typename A::E;
+  using V2 = typename CT<R>::V2;
+  const int lo = P.lo, k = P.k, c = P.c;
+  const int NE = 1 << (k + c);
+  if (sizeof(R) == 8) {
+    for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+      E z = sm[e];
+      if (P.twiddle) {
+        const int f = (int)(__brev((unsigned)(e >> c)) >> (32 - k));
+        const int x = (e & ((1 << c) - 1)) * f;  // < 2^{c+k}
+        z = A::mul(A::mul(V[f], A::mul(TWA[x & 127], TWB[x >> 7])), z);
+      } else if (P.scale_p) {
+        z = A::scale_by(z, sc);
+      }
+      s[tile_global(e, T, lo, k, c)] = A::to(z);
+    }
+  } else {
+    for (int e = 2 * threadIdx.x; e < NE; e += 2 * blockDim.x) {
+      E z0 = sm[e], z1 = sm[e + 1];
+      if (P.twiddle) {
+        // e and e+1 share the group bits (c >= 1 whenever lo > 0)
+        const int f = (int)(__brev((unsigned)(e >> c)) >> (32 - k));
+        const int x0 = (e & ((1 << c) - 1)) * f, x1 = x0 + f;
+        const E v = V[f];
+        z0 = A::mul(A::mul(v, A::mul(TWA[x0 & 127], TWB[x0 >> 7])), z0);
+        z1 = A::mul(A::mul(v, A::mul(TWA[x1 & 127], TWB[x1 >> 7])), z1);
+      } else if (P.scale_p) {
+        z0 = A::scale_by(z0, sc);
+        z1 = A::scale_by(z1, sc);
+      }
+      const V2 w0 = A::to(z0), w1 = A::to(z1);
+      *reinterpret_cast<float4*>(s + tile_global(e, T, lo, k, c)) = make_float4(w0.x, w0.y, w1.x, w1.y);
+    }
+  }
+}
+
+// Two CTAs per SM (64 registers): every layer program and the complex128 QFT.
+template <typename R>
+__global__ void __launch_bounds__(512, 2) k_tile(typename CT<R>::V2* __restrict__ s, uint64_t ntiles,
+                                                 const TileProg<R> P, const typename CT<R>::V2* __restrict__ tlo,
+                                                 const typename CT<R>::V2* __restrict__ thi) {
   using A = TA<R>;
   using E = typename A::E;
   using V2 = typename CT<R>::V2;
@@ -257,46 +455,16 @@ __global__ void __launch_bounds__(512, QREG ? 1 : 2) k_tile(typename CT<R>::V2* 
   const int kl = lad_levels<R>(k);  // levels in the table
   E* TWA = LAD + (P.qft ? lad_entries<R>(k) : 0);
   E* TWB = TWA + TS_TWA;
-  const int hi = lo + k - 1;
   const typename A::S sc = A::scale_const(P.scale_p);
-  if (P.qft) {
-    // ladder tables, one per level: LAD[2^j - 1 + x] = e^{2 pi i x / 2^{j+1}}
-    for (int a = threadIdx.x; a < (1 << kl) - 1; a += blockDim.x) {
-      const int j = 31 - __clz(a + 1);
-      LAD[a] = A::root((uint64_t)(a + 1 - (1 << j)), j + 1);
-    }
-    if (k > kl && threadIdx.x == 0) LAD[(1 << kl) - 1] = A::root(1, k);  // e^{2 pi i / 2^k}
-  }
-  // L_j(y) = e^{2 pi i y / 2^{j+1}}, y < 2^j (j <= kl: one level past the table)
-  auto ladder = [&](int j, int y) -> E {
-    if (j < kl) return LAD[(1 << j) - 1 + y];
-    const E m = LAD[(1 << (j - 1)) - 1 + (y >> 1)];
-    return (y & 1) ? A::mul(m, LAD[(1 << kl) - 1]) : m;
-  };
-  if (P.qft) {
-    // twiddle remainder: Omega_{hi+1}^x = TWA[x & 127] * TWB[x >> 7], x < 2^{c+k}
-    if (P.twiddle)
-      for (int i = threadIdx.x; i < TS_TWA + TS_TWB; i += blockDim.x) {
-        if (i < TS_TWA) TWA[i] = A::root((uint64_t)i, hi + 1);
-        else TWB[i - TS_TWA] = A::root((uint64_t)(i - TS_TWA) << 7, hi + 1);
-      }
-  }
+  tile_tables<R>(P, LAD, TWA, TWB, kl);
   for (uint64_t T = blockIdx.x; T < ntiles; T += gridDim.x) {
-    if (P.twiddle) {
-      // V[f] = 2^{-p/2} Omega_{hi+1}^{Ltile f}, Ltile = the tile's bits between c and lo
-      const uint64_t Lt = (T & ((1ull << (lo - c)) - 1ull)) << c;
-      for (int f = threadIdx.x; f < (1 << k); f += blockDim.x) {
-        const uint64_t r = (Lt * (uint64_t)f) & ((2ull << hi) - 1ull);
-        V[f] = A::scale_by(omega<R>(tlo, thi, r << (P.n - hi - 1), P.nl), sc);
-      }
-    }
+    if (P.twiddle) tile_twiddle_v<R>(P, T, V, tlo, thi, sc);
     // load: 16-byte vectors; for complex64 two neighbouring elements (c >= 1
-    // or a fully contiguous tile, so e and e+1 are neighbours in memory)
-    // several 16-byte loads in flight per thread before the first
-    // shared-memory store (the tile is read once; with one or two CTAs per SM
-    // the load phase is otherwise latency bound): four within the
-    // 64-register budget, eight at one CTA per SM.
-    constexpr int LU = QREG ? 8 : 4;
+    // or a fully contiguous tile, so e and e+1 are neighbours in memory);
+    // four 16-byte loads in flight per thread before the first shared-memory
+    // store (the tile is read once; with two CTAs per SM the load phase is
+    // otherwise latency bound)
+    constexpr int LU = 4;
     if (sizeof(R) == 8) {
       for (int e0 = threadIdx.x; e0 < NE; e0 += LU * blockDim.x) {
         V2 v[LU];
@@ -330,138 +498,188 @@ __global__ void __launch_bounds__(512, QREG ? 1 : 2) k_tile(typename CT<R>::V2* 
       }
     }
     __syncthreads();
-    for (int o = 0; o < P.nops; ++o) {
-      const int b = c + P.q[o];
-      const int kind = P.kind[o];
-      // four descending QFT levels in registers (complex64: the passes are
-      // bound by shared-memory traffic)
-      if (QREG && kind == TOP_QFTLEVEL && o + 3 < P.nops && P.kind[o + 1] == kind &&
-          P.kind[o + 2] == kind && P.kind[o + 3] == kind && P.q[o + 1] == P.q[o] - 1 &&
-          P.q[o + 2] == P.q[o] - 2 && P.q[o + 3] == P.q[o] - 3) {
-        qft_levels_regs<R, 4>(sm, NE, c, P.q[o], LAD);
-        __syncthreads();
-        o += 3;
-        continue;
-      }
-      // two butterfly levels on neighbouring qubits: one shared-memory round
-      // trip (radix 4).  QFT levels come in descending order j, j-1; plain
-      // Hadamard butterflies commute, so any neighbouring pair qualifies.
-      if (kind != TOP_U2 && o + 1 < P.nops && P.kind[o + 1] == kind &&
-          (P.q[o + 1] == P.q[o] - 1 || (kind == TOP_HB && P.q[o + 1] == P.q[o] + 1))) {
-        const int jh = max(P.q[o], P.q[o + 1]), jl = jh - 1;  // levels jh then jl
-        const int bh = c + jh, bl = c + jl;
-        const bool lad = (kind == TOP_QFTLEVEL);
-        for (int p = threadIdx.x; p < (NE >> 2); p += blockDim.x) {
-          const int e00 = (int)insert0(insert0((uint64_t)p, bl), bh);
-          const int e01 = e00 | (1 << bl), e10 = e00 | (1 << bh), e11 = e01 | (1 << bh);
-          const E a00 = sm[e00], a01 = sm[e01], a10 = sm[e10], a11 = sm[e11];
-          // level jh on bit bh: pairs (e00, e10), (e01, e11)
-          const E s0 = A::add_u(a00, a10), d0 = A::sub_u(a00, a10);
-          const E s1 = A::add_u(a01, a11), d1 = A::sub_u(a01, a11);
-          E t0, u0, t1, u1;
-          if (lad) {
-            // With L(y) = e^{2 pi i y / 2^{jh+1}} and x = group bits below jl:
-            // level jh multiplies d0 by L(x) and d1 by L(x + 2^jl) = i L(x);
-            // level jl multiplies its bit-1 outputs by L(2x).  So
-            //   t0 = s0 + s1,  u0 = L(2x) (s0 - s1),
-            //   t1 = L(x) (d0 + i d1),  u1 = L(3x) (d0 - i d1):
-            // three multiplications per four amplitudes instead of four.
-            const int x = (e00 >> c) & ((1 << jl) - 1);
-            const E id1 = A::times_i(d1);
-            t0 = A::add(s0, s1);
-            // the products renormalise u0, t1, u1; without one (x = 0) the
-            // closing fast two-sum does
-            u0 = A::sub_u(s0, s1);
-            t1 = A::add_u(d0, id1);
-            u1 = A::sub_u(d0, id1);
-            if (x) {
-              u0 = A::mul(ladder(jh, 2 * x), u0);
-              t1 = A::mul(ladder(jh, x), t1);
-              const int x3 = 3 * x;  // < 1.5 2^jh; L(y + 2^jh) = -L(y)
-              u1 = A::mul(ladder(jh, x3 & ((1 << jh) - 1)), u1);
-              if (x3 >> jh) u1 = A::neg(u1);
-            } else {
-              u0 = A::norm(u0);
-              t1 = A::norm(t1);
-              u1 = A::norm(u1);
-            }
-          } else {  // plain butterflies on both bits
-            t0 = A::add(s0, s1);
-            u0 = A::sub(s0, s1);
-            t1 = A::add(d0, d1);
-            u1 = A::sub(d0, d1);
-          }
-          sm[e00] = t0;
-          sm[e01] = u0;
-          sm[e10] = t1;
-          sm[e11] = u1;
-        }
-        __syncthreads();
-        ++o;
-        continue;
-      }
-      if (kind == TOP_U2) {
-        const int mk = P.mk[o];
-        for (int p = threadIdx.x; p < (NE >> 1); p += blockDim.x) {
-          const int e0 = (int)insert0((uint64_t)p, b), e1 = e0 | (1 << b);
-          E a0 = sm[e0], a1 = sm[e1];
-          A::u2(mk, P.U[o], a0, a1);
-          sm[e0] = a0;
-          sm[e1] = a1;
-        }
-      } else {
-        // unnormalised butterfly (a0 + a1, a0 - a1); for a QFT level the
-        // bit-1 half then takes the ladder phase e^{2 pi i x / 2^{j+1}}
-        // = omega_k^{x 2^{k-j-1}}, x = group bits below group qubit j
-        const int j = P.q[o];
-        const bool lad = (kind == TOP_QFTLEVEL);
-        for (int p = threadIdx.x; p < (NE >> 1); p += blockDim.x) {
-          const int e0 = (int)insert0((uint64_t)p, b), e1 = e0 | (1 << b);
-          const E a0 = sm[e0], a1 = sm[e1];
-          sm[e0] = A::add(a0, a1);
-          E d = A::sub(a0, a1);
-          if (lad) {
-            const int x = (e0 >> c) & ((1 << j) - 1);
-            if (x) d = A::mul(ladder(j, x), d);
-          }
-          sm[e1] = d;
-        }
-      }
-      __syncthreads();
+    tile_ops<R, false>(sm, P, LAD, kl);
+    tile_store<R>(s, T, sm, P, V, TWA, TWB, sc);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------- complex64 QFT passes --
+// One CTA per SM with two 64 KiB tile buffers: the next tile's loads
+// (cp.async, 16 bytes each) are in flight while the current tile is
+// transformed and written back.  The group's levels run in register blocks
+// of up to four levels (one shared-memory round trip each).  Within a block
+// on group qubits jlo .. jlo+QR-1, level j = jlo + lv multiplies the
+// difference of the pair with local low bits m by
+//   L_j(x) = e^{2 pi i x / 2^{j+1}},  x = m 2^jlo + xlow,
+//   L_j(x) = e^{2 pi i m / 2^{lv+1}} L_j(xlow),
+// so a thread loads one ladder entry per level (its xlow is fixed) and
+// multiplies it by constant roots of unity.  The shared tile is swizzled in
+// 16-byte units (pairs of amplitudes stay together for the 16-byte copies):
+// strided register blocks then hit at most twice the minimum number of
+// shared-memory wavefronts instead of up to 16x.
+__device__ __forceinline__ int qsw(int e) { return e ^ (((e >> 4) & 7) << 1); }
+
+__device__ __forceinline__ float2 c2mul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// e^{2 pi i m / 2^{lv+1}} for m < 2^lv, lv <= 3 (constants)
+__device__ __forceinline__ float2 qroot(int lv, int m) {
+  const float r = 0.70710678118654752f, c1 = 0.92387953251128676f, s1 = 0.38268343236508977f;
+  if (lv <= 0 || m == 0) return make_float2(1.f, 0.f);
+  if (lv == 1) return make_float2(0.f, 1.f);
+  if (lv == 2) {
+    switch (m) {
+      case 1: return make_float2(r, r);
+      case 2: return make_float2(0.f, 1.f);
+      default: return make_float2(-r, r);
     }
-    // store: twiddle (which carries the 2^{-p/2} scale) or the bare scale
-    if (sizeof(R) == 8) {
-      for (int e = threadIdx.x; e < NE; e += blockDim.x) {
-        E z = sm[e];
-        if (P.twiddle) {
-          const int f = (int)(__brev((unsigned)(e >> c)) >> (32 - k));
-          const int x = (e & ((1 << c) - 1)) * f;  // < 2^{c+k}
-          z = A::mul(A::mul(V[f], A::mul(TWA[x & 127], TWB[x >> 7])), z);
-        } else if (P.scale_p) {
-          z = A::scale_by(z, sc);
-        }
-        s[tile_global(e, T, lo, k, c)] = A::to(z);
+  }
+  switch (m) {  // lv == 3: sixteenth roots e^{2 pi i m / 16}
+    case 1: return make_float2(c1, s1);
+    case 2: return make_float2(r, r);
+    case 3: return make_float2(s1, c1);
+    case 4: return make_float2(0.f, 1.f);
+    case 5: return make_float2(-s1, c1);
+    case 6: return make_float2(-r, r);
+    default: return make_float2(-c1, s1);
+  }
+}
+
+template <int QR>
+__device__ __forceinline__ void qft_block_c64(float2* sm, int NE, int c, int jtop, const float2* LAD) {
+  constexpr int NR = 1 << QR;
+  const int jlo = jtop - QR + 1;
+  const int bl = c + jlo;
+  for (int p = threadIdx.x; p < (NE >> QR); p += blockDim.x) {
+    const int base = ((p >> bl) << (bl + QR)) | (p & ((1 << bl) - 1));
+    float2 a[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) a[i] = sm[qsw(base | (i << bl))];
+    const int xlow = (base >> c) & ((1 << jlo) - 1);
+#pragma unroll
+    for (int lv = QR - 1; lv >= 0; --lv) {
+      const int j = jlo + lv;
+      const float2 u = LAD[(1 << j) - 1 + xlow];  // L_j(xlow)
+#pragma unroll
+      for (int i = 0; i < NR; ++i) {
+        if ((i >> lv) & 1) continue;
+        const int i1 = i | (1 << lv);
+        const float2 x0 = a[i], x1 = a[i1];
+        a[i] = make_float2(x0.x + x1.x, x0.y + x1.y);
+        const int m = i & ((1 << lv) - 1);  // the factor e^{2 pi i m / 2^{lv+1}} L_j(xlow)
+        a[i1] = c2mul(make_float2(x0.x - x1.x, x0.y - x1.y), m ? c2mul(qroot(lv, m), u) : u);
       }
-    } else {
-      for (int e = 2 * threadIdx.x; e < NE; e += 2 * blockDim.x) {
-        E z0 = sm[e], z1 = sm[e + 1];
-        if (P.twiddle) {
-          // e and e+1 share the group bits (c >= 1 whenever lo > 0)
-          const int f = (int)(__brev((unsigned)(e >> c)) >> (32 - k));
-          const int x0 = (e & ((1 << c) - 1)) * f, x1 = x0 + f;
-          const E v = V[f];
-          z0 = A::mul(A::mul(v, A::mul(TWA[x0 & 127], TWB[x0 >> 7])), z0);
-          z1 = A::mul(A::mul(v, A::mul(TWA[x1 & 127], TWB[x1 >> 7])), z1);
-        } else if (P.scale_p) {
-          z0 = A::scale_by(z0, sc);
-          z1 = A::scale_by(z1, sc);
-        }
-        const V2 w0 = A::to(z0), w1 = A::to(z1);
-        *reinterpret_cast<float4*>(s + tile_global(e, T, lo, k, c)) = make_float4(w0.x, w0.y, w1.x, w1.y);
+    }
+#pragma unroll
+    for (int i = 0; i < NR; ++i) sm[qsw(base | (i << bl))] = a[i];
+  }
+}
+
+// Register blocks over levels k-1 .. 0: ceil(k/4) blocks, the larger first.
+__device__ __forceinline__ void qft_levels_c64(float2* sm, int NE, int c, int k, const float2* LAD) {
+  const int nb = (k + 3) >> 2;
+  int j = k - 1;
+  for (int b = 0; b < nb; ++b) {
+    const int qr = (j + 1 + (nb - b) - 1) / (nb - b);  // balanced, larger first
+    switch (qr) {
+      case 4: qft_block_c64<4>(sm, NE, c, j, LAD); break;
+      case 3: qft_block_c64<3>(sm, NE, c, j, LAD); break;
+      case 2: qft_block_c64<2>(sm, NE, c, j, LAD); break;
+      default: qft_block_c64<1>(sm, NE, c, j, LAD); break;
+    }
+    __syncthreads();
+    j -= qr;
+  }
+}
+
+// P holds the pass: group [lo, lo+k), c contiguous bits, twiddle = lo > 0,
+// scale_p = k.  Shared memory: two tile buffers, then (twiddle passes) the
+// per-pass table W[e] = Omega_{hi+1}^{l f} (l = e's c low bits, f = its
+// group bits reversed) and V[f] (per tile), then the ladder table.
+__global__ void __launch_bounds__(512, 1) k_qft_db_c64(float2* __restrict__ s, uint64_t ntiles, const TileProg<float> P,
+                                                       const float2* __restrict__ tlo, const float2* __restrict__ thi) {
+  using A = TA<float>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int lo = P.lo, k = P.k, c = P.c, hi = lo + k - 1;
+  const int NE = 1 << (k + c);
+  float2* buf0 = reinterpret_cast<float2*>(smraw);
+  float2* buf1 = buf0 + NE;
+  float2* W = buf1 + NE;
+  float2* V = W + (P.twiddle ? NE : 0);
+  float2* LAD = V + (P.twiddle ? (1 << k) : 0);
+  const float sc = (float)exp2(-0.5 * P.scale_p);
+  // 16-byte copies of amplitude pairs (e, e+1); successive ones of a thread
+  // are 1024 tile elements apart
+  const bool step_ok = c <= 10;
+  const uint64_t gstep = step_ok ? ((uint64_t)(1024 >> c) << lo) : 0;
+  auto issue = [&](uint64_t T, float2* dst) {
+    const int e0 = 2 * threadIdx.x;
+    uint64_t g = tile_global((uint64_t)e0, T, lo, k, c);
+    for (int e = e0; e < NE; e += 1024) {
+      if (!step_ok) g = tile_global((uint64_t)e, T, lo, k, c);
+      const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + qsw(e));
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(s + g) : "memory");
+      g += gstep;
+    }
+  };
+  uint64_t T = blockIdx.x;
+  if (T < ntiles) issue(T, buf0);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  // ladder table: LAD[2^j - 1 + x] = e^{2 pi i x / 2^{j+1}}, j < k
+  for (int a = threadIdx.x; a < (1 << k) - 1; a += blockDim.x) {
+    const int j = 31 - __clz(a + 1);
+    const A::E z = A::root((uint64_t)(a + 1 - (1 << j)), j + 1);
+    LAD[a] = make_float2(z.re, z.im);
+  }
+  if (P.twiddle)
+    for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+      const int f = (int)(__brev((unsigned)(e >> c)) >> (32 - k));
+      const A::E z = A::root((uint64_t)((e & ((1 << c) - 1)) * f), hi + 1);  // l f < 2^{c+k}
+      W[e] = make_float2(z.re, z.im);
+    }
+  for (int it = 0; T < ntiles; T += gridDim.x, ++it) {
+    float2* cur = (it & 1) ? buf1 : buf0;
+    float2* nxt = (it & 1) ? buf0 : buf1;
+    // nxt was last read by the previous tile's store, which ended at that
+    // iteration's closing barrier
+    if (T + gridDim.x < ntiles) issue(T + gridDim.x, nxt);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    if (P.twiddle) {
+      // V[f] = 2^{-k/2} Omega_{hi+1}^{Ltile f}
+      const uint64_t Lt = (T & ((1ull << (lo - c)) - 1ull)) << c;
+      for (int f = threadIdx.x; f < (1 << k); f += blockDim.x) {
+        const uint64_t r = (Lt * (uint64_t)f) & ((2ull << hi) - 1ull);
+        const A::E z = A::scale_by(omega<float>(tlo, thi, r << (P.n - hi - 1), P.nl), sc);
+        V[f] = make_float2(z.re, z.im);
       }
+    }
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this thread's copies of the current tile
+    __syncthreads();                                         // ... and everyone's; tables and V written
+    qft_levels_c64(cur, NE, c, k, LAD);
+    // store: pairs (e, e+1) share the group bits (c >= 1 whenever lo > 0)
+    const int e0 = 2 * threadIdx.x;
+    uint64_t g = tile_global((uint64_t)e0, T, lo, k, c);
+    for (int e = e0; e < NE; e += 1024) {
+      if (!step_ok) g = tile_global((uint64_t)e, T, lo, k, c);
+      float4 z = *reinterpret_cast<const float4*>(cur + qsw(e));
+      if (P.twiddle) {
+        const int f = (int)(__brev((unsigned)(e >> c)) >> (32 - k));
+        const float2 v = V[f];
+        const float4 w = *reinterpret_cast<const float4*>(W + e);
+        const float2 z0 = c2mul(c2mul(make_float2(z.x, z.y), make_float2(w.x, w.y)), v);
+        const float2 z1 = c2mul(c2mul(make_float2(z.z, z.w), make_float2(w.z, w.w)), v);
+        z = make_float4(z0.x, z0.y, z1.x, z1.y);
+      } else {
+        z = make_float4(z.x * sc, z.y * sc, z.z * sc, z.w * sc);
+      }
+      *reinterpret_cast<float4*>(s + g) = z;
+      g += gstep;
     }
     __syncthreads();
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 // Tables of Omega^a (a < 2^nl) and Omega^{a 2^nl} (a < 2^{n-nl}),
@@ -486,28 +704,28 @@ __global__ void k_roots(typename CT<R>::V2* tlo, typename CT<R>::V2* thi, int n,
 
 // --------------------------------------------------------------------------
 // Tile-size choices: c low contiguous bits give 128-byte rows; k group bits;
-// the tile holds 2^{k+c} amplitudes (64 KiB complex128, up to 128 KiB
-// complex64: 32 complex64 qubits in three passes, 13 + 10 + 9).
+// the tile holds 2^{k+c} amplitudes (64 KiB: 2^12 complex128 or 2^13
+// complex64 amplitudes, 128 KiB for complex64 layer groups of 10): 30
+// complex128 qubits in three QFT passes, 12 + 9 + 9, 32 complex64 qubits in
+// four, 13 + 7 + 6 + 6.
 template <typename R> struct TileCfg;
 template <> struct TileCfg<double> { static constexpr int C = 3, K = 9, BOT = 12; };
 // the ladder helper reaches one level past the table (levels 0..10)
 static_assert(TileCfg<double>::BOT <= 12 && TileCfg<double>::K <= 12, "complex128 groups of at most 12 qubits");
-// complex64: 128 KiB tiles (k = 10, c = 4); the lowest group (c = 0) stops at
-// 13 qubits, where its tile and ladder table take 64 KiB each
+// complex64 layers: 128 KiB tiles for groups of 10 (c = 4, one CTA per SM),
+// 64 KiB for smaller ones; the complex64 QFT plans groups of at most 9 above
+// the lowest 13 (64 KiB tiles, two buffers in one CTA)
 template <> struct TileCfg<float> { static constexpr int C = 4, K = 10, BOT = 13; };
 
 struct Group {
   int lo, k;
 };
 
-// Groups covering qubits [0, n): the lowest group holds up to C + K qubits
-// (no separate contiguous bits needed), the others up to K.
-template <typename R>
-static std::vector<Group> plan_groups(int n) {
-  const int C = TileCfg<R>::C, K = TileCfg<R>::K;
+// Groups covering qubits [0, n): the lowest group up to bot qubits (no
+// separate contiguous bits needed), the others up to K, balanced.
+static std::vector<Group> plan_groups_k(int n, int bot, int K) {
   std::vector<Group> g;
-  (void)C;
-  const int g0 = std::min(n, TileCfg<R>::BOT);
+  const int g0 = std::min(n, bot);
   g.push_back({0, g0});
   int rest = n - g0;
   if (rest > 0) {
@@ -521,6 +739,11 @@ static std::vector<Group> plan_groups(int n) {
     }
   }
   return g;
+}
+
+template <typename R>
+static std::vector<Group> plan_groups(int n) {
+  return plan_groups_k(n, TileCfg<R>::BOT, TileCfg<R>::K);
 }
 
 template <typename R>
@@ -540,46 +763,55 @@ static qc_status run_tile(qc_state* s, TileProg<R>& P, const typename CT<R>::V2*
   const uint64_t ntiles = 1ull << (s->n - tb);
   const size_t smem = tile_smem<R>(P.k, P.c, P.twiddle != 0, P.qft != 0);
   constexpr int threads = 512;
-  if constexpr (sizeof(R) == 4) {
-    if (P.qft) {
-      static bool attr_q = false;
-      if (!attr_q) {
-        cudaFuncSetAttribute(k_tile<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_q = true;
-      }
-      const unsigned grid = resident_grid(k_tile<R, true>, threads, (int64_t)ntiles, 1, smem);
-      k_tile<R, true><<<grid, threads, smem, s->stream>>>(reinterpret_cast<V2*>(s->data), ntiles, P, tlo, thi);
-      return check_launch("tile pass");
-    }
-  }
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_tile<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_tile<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  const unsigned grid = resident_grid(k_tile<R, false>, threads, (int64_t)ntiles, 1, smem);
-  k_tile<R, false><<<grid, threads, smem, s->stream>>>(reinterpret_cast<V2*>(s->data), ntiles, P, tlo, thi);
+  const unsigned grid = resident_grid(k_tile<R>, threads, (int64_t)ntiles, 1, smem);
+  k_tile<R><<<grid, threads, smem, s->stream>>>(reinterpret_cast<V2*>(s->data), ntiles, P, tlo, thi);
   return check_launch("tile pass");
+}
+
+// complex64 QFT pass through the double-buffered kernel: two tile buffers
+// plus the pass's tables.
+static size_t qft_db_smem(int k, int c, bool twiddle) {
+  const size_t NE = (size_t)1 << (k + c);
+  return sizeof(float2) * (2 * NE + (twiddle ? NE + ((size_t)1 << k) : 0) + ((size_t)1 << k) - 1);
+}
+
+static qc_status run_qft_db_c64(qc_state* s, TileProg<float>& P, const float2* tlo, const float2* thi) {
+  P.n = s->n;
+  const uint64_t ntiles = 1ull << (s->n - (P.k + P.c));
+  const size_t smem = qft_db_smem(P.k, P.c, P.twiddle != 0);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_qft_db_c64, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr_set = true;
+  }
+  const unsigned grid = resident_grid(k_qft_db_c64, 512, (int64_t)ntiles, 1, smem);
+  k_qft_db_c64<<<grid, 512, smem, s->stream>>>(reinterpret_cast<float2*>(s->data), ntiles, P, tlo, thi);
+  return check_launch("qft pass");
 }
 
 // Contiguous low bits of a group's tile: at least C (128-byte rows) and, for
 // small groups, enough to fill the tile to 2^TB amplitudes, so that a pass
 // has few large tiles with long rows rather than many small ones (each tile
 // costs a DRAM round trip before its compute).  TB: 64 KiB tiles (two CTAs
-// per SM), 128 KiB for the complex64 QFT kernel (one CTA per SM).  The QFT
+// per SM; the complex64 QFT kernel holds two of them in one CTA).  The QFT
 // twiddle tables need c + k <= 14.
 template <typename R>
-static int tile_c(const Group& g, bool qreg) {
-  const int TB = sizeof(R) == 8 ? 12 : (qreg ? 14 : 13);
+static int tile_c(const Group& g) {
+  const int TB = sizeof(R) == 8 ? 12 : 13;
   return std::min(g.lo, std::max(TileCfg<R>::C, TB - g.k));
 }
 
 template <typename R>
-static void prog_init(TileProg<R>& P, const Group& g, int n, bool qreg = false) {
+static void prog_init(TileProg<R>& P, const Group& g, int n) {
   P.nops = 0;
   P.lo = g.lo;
   P.k = g.k;
-  P.c = tile_c<R>(g, qreg);
+  P.c = tile_c<R>(g);
   P.n = n;
   P.twiddle = 0;
   P.qft = 0;
@@ -749,11 +981,12 @@ static qc_status qft_impl(qc_state* s) {
     k_roots<R><<<grid_for(tot, 256, 4), 256, 0, s->stream>>>(tlo, thi, n, nl);
   }
   qc_status st = check_launch("qft roots");
-  std::vector<Group> groups = plan_groups<R>(n);
+  // complex64: groups of at most 9 above the lowest 13 (64 KiB tiles)
+  std::vector<Group> groups = sizeof(R) == 4 ? plan_groups_k(n, 13, 9) : plan_groups<R>(n);
   for (int gi = (int)groups.size() - 1; gi >= 0 && !st; --gi) {
     const Group& g = groups[gi];
     TileProg<R> P;
-    prog_init(P, g, n, sizeof(R) == 4);  // complex64 QFT passes run the one-CTA kernel
+    prog_init(P, g, n);
     P.nl = nl;
     P.qft = 1;
     for (int j = g.k - 1; j >= 0; --j) {
@@ -764,7 +997,8 @@ static qc_status qft_impl(qc_state* s) {
     }
     P.scale_p = g.k;
     P.twiddle = g.lo > 0;
-    st = run_tile<R>(s, P, tlo, thi);
+    if constexpr (sizeof(R) == 4) st = run_qft_db_c64(s, P, tlo, thi);
+    else st = run_tile<R>(s, P, tlo, thi);
   }
   if (!st) st = bitrev_impl<R>(s);
   cudaFreeAsync(tab, s->stream);
