@@ -281,6 +281,202 @@ __global__ void __launch_bounds__(WHT_T, 2) k_wht_c64(float2* __restrict__ s, ui
   }
 }
 
+// ------------------------------------------------ whole-group layers ----
+// The common case (HALL among them): every qubit of the group is
+// butterflied, i.e. the top L bits of the 2^TB-element tile.  The bit
+// positions are then compile-time, and the shared tile is padded (one
+// element after every 128 bytes) instead of swizzled: an element's address
+// pad(e) = e + (e >> r) is additive over disjoint index bits, so every
+// element of a register block is the thread's base address plus a constant
+// offset, and blocks of elements 2^b apart still hit distinct bank groups.
+// The global addresses of a thread's PER elements are one base plus
+// multiples of a per-pass stride.
+template <int SH>
+__host__ __device__ __forceinline__ int padded(int e) { return e + (e >> SH); }
+
+// insert RB zero bits at position B0 of p
+template <int B0, int RB>
+__device__ __forceinline__ int ins_bits(int p) {
+  return ((p >> B0) << (B0 + RB)) | (p & ((1 << B0) - 1));
+}
+
+template <int TB, int B0, int RB>
+__device__ __forceinline__ void wht_block_c128(longlong2* sm) {
+  constexpr int NR = 1 << RB;
+  for (int p = threadIdx.x; p < ((1 << TB) >> RB); p += WHT_T) {
+    const int base = padded<3>(ins_bits<B0, RB>(p));
+    longlong2 a[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) a[j] = sm[base + padded<3>(j << B0)];
+    bfly_regs<RB>(a);
+#pragma unroll
+    for (int j = 0; j < NR; ++j) sm[base + padded<3>(j << B0)] = a[j];
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(WHT_T, 2) k_wht_c128_top(double2* __restrict__ s, uint64_t ntiles, int lo, int k,
+                                                            int c, long long rsqrt2) {
+  constexpr int TB = 12, NE = 1 << TB, PER = NE / WHT_T;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  longlong2* sm = reinterpret_cast<longlong2*>(smraw);
+  __shared__ int wmax[WHT_T / 32];
+  const int tid = threadIdx.x;
+  const uint64_t gstep = c <= 9 ? ((uint64_t)(WHT_T >> c) << lo) : 0;
+  const int st = padded<3>(tid);
+  for (uint64_t T = blockIdx.x; T < ntiles; T += gridDim.x) {
+    const uint64_t g0 = wht_global((uint64_t)tid, T, lo, k, c);
+    double2 v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u)
+      v[u] = s[c <= 9 ? g0 + u * gstep : wht_global((uint64_t)(tid + u * WHT_T), T, lo, k, c)];
+    int em = 0;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      em = max(em, (int)((__double_as_longlong(v[u].x) >> 52) & 0x7FF));
+      em = max(em, (int)((__double_as_longlong(v[u].y) >> 52) & 0x7FF));
+    }
+    for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+    if ((tid & 31) == 0) wmax[tid >> 5] = em;
+    __syncthreads();
+    em = 0;
+#pragma unroll
+    for (int w = 0; w < WHT_T / 32; ++w) em = max(em, wmax[w]);
+    const int G = em + L - 9;  // as in k_wht_c128: L doublings stay below 2^62
+#pragma unroll
+    for (int u = 0; u < PER; ++u) sm[st + u * padded<3>(WHT_T)] = make_longlong2(d2fix(v[u].x, G), d2fix(v[u].y, G));
+    __syncthreads();
+    // blocks of three bits from the top: [TB-3, TB), [TB-6, TB-3), ...
+    if constexpr (L >= 3) { wht_block_c128<TB, TB - 3, 3>(sm); __syncthreads(); }
+    if constexpr (L >= 6) { wht_block_c128<TB, TB - 6, 3>(sm); __syncthreads(); }
+    if constexpr (L >= 9) { wht_block_c128<TB, TB - 9, 3>(sm); __syncthreads(); }
+    if constexpr (L >= 12) { wht_block_c128<TB, TB - 12, 3>(sm); __syncthreads(); }
+    if constexpr (L % 3 == 2) { wht_block_c128<TB, TB - L, 2>(sm); __syncthreads(); }
+    if constexpr (L % 3 == 1) { wht_block_c128<TB, TB - L, 1>(sm); __syncthreads(); }
+    const int F = 1075 - G + L / 2;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      longlong2 z = sm[st + u * padded<3>(WHT_T)];
+      if (L & 1) {
+        z.x = __mul64hi(z.x, rsqrt2) << 1;
+        z.y = __mul64hi(z.y, rsqrt2) << 1;
+      }
+      s[c <= 9 ? g0 + u * gstep : wht_global((uint64_t)(tid + u * WHT_T), T, lo, k, c)] =
+          make_double2(fix2d(z.x, F), fix2d(z.y, F));
+    }
+    __syncthreads();  // the tile is read before the next one is staged
+  }
+}
+
+template <int TB, int B0, int RB>
+__device__ __forceinline__ void wht_block_c64(float2* sm) {
+  constexpr int NR = 1 << RB;
+  for (int p = threadIdx.x; p < ((1 << TB) >> RB); p += WHT_T) {
+    const int base = padded<4>(ins_bits<B0, RB>(p));
+    float2 a[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) a[j] = sm[base + padded<4>(j << B0)];
+#pragma unroll
+    for (int lv = 0; lv < RB; ++lv)
+#pragma unroll
+      for (int i = 0; i < NR; ++i) {
+        if ((i >> lv) & 1) continue;
+        const int j = i | (1 << lv);
+        const float2 x = a[i], y = a[j];
+        a[i] = make_float2(x.x + y.x, x.y + y.y);
+        a[j] = make_float2(x.x - y.x, x.y - y.y);
+      }
+#pragma unroll
+    for (int j = 0; j < NR; ++j) sm[base + padded<4>(j << B0)] = a[j];
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(WHT_T, 2) k_wht_c64_top(float2* __restrict__ s, uint64_t ntiles, int lo, int k, int c,
+                                                           float scale) {
+  constexpr int TB = 13, NE = 1 << TB, PER = NE / WHT_T;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  const int tid = threadIdx.x;
+  const uint64_t gstep = c <= 9 ? ((uint64_t)(WHT_T >> c) << lo) : 0;
+  const int st = padded<4>(tid);
+  for (uint64_t T = blockIdx.x; T < ntiles; T += gridDim.x) {
+    const uint64_t g0 = wht_global((uint64_t)tid, T, lo, k, c);
+    float2 v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u)
+      v[u] = s[c <= 9 ? g0 + u * gstep : wht_global((uint64_t)(tid + u * WHT_T), T, lo, k, c)];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) sm[st + u * padded<4>(WHT_T)] = v[u];
+    __syncthreads();
+    // blocks of four bits from the top
+    if constexpr (L >= 4) { wht_block_c64<TB, TB - 4, 4>(sm); __syncthreads(); }
+    if constexpr (L >= 8) { wht_block_c64<TB, TB - 8, 4>(sm); __syncthreads(); }
+    if constexpr (L >= 12) { wht_block_c64<TB, TB - 12, 4>(sm); __syncthreads(); }
+    if constexpr (L % 4 == 3) { wht_block_c64<TB, TB - L, 3>(sm); __syncthreads(); }
+    if constexpr (L % 4 == 2) { wht_block_c64<TB, TB - L, 2>(sm); __syncthreads(); }
+    if constexpr (L % 4 == 1) { wht_block_c64<TB, TB - L, 1>(sm); __syncthreads(); }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const float2 z = sm[st + u * padded<4>(WHT_T)];
+      s[c <= 9 ? g0 + u * gstep : wht_global((uint64_t)(tid + u * WHT_T), T, lo, k, c)] =
+          make_float2(z.x * scale, z.y * scale);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename K>
+static void wht_top_attr(K kernel, size_t smem) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// Launch the whole-group kernel for L = k butterfly bits (L <= TB); false if
+// this L has no instantiation.
+static bool launch_wht_top_c128(qc_state* s, int L, uint64_t ntiles, int lo, int k, int c, long long rsqrt2) {
+  const size_t smem = (size_t)padded<3>(1 << 12) * 16;
+  double2* d = reinterpret_cast<double2*>(s->data);
+#define QC_WHT_C128(LL)                                                                            \
+  case LL: {                                                                                       \
+    static bool a = false;                                                                         \
+    if (!a) {                                                                                      \
+      wht_top_attr(k_wht_c128_top<LL>, smem);                                                      \
+      a = true;                                                                                    \
+    }                                                                                              \
+    const unsigned grid = resident_grid(k_wht_c128_top<LL>, WHT_T, (int64_t)ntiles, 1, smem);      \
+    k_wht_c128_top<LL><<<grid, WHT_T, smem, s->stream>>>(d, ntiles, lo, k, c, rsqrt2);             \
+    return true;                                                                                   \
+  }
+  switch (L) {
+    QC_WHT_C128(3) QC_WHT_C128(4) QC_WHT_C128(5) QC_WHT_C128(6) QC_WHT_C128(7) QC_WHT_C128(8)
+    QC_WHT_C128(9) QC_WHT_C128(10) QC_WHT_C128(12)
+    default: return false;
+  }
+#undef QC_WHT_C128
+}
+
+static bool launch_wht_top_c64(qc_state* s, int L, uint64_t ntiles, int lo, int k, int c, float scale) {
+  const size_t smem = (size_t)padded<4>(1 << 13) * 8;
+  float2* d = reinterpret_cast<float2*>(s->data);
+#define QC_WHT_C64(LL)                                                                             \
+  case LL: {                                                                                       \
+    static bool a = false;                                                                         \
+    if (!a) {                                                                                      \
+      wht_top_attr(k_wht_c64_top<LL>, smem);                                                       \
+      a = true;                                                                                    \
+    }                                                                                              \
+    const unsigned grid = resident_grid(k_wht_c64_top<LL>, WHT_T, (int64_t)ntiles, 1, smem);       \
+    k_wht_c64_top<LL><<<grid, WHT_T, smem, s->stream>>>(d, ntiles, lo, k, c, scale);               \
+    return true;                                                                                   \
+  }
+  switch (L) {
+    QC_WHT_C64(4) QC_WHT_C64(5) QC_WHT_C64(6) QC_WHT_C64(7) QC_WHT_C64(8) QC_WHT_C64(9) QC_WHT_C64(10)
+    QC_WHT_C64(13)
+    default: return false;
+  }
+#undef QC_WHT_C64
+}
+
 // --------------------------------------------------------------- host ----
 // floor(2^62.5) = floor(sqrt(2^125)) by integer Newton iteration (exact).
 static long long rsqrt2_fixed() {
@@ -363,6 +559,16 @@ static qc_status wht_layer(qc_state* s, uint64_t mask) {
     P.rsqrt2 = rsqrt2_fixed();
     const uint64_t ntiles = 1ull << (n - g.k - P.c);
     const size_t smem = ((size_t)1 << (g.k + P.c)) * (sizeof(R) * 2 == 16 ? 16 : 8);
+    // every qubit of the group butterflied: the compile-time kernels
+    if (P.nb == g.k && g.k + P.c == TB) {
+      const bool done = sizeof(R) == 8 ? launch_wht_top_c128(s, g.k, ntiles, g.lo, g.k, P.c, P.rsqrt2)
+                                       : launch_wht_top_c64(s, g.k, ntiles, g.lo, g.k, P.c,
+                                                            (float)std::exp2(-0.5 * P.nb));
+      if (done) {
+        ++launches;
+        continue;
+      }
+    }
     if constexpr (sizeof(R) == 8) {
       const unsigned grid = resident_grid(k_wht_c128, WHT_T, (int64_t)ntiles, 1, smem);
       k_wht_c128<<<grid, WHT_T, smem, s->stream>>>(reinterpret_cast<double2*>(s->data), ntiles, P);
