@@ -594,6 +594,153 @@ __device__ __forceinline__ void qft_levels_c64(float2* sm, int NE, int c, int k,
   }
 }
 
+// Compile-time forms for the passes of states of at least 13 qubits, where
+// every tile holds 2^13 amplitudes (k + c = 13): the register blocks' bit
+// positions, the swizzled offsets of a block's elements and a thread's
+// copy and store offsets are constants, so the index arithmetic is one XOR
+// per element.  qsw is linear over XOR, qsw(x ^ y) = qsw(x) ^ qsw(y).
+template <int QR, int BL, int JLO>
+__device__ __forceinline__ void qft_block_c64_ct(float2* sm, const float2* LAD) {
+  constexpr int NR = 1 << QR, NE = 1 << 13;
+  constexpr int C = BL - JLO;
+#pragma unroll
+  for (int r = 0; r < (NE >> QR) / 512; ++r) {
+    const int p = threadIdx.x + 512 * r;
+    const int base = ((p >> BL) << (BL + QR)) | (p & ((1 << BL) - 1));
+    const int sb = qsw(base);
+    float2 a[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) a[i] = sm[sb ^ qsw(i << BL)];
+    const int xlow = (base >> C) & ((1 << JLO) - 1);
+#pragma unroll
+    for (int lv = QR - 1; lv >= 0; --lv) {
+      const int j = JLO + lv;
+      const float2 u = LAD[(1 << j) - 1 + xlow];  // L_j(xlow)
+#pragma unroll
+      for (int i = 0; i < NR; ++i) {
+        if ((i >> lv) & 1) continue;
+        const int i1 = i | (1 << lv);
+        const float2 x0 = a[i], x1 = a[i1];
+        a[i] = make_float2(x0.x + x1.x, x0.y + x1.y);
+        const int m = i & ((1 << lv) - 1);  // the factor e^{2 pi i m / 2^{lv+1}} L_j(xlow)
+        a[i1] = c2mul(make_float2(x0.x - x1.x, x0.y - x1.y), m ? c2mul(qroot(lv, m), u) : u);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NR; ++i) sm[sb ^ qsw(i << BL)] = a[i];
+  }
+}
+
+// block b of the K levels: ceil(K/4) blocks, balanced, the larger first
+__host__ __device__ constexpr int qft_nblocks(int K) { return (K + 3) >> 2; }
+__host__ __device__ constexpr int qft_block_size(int K, int b) {
+  int j = K - 1, qr = 0;
+  for (int i = 0; i <= b; ++i) {
+    const int nb = qft_nblocks(K);
+    qr = (j + 1 + (nb - i) - 1) / (nb - i);
+    if (i < b) j -= qr;
+  }
+  return qr;
+}
+__host__ __device__ constexpr int qft_block_jlo(int K, int b) {
+  int j = K - 1;
+  for (int i = 0; i <= b; ++i) j -= qft_block_size(K, i);
+  return j + 1;
+}
+
+template <int K, int B>
+__device__ __forceinline__ void qft_levels_c64_ct(float2* sm, const float2* LAD) {
+  if constexpr (B < qft_nblocks(K)) {
+    constexpr int QR = qft_block_size(K, B), JLO = qft_block_jlo(K, B), C = 13 - K;
+    qft_block_c64_ct<QR, C + JLO, JLO>(sm, LAD);
+    __syncthreads();
+    qft_levels_c64_ct<K, B + 1>(sm, LAD);
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(512, 1) k_qft_db_c64_k(float2* __restrict__ s, uint64_t ntiles, const TileProg<float> P,
+                                                         const float2* __restrict__ tlo,
+                                                         const float2* __restrict__ thi) {
+  using A = TA<float>;
+  constexpr int C = 13 - K, NE = 1 << 13;
+  static_assert(C <= 10, "1024-element copy strides stay inside the group bits");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int lo = P.lo, hi = lo + K - 1;
+  const bool tw = P.twiddle != 0;
+  float2* buf0 = reinterpret_cast<float2*>(smraw);
+  float2* buf1 = buf0 + NE;
+  float2* W = buf1 + NE;
+  float2* V = W + (tw ? NE : 0);
+  float2* LAD = V + (tw ? (1 << K) : 0);
+  const float sc = (float)exp2(-0.5 * K);
+  const int e0 = 2 * threadIdx.x;
+  const int se0 = qsw(e0);
+  const uint64_t gstep = (uint64_t)(1024 >> C) << lo;
+  // this thread's copy / store elements e0 + 1024 u share the group bits'
+  // low part; their reversed group bits are f0 | brev(u) at the top
+  const int f0 = (int)(__brev((unsigned)(e0 >> C)) >> (32 - K));
+  auto issue = [&](uint64_t T, float2* dst) {
+    const uint64_t g = tile_global((uint64_t)e0, T, lo, K, C);
+#pragma unroll
+    for (int u = 0; u < NE / 1024; ++u) {
+      const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + (se0 ^ qsw(1024 * u)));
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(s + g + u * gstep) : "memory");
+    }
+  };
+  uint64_t T = blockIdx.x;
+  if (T < ntiles) issue(T, buf0);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  for (int a = threadIdx.x; a < (1 << K) - 1; a += blockDim.x) {
+    const int j = 31 - __clz(a + 1);
+    const A::E z = A::root((uint64_t)(a + 1 - (1 << j)), j + 1);
+    LAD[a] = make_float2(z.re, z.im);
+  }
+  if (tw)
+    for (int e = threadIdx.x; e < NE; e += blockDim.x) {
+      const int f = (int)(__brev((unsigned)(e >> C)) >> (32 - K));
+      const A::E z = A::root((uint64_t)((e & ((1 << C) - 1)) * f), hi + 1);
+      W[e] = make_float2(z.re, z.im);
+    }
+  for (int it = 0; T < ntiles; T += gridDim.x, ++it) {
+    float2* cur = (it & 1) ? buf1 : buf0;
+    float2* nxt = (it & 1) ? buf0 : buf1;
+    if (T + gridDim.x < ntiles) issue(T + gridDim.x, nxt);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    if (tw) {
+      const uint64_t Lt = (T & ((1ull << (lo - C)) - 1ull)) << C;
+      for (int f = threadIdx.x; f < (1 << K); f += blockDim.x) {
+        const uint64_t r = (Lt * (uint64_t)f) & ((2ull << hi) - 1ull);
+        const A::E z = A::scale_by(omega<float>(tlo, thi, r << (P.n - hi - 1), P.nl), sc);
+        V[f] = make_float2(z.re, z.im);
+      }
+    }
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncthreads();
+    qft_levels_c64_ct<K, 0>(cur, LAD);
+    const uint64_t g = tile_global((uint64_t)e0, T, lo, K, C);
+#pragma unroll
+    for (int u = 0; u < NE / 1024; ++u) {
+      float4 z = *reinterpret_cast<const float4*>(cur + (se0 ^ qsw(1024 * u)));
+      if (tw) {
+        // the group bits of e0 + 1024 u are (e0 >> C) + (1024 u >> C): reversed,
+        // brev(u) lands below f0's bits
+        const int f = f0 | (int)(__brev((unsigned)((1024 * u) >> C)) >> (32 - K));
+        const float2 v = V[f];
+        const float4 w = *reinterpret_cast<const float4*>(W + e0 + 1024 * u);
+        const float2 z0 = c2mul(c2mul(make_float2(z.x, z.y), make_float2(w.x, w.y)), v);
+        const float2 z1 = c2mul(c2mul(make_float2(z.z, z.w), make_float2(w.z, w.w)), v);
+        z = make_float4(z0.x, z0.y, z1.x, z1.y);
+      } else {
+        z = make_float4(z.x * sc, z.y * sc, z.z * sc, z.w * sc);
+      }
+      *reinterpret_cast<float4*>(s + g + u * gstep) = z;
+    }
+    __syncthreads();
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // P holds the pass: group [lo, lo+k), c contiguous bits, twiddle = lo > 0,
 // scale_p = k.  Shared memory: two tile buffers, then (twiddle passes) the
 // per-pass table W[e] = Omega_{hi+1}^{l f} (l = e's c low bits, f = its
@@ -789,8 +936,28 @@ static qc_status run_qft_db_c64(qc_state* s, TileProg<float>& P, const float2* t
     cudaFuncSetAttribute(k_qft_db_c64, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr_set = true;
   }
+  float2* d = reinterpret_cast<float2*>(s->data);
+  // 2^13-amplitude tiles (states of at least 13 qubits): the compile-time kernels
+  if (P.k + P.c == 13 && P.c == 13 - P.k && P.scale_p == P.k) {
+    switch (P.k) {
+#define QC_QFT_DB(KK)                                                                              \
+  case KK: {                                                                                       \
+    static bool a = false;                                                                         \
+    if (!a) {                                                                                      \
+      cudaFuncSetAttribute(k_qft_db_c64_k<KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024); \
+      a = true;                                                                                    \
+    }                                                                                              \
+    const unsigned g = resident_grid(k_qft_db_c64_k<KK>, 512, (int64_t)ntiles, 1, smem);          \
+    k_qft_db_c64_k<KK><<<g, 512, smem, s->stream>>>(d, ntiles, P, tlo, thi);                       \
+    return check_launch("qft pass");                                                               \
+  }
+      QC_QFT_DB(3) QC_QFT_DB(4) QC_QFT_DB(5) QC_QFT_DB(6) QC_QFT_DB(7) QC_QFT_DB(8) QC_QFT_DB(9) QC_QFT_DB(13)
+#undef QC_QFT_DB
+      default: break;
+    }
+  }
   const unsigned grid = resident_grid(k_qft_db_c64, 512, (int64_t)ntiles, 1, smem);
-  k_qft_db_c64<<<grid, 512, smem, s->stream>>>(reinterpret_cast<float2*>(s->data), ntiles, P, tlo, thi);
+  k_qft_db_c64<<<grid, 512, smem, s->stream>>>(d, ntiles, P, tlo, thi);
   return check_launch("qft pass");
 }
 
