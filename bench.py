@@ -479,11 +479,10 @@ def run_e2e(args, st, step_fn, ops_per_step, N):
     the 1000 measurement samples, back to pinned host memory.  Two device
     states are used in turn, so a step's upload overlaps the other state's
     step; the uploads go through one copy stream.  (On the GB300 machines' host
-    link a single copy runs at about 210 GB/s host->device; copies in both
-    directions, concurrent or alternating, dropped to 10-35 GB/s on boxes
-    that had run other jobs since boot, so the state itself is not read
-    back: the step's result is its samples.)  The timed region holds every
-    step's copies."""
+    link a single copy runs at up to about 210 GB/s host->device, but at
+    times at 16-85 GB/s, alone or overlapped, and two copies at once run at
+    9-17 GB/s; the state itself is not read back: the step's result is its
+    samples.)  The timed region holds every step's copies."""
     import numpy as np
     import torch
     import paper_0902_0699_gb300 as qc
