@@ -343,11 +343,16 @@ __global__ void __launch_bounds__(WHT_T, 2) k_wht_c128_top(double2* __restrict__
 #pragma unroll
     for (int w = 0; w < WHT_T / 32; ++w) em = max(em, wmax[w]);
     const int G = em + L - 9;  // as in k_wht_c128: L doublings stay below 2^62
+    // a thread's eight elements tid + 512 u differ exactly in the top three
+    // tile bits: their butterflies run in registers before the first store
+    longlong2 a[PER];
 #pragma unroll
-    for (int u = 0; u < PER; ++u) sm[st + u * padded<3>(WHT_T)] = make_longlong2(d2fix(v[u].x, G), d2fix(v[u].y, G));
+    for (int u = 0; u < PER; ++u) a[u] = make_longlong2(d2fix(v[u].x, G), d2fix(v[u].y, G));
+    bfly_regs<3>(a);
+#pragma unroll
+    for (int u = 0; u < PER; ++u) sm[st + u * padded<3>(WHT_T)] = a[u];
     __syncthreads();
-    // blocks of three bits from the top: [TB-3, TB), [TB-6, TB-3), ...
-    if constexpr (L >= 3) { wht_block_c128<TB, TB - 3, 3>(sm); __syncthreads(); }
+    // the other blocks of three bits from the top: [TB-6, TB-3), [TB-9, TB-6), ...
     if constexpr (L >= 6) { wht_block_c128<TB, TB - 6, 3>(sm); __syncthreads(); }
     if constexpr (L >= 9) { wht_block_c128<TB, TB - 9, 3>(sm); __syncthreads(); }
     if constexpr (L >= 12) { wht_block_c128<TB, TB - 12, 3>(sm); __syncthreads(); }
@@ -406,11 +411,22 @@ __global__ void __launch_bounds__(WHT_T, 2) k_wht_c64_top(float2* __restrict__ s
 #pragma unroll
     for (int u = 0; u < PER; ++u)
       v[u] = s[c <= 9 ? g0 + u * gstep : wht_global((uint64_t)(tid + u * WHT_T), T, lo, k, c)];
+    // a thread's sixteen elements tid + 512 u differ exactly in the top four
+    // tile bits: their butterflies run in registers before the first store
+#pragma unroll
+    for (int lv = 0; lv < 4; ++lv)
+#pragma unroll
+      for (int i = 0; i < PER; ++i) {
+        if ((i >> lv) & 1) continue;
+        const int j = i | (1 << lv);
+        const float2 x = v[i], y = v[j];
+        v[i] = make_float2(x.x + y.x, x.y + y.y);
+        v[j] = make_float2(x.x - y.x, x.y - y.y);
+      }
 #pragma unroll
     for (int u = 0; u < PER; ++u) sm[st + u * padded<4>(WHT_T)] = v[u];
     __syncthreads();
-    // blocks of four bits from the top
-    if constexpr (L >= 4) { wht_block_c64<TB, TB - 4, 4>(sm); __syncthreads(); }
+    // the other blocks of four bits from the top
     if constexpr (L >= 8) { wht_block_c64<TB, TB - 8, 4>(sm); __syncthreads(); }
     if constexpr (L >= 12) { wht_block_c64<TB, TB - 12, 4>(sm); __syncthreads(); }
     if constexpr (L % 4 == 3) { wht_block_c64<TB, TB - L, 3>(sm); __syncthreads(); }
