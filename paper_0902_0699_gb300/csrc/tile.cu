@@ -504,6 +504,138 @@ __global__ void __launch_bounds__(512, 2) k_tile(typename CT<R>::V2* __restrict_
   }
 }
 
+// ------------------------------------------------ complex128 QFT passes --
+// For states of at least 12 qubits every complex128 QFT pass has k + c = 12,
+// so the pass is compiled per group size K: the radix-4 level pairs' bit
+// positions are constants, the tile is XOR-swizzled in 16-byte elements
+// (bits 0..2 take bits 3..5, which is linear over XOR, so every element of a
+// radix-4 quad is one XOR away from the thread's base and the low-bit
+// stages are free of bank conflicts), and a thread's eight load / store
+// addresses are one base plus multiples of a per-pass stride.  The
+// arithmetic is that of k_tile's QFT programs.
+__device__ __forceinline__ int tsw(int e) { return e ^ ((e >> 3) & 7); }
+
+template <int BH, int BL, int JH, int C>
+__device__ __forceinline__ void qft_quad_c128(ffc* sm, const ffc* LAD, int kl) {
+  using A = TA<double>;
+  constexpr int NE = 1 << 12, JL = JH - 1;
+  static_assert(BH == BL + 1, "neighbouring levels");
+#pragma unroll
+  for (int r = 0; r < (NE >> 2) / 512; ++r) {
+    const int p = threadIdx.x + 512 * r;
+    const int e00 = ((p >> BL) << (BL + 2)) | (p & ((1 << BL) - 1));
+    const int b = tsw(e00);
+    const int o01 = tsw(1 << BL), o10 = tsw(1 << BH), o11 = tsw(3 << BL);
+    const ffc a00 = sm[b], a01 = sm[b ^ o01], a10 = sm[b ^ o10], a11 = sm[b ^ o11];
+    const ffc s0 = A::add_u(a00, a10), d0 = A::sub_u(a00, a10);
+    const ffc s1 = A::add_u(a01, a11), d1 = A::sub_u(a01, a11);
+    // as in k_tile: t0 = s0 + s1, u0 = L(2x)(s0 - s1), t1 = L(x)(d0 + i d1),
+    // u1 = L(3x)(d0 - i d1), L(y) = e^{2 pi i y / 2^{JH+1}}, x = group bits below JL
+    const int x = (e00 >> C) & ((1 << JL) - 1);
+    const ffc id1 = A::times_i(d1);
+    const ffc t0 = A::add(s0, s1);
+    ffc u0 = A::sub_u(s0, s1), t1 = A::add_u(d0, id1), u1 = A::sub_u(d0, id1);
+    if (x) {
+      u0 = A::mul(ladder_at<double>(LAD, kl, JH, 2 * x), u0);
+      t1 = A::mul(ladder_at<double>(LAD, kl, JH, x), t1);
+      const int x3 = 3 * x;
+      u1 = A::mul(ladder_at<double>(LAD, kl, JH, x3 & ((1 << JH) - 1)), u1);
+      if (x3 >> JH) u1 = A::neg(u1);
+    } else {
+      u0 = A::norm(u0);
+      t1 = A::norm(t1);
+      u1 = A::norm(u1);
+    }
+    sm[b] = t0;
+    sm[b ^ o01] = u0;
+    sm[b ^ o10] = t1;
+    sm[b ^ o11] = u1;
+  }
+}
+
+// level 0 alone (odd K): plain butterflies on tile bit C (no ladder below it)
+template <int C>
+__device__ __forceinline__ void qft_single0_c128(ffc* sm) {
+  using A = TA<double>;
+  constexpr int NE = 1 << 12;
+#pragma unroll
+  for (int r = 0; r < (NE >> 1) / 512; ++r) {
+    const int p = threadIdx.x + 512 * r;
+    const int e0 = ((p >> C) << (C + 1)) | (p & ((1 << C) - 1));
+    const int b = tsw(e0), o = tsw(1 << C);
+    const ffc a0 = sm[b], a1 = sm[b ^ o];
+    sm[b] = A::add(a0, a1);
+    sm[b ^ o] = A::sub(a0, a1);
+  }
+}
+
+// levels JH, JH-1 as one quad stage, then the rest
+template <int K, int JH>
+__device__ __forceinline__ void qft_stages_c128(ffc* sm, const ffc* LAD, int kl) {
+  constexpr int C = 12 - K;
+  if constexpr (JH >= 1) {
+    qft_quad_c128<C + JH, C + JH - 1, JH, C>(sm, LAD, kl);
+    __syncthreads();
+    qft_stages_c128<K, JH - 2>(sm, LAD, kl);
+  } else if constexpr (JH == 0) {
+    qft_single0_c128<C>(sm);
+    __syncthreads();
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(512, 2) k_qft_c128_k(double2* __restrict__ s, uint64_t ntiles, const TileProg<double> P,
+                                                       const double2* __restrict__ tlo,
+                                                       const double2* __restrict__ thi) {
+  using A = TA<double>;
+  constexpr int C = 12 - K, NE = 1 << 12, PER = NE / 512;
+  static_assert(C <= 9, "512-element strides stay inside the group bits");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  ffc* sm = reinterpret_cast<ffc*>(smraw);
+  const int lo = P.lo;
+  const bool tw = P.twiddle != 0;
+  ffc* V = sm + NE;
+  ffc* LAD = V + (tw ? (1 << K) : 0);
+  constexpr int kl = lad_levels<double>(K);
+  ffc* TWA = LAD + lad_entries<double>(K);
+  ffc* TWB = TWA + TS_TWA;
+  const typename A::S sc = A::scale_const(K);
+  tile_tables<double>(P, LAD, TWA, TWB, kl);
+  const int tid = threadIdx.x;
+  const int st = tsw(tid);
+  const uint64_t gstep = (uint64_t)(512 >> C) << lo;
+  for (uint64_t T = blockIdx.x; T < ntiles; T += gridDim.x) {
+    if (tw) tile_twiddle_v<double>(P, T, V, tlo, thi, sc);
+    const uint64_t g0 = tile_global((uint64_t)tid, T, lo, K, C);
+    // four 16-byte loads in flight per thread, twice
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      double2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = s[g0 + (4 * h + u) * gstep];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sm[st ^ tsw(512 * (4 * h + u))] = A::from(v[u]);
+    }
+    __syncthreads();
+    qft_stages_c128<K, K - 1>(sm, LAD, kl);
+    // store: the twiddle (which carries the 2^{-K/2} scale), or the scale
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + 512 * u;
+      ffc z = sm[st ^ tsw(512 * u)];
+      if (tw) {
+        const int f = (int)(__brev((unsigned)(e >> C)) >> (32 - K));
+        const int x = (e & ((1 << C) - 1)) * f;  // < 2^12
+        z = A::mul(A::mul(V[f], A::mul(TWA[x & 127], TWB[x >> 7])), z);
+      } else {
+        z = A::scale_by(z, sc);
+      }
+      s[g0 + u * gstep] = A::to(z);
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------- complex64 QFT passes --
 // One CTA per SM with two 64 KiB tile buffers: the next tile's loads
 // (cp.async, 16 bytes each) are in flight while the current tile is
@@ -920,6 +1052,35 @@ static qc_status run_tile(qc_state* s, TileProg<R>& P, const typename CT<R>::V2*
   return check_launch("tile pass");
 }
 
+// complex128 QFT pass: the compiled kernel for 2^12-amplitude tiles, else
+// the general tile program.
+static qc_status run_qft_c128(qc_state* s, TileProg<double>& P, const double2* tlo, const double2* thi) {
+  P.n = s->n;
+  if (P.k + P.c == 12 && P.scale_p == P.k && P.nops == P.k) {
+    const uint64_t ntiles = 1ull << (s->n - 12);
+    const size_t smem = tile_smem<double>(P.k, P.c, P.twiddle != 0, true);
+    double2* d = reinterpret_cast<double2*>(s->data);
+    switch (P.k) {
+#define QC_QFT_C128(KK)                                                                             \
+  case KK: {                                                                                        \
+    static bool a = false;                                                                          \
+    if (!a) {                                                                                       \
+      cudaFuncSetAttribute(k_qft_c128_k<KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); \
+      a = true;                                                                                     \
+    }                                                                                               \
+    const unsigned g = resident_grid(k_qft_c128_k<KK>, 512, (int64_t)ntiles, 1, smem);             \
+    k_qft_c128_k<KK><<<g, 512, smem, s->stream>>>(d, ntiles, P, tlo, thi);                          \
+    return check_launch("qft pass");                                                                \
+  }
+      QC_QFT_C128(3) QC_QFT_C128(4) QC_QFT_C128(5) QC_QFT_C128(6) QC_QFT_C128(7) QC_QFT_C128(8)
+      QC_QFT_C128(9) QC_QFT_C128(12)
+#undef QC_QFT_C128
+      default: break;
+    }
+  }
+  return run_tile<double>(s, P, tlo, thi);
+}
+
 // complex64 QFT pass through the double-buffered kernel: two tile buffers
 // plus the pass's tables.
 static size_t qft_db_smem(int k, int c, bool twiddle) {
@@ -1165,7 +1326,7 @@ static qc_status qft_impl(qc_state* s) {
     P.scale_p = g.k;
     P.twiddle = g.lo > 0;
     if constexpr (sizeof(R) == 4) st = run_qft_db_c64(s, P, tlo, thi);
-    else st = run_tile<R>(s, P, tlo, thi);
+    else st = run_qft_c128(s, P, tlo, thi);
   }
   if (!st) st = bitrev_impl<R>(s);
   cudaFreeAsync(tab, s->stream);
