@@ -780,13 +780,57 @@ __host__ __device__ constexpr int qft_block_jlo(int K, int b) {
   return j + 1;
 }
 
-template <int K, int B>
+// blocks B .. END-1 of the K levels, a barrier after each
+template <int K, int B, int END>
 __device__ __forceinline__ void qft_levels_c64_ct(float2* sm, const float2* LAD) {
-  if constexpr (B < qft_nblocks(K)) {
+  if constexpr (B < END) {
     constexpr int QR = qft_block_size(K, B), JLO = qft_block_jlo(K, B), C = 13 - K;
     qft_block_c64_ct<QR, C + JLO, JLO>(sm, LAD);
     __syncthreads();
-    qft_levels_c64_ct<K, B + 1>(sm, LAD);
+    qft_levels_c64_ct<K, B + 1, END>(sm, LAD);
+  }
+}
+
+// The last block (levels QR-1 .. 0, on tile bits C .. C+QR-1) of a twiddle
+// pass, written straight to the state: element i of a thread's block has
+// group bits (base >> C) | i, so its state index is the block base's plus
+// i << lo, and its twiddle is W[e] V[f] with f = brev(base >> C) | brev(i).
+// Consecutive threads hold consecutive low bits (2^C >= 16 amplitudes, at
+// least 128 contiguous bytes per warp and element).
+template <int K, int QR>
+__device__ __forceinline__ void qft_last_block_store_c64(const float2* sm, const float2* LAD, const float2* W,
+                                                         const float2* V, float2* __restrict__ s, uint64_t T,
+                                                         int lo) {
+  constexpr int NR = 1 << QR, NE = 1 << 13, C = 13 - K, BL = C;
+#pragma unroll
+  for (int r = 0; r < (NE >> QR) / 512; ++r) {
+    const int p = threadIdx.x + 512 * r;
+    const int base = ((p >> BL) << (BL + QR)) | (p & ((1 << BL) - 1));
+    const int sb = qsw(base);
+    float2 a[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) a[i] = sm[sb ^ qsw(i << BL)];
+    // jlo = 0: every level's ladder phase is a constant root (xlow = 0)
+#pragma unroll
+    for (int lv = QR - 1; lv >= 0; --lv) {
+#pragma unroll
+      for (int i = 0; i < NR; ++i) {
+        if ((i >> lv) & 1) continue;
+        const int i1 = i | (1 << lv);
+        const float2 x0 = a[i], x1 = a[i1];
+        a[i] = make_float2(x0.x + x1.x, x0.y + x1.y);
+        const int m = i & ((1 << lv) - 1);
+        const float2 d = make_float2(x0.x - x1.x, x0.y - x1.y);
+        a[i1] = m ? c2mul(d, qroot(lv, m)) : d;
+      }
+    }
+    const uint64_t g = tile_global((uint64_t)base, T, lo, K, C);
+    const int fb = (int)(__brev((unsigned)(base >> C)) >> (32 - K));
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+      const int f = fb | (int)(__brev((unsigned)i) >> (32 - K));
+      s[g + ((uint64_t)i << lo)] = c2mul(c2mul(a[i], W[base | (i << BL)]), V[f]);
+    }
   }
 }
 
@@ -849,7 +893,17 @@ __global__ void __launch_bounds__(512, 1) k_qft_db_c64_k(float2* __restrict__ s,
     }
     asm volatile("cp.async.wait_group 1;\n" ::: "memory");
     __syncthreads();
-    qft_levels_c64_ct<K, 0>(cur, LAD);
+    if constexpr (C >= 4) {
+      if (tw) {
+        // every pass above the lowest group: the last block goes straight to the state
+        constexpr int NB = qft_nblocks(K);
+        qft_levels_c64_ct<K, 0, NB - 1>(cur, LAD);
+        qft_last_block_store_c64<K, qft_block_size(K, NB - 1)>(cur, LAD, W, V, s, T, lo);
+        __syncthreads();
+        continue;
+      }
+    }
+    qft_levels_c64_ct<K, 0, qft_nblocks(K)>(cur, LAD);
     const uint64_t g = tile_global((uint64_t)e0, T, lo, K, C);
 #pragma unroll
     for (int u = 0; u < NE / 1024; ++u) {
