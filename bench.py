@@ -423,17 +423,26 @@ def gpu_numa_node(dev):
 
 
 class HostBuffer:
-    """Page-locked host memory for the end-to-end copies, allocated by
-    cudaHostAlloc (torch's pinned allocator) from a thread bound to the CPUs
-    of the GPU's NUMA node, so that the pages are placed next to the GPU.
-    (An anonymous mapping bound with mbind and registered with
-    cudaHostRegister was tried as well: on the GB300 machines its host->device
-    rate dropped to about 10 GB/s for good once two copies had overlapped on
-    it, while cudaHostAlloc memory keeps about 210 GB/s.)"""
+    """Page-locked host memory for the end-to-end copies: an anonymous
+    mapping advised to transparent huge pages (MADV_HUGEPAGE), first touched
+    from a thread bound to the CPUs of the GPU's NUMA node and registered
+    with cudaHostRegister, so that the pages sit next to the GPU and are
+    mapped with a few large translations.  Falls back to torch's pinned
+    allocator (cudaHostAlloc) where the registration fails.  (On the GB300
+    boxes cudaHostAlloc memory copied at 210 GB/s host->device on a fresh
+    box but at 16-85 GB/s once the box had run the GPU tests; the huge-page
+    buffer kept 210 GB/s on such a box.)"""
+
+    MADV_HUGEPAGE = 14
 
     def __init__(self, nbytes, node):
+        import ctypes
+        import mmap
         import torch
         self.nbytes, self.node = nbytes, node
+        self.t = None
+        self.buf = None
+        self.addr = None
         cpus = None
         if node is not None:
             try:
@@ -446,19 +455,44 @@ class HostBuffer:
             os.sched_setaffinity(0, cpus & old)
             bound = True
         try:
-            self.t = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
-            self.t.zero_()  # first touch from the bound thread (pages are placed at pinning already)
+            try:
+                libc = ctypes.CDLL(None, use_errno=True)
+                libc.madvise.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+                libc.memset.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t]
+                buf = mmap.mmap(-1, nbytes, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+                addr = ctypes.addressof(ctypes.c_char.from_buffer(buf))
+                thp = libc.madvise(ctypes.c_void_p(addr), ctypes.c_size_t(nbytes), self.MADV_HUGEPAGE) == 0
+                libc.memset(ctypes.c_void_p(addr), 0, ctypes.c_size_t(nbytes))  # first touch, bound thread
+                if int(torch.cuda.cudart().cudaHostRegister(addr, nbytes, 0)) != 0:
+                    raise RuntimeError("cudaHostRegister failed")
+                self.buf, self.addr = buf, addr
+                self.t = torch.frombuffer(buf, dtype=torch.uint8, count=nbytes)
+                self.method = "anonymous mapping%s, first touch from %s, cudaHostRegister" % (
+                    " with MADV_HUGEPAGE" if thp else "",
+                    ("a thread bound to node %d's CPUs" % node) if bound else "an unbound thread")
+            except Exception as e:
+                self.t = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+                self.t.zero_()
+                self.method = "cudaHostAlloc (registration of a huge-page mapping failed: %s)" % e
         finally:
             if bound:
                 os.sched_setaffinity(0, old)
-        self.method = ("cudaHostAlloc from a thread bound to node %d's CPUs" % node) if bound else \
-            "cudaHostAlloc (NUMA node unknown: default placement)"
 
     def tensor(self, dtype, numel):
         return self.t.view(dtype)[:numel]
 
     def close(self):
+        import torch
         self.t = None
+        if self.addr is not None:
+            torch.cuda.cudart().cudaHostUnregister(self.addr)
+            self.addr = None
+        if self.buf is not None:
+            try:
+                self.buf.close()
+            except BufferError:
+                pass  # a view is still alive: the mapping goes with the process
+            self.buf = None
 
 
 def parse_cpulist(txt):
@@ -479,10 +513,10 @@ def run_e2e(args, st, step_fn, ops_per_step, N):
     the 1000 measurement samples, back to pinned host memory.  Two device
     states are used in turn, so a step's upload overlaps the other state's
     step; the uploads go through one copy stream.  (On the GB300 machines' host
-    link a single copy runs at up to about 210 GB/s host->device, but at
-    times at 16-85 GB/s, alone or overlapped, and two copies at once run at
-    9-17 GB/s; the state itself is not read back: the step's result is its
-    samples.)  The timed region holds every step's copies."""
+    link a single copy runs at about 210 GB/s host->device from a huge-page
+    buffer, while two copies at once ran at 9-17 GB/s; the state itself is
+    not read back: the step's result is its samples.)  The timed region
+    holds every step's copies."""
     import numpy as np
     import torch
     import paper_0902_0699_gb300 as qc
