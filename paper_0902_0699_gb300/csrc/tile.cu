@@ -867,15 +867,18 @@ __global__ void __launch_bounds__(512, 1) k_qft_db_c64_k(float2* __restrict__ s,
   uint64_t T = blockIdx.x;
   if (T < ntiles) issue(T, buf0);
   asm volatile("cp.async.commit_group;\n" ::: "memory");
+  // the pass's tables from the global root tables (powers of Omega_n), in
+  // FP32: e^{2 pi i x / 2^{j+1}} = Omega_n^{x 2^{n-j-1}}
   for (int a = threadIdx.x; a < (1 << K) - 1; a += blockDim.x) {
     const int j = 31 - __clz(a + 1);
-    const A::E z = A::root((uint64_t)(a + 1 - (1 << j)), j + 1);
+    const A::E z = omega<float>(tlo, thi, (uint64_t)(a + 1 - (1 << j)) << (P.n - j - 1), P.nl);
     LAD[a] = make_float2(z.re, z.im);
   }
   if (tw)
     for (int e = threadIdx.x; e < NE; e += blockDim.x) {
       const int f = (int)(__brev((unsigned)(e >> C)) >> (32 - K));
-      const A::E z = A::root((uint64_t)((e & ((1 << C) - 1)) * f), hi + 1);
+      const uint64_t x = (uint64_t)((e & ((1 << C) - 1)) * f);  // < 2^13 <= 2^{hi+1}
+      const A::E z = omega<float>(tlo, thi, x << (P.n - hi - 1), P.nl);
       W[e] = make_float2(z.re, z.im);
     }
   for (int it = 0; T < ntiles; T += gridDim.x, ++it) {
@@ -961,15 +964,17 @@ __global__ void __launch_bounds__(512, 1) k_qft_db_c64(float2* __restrict__ s, u
   if (T < ntiles) issue(T, buf0);
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   // ladder table: LAD[2^j - 1 + x] = e^{2 pi i x / 2^{j+1}}, j < k
+  // (from the global root tables: e^{2 pi i x / 2^{j+1}} = Omega_n^{x 2^{n-j-1}})
   for (int a = threadIdx.x; a < (1 << k) - 1; a += blockDim.x) {
     const int j = 31 - __clz(a + 1);
-    const A::E z = A::root((uint64_t)(a + 1 - (1 << j)), j + 1);
+    const A::E z = omega<float>(tlo, thi, (uint64_t)(a + 1 - (1 << j)) << (P.n - j - 1), P.nl);
     LAD[a] = make_float2(z.re, z.im);
   }
   if (P.twiddle)
     for (int e = threadIdx.x; e < NE; e += blockDim.x) {
       const int f = (int)(__brev((unsigned)(e >> c)) >> (32 - k));
-      const A::E z = A::root((uint64_t)((e & ((1 << c) - 1)) * f), hi + 1);  // l f < 2^{c+k}
+      const uint64_t x = (uint64_t)((e & ((1 << c) - 1)) * f);  // l f < 2^{c+k} <= 2^{hi+1}
+      const A::E z = omega<float>(tlo, thi, x << (P.n - hi - 1), P.nl);
       W[e] = make_float2(z.re, z.im);
     }
   for (int it = 0; T < ntiles; T += gridDim.x, ++it) {
