@@ -127,8 +127,9 @@ def test_bench_workload_full_size(qc, n, dt, tol, seed):
 @pytest.mark.parametrize("n,dt,tol,rel", [(34, 1, 1e-5, 1e-5), (33, 0, 1e-12, 1e-11)])
 def test_maximum_size(qc, n, dt, tol, rel):
     # the largest states the API takes (128 GiB): indices above 2^32 in
-    # every kernel, Grover against its closed form, exact sampling against
-    # the closed-form integer CDF, and self-inverse gates on the top qubit
+    # every kernel; HALL of |0..0>, then Grover against its closed form,
+    # exact sampling against the closed-form integer CDF, self-inverse gates
+    # on the top qubit, and the QFT against its closed form
     import torch
     N = 1 << n
     need = N * (8 if dt == 1 else 16)
@@ -137,8 +138,8 @@ def test_maximum_size(qc, n, dt, tol, rel):
         pytest.skip("needs a GPU with room for a %d GiB state" % (need >> 30))
     M, iters = 8, 3
     marked = W.marked_indices(W.rng(n), n, M)
-    st = qc.State(n, dt)
-    st.uniform()
+    st = qc.State(n, dt).reset(0)
+    st.hall()  # Walsh-Hadamard passes at the largest size: the uniform start
     for _ in range(iters):
         st.grover_step(marked)
     a, b = closed(n, M, iters)
@@ -178,6 +179,11 @@ def test_maximum_size(qc, n, dt, tol, rel):
     st.cnot(0, n - 1)
     st.apply_1q(n - 1, H)
     assert np.max(np.abs(gather(st, idx) - got)) <= 4 * tol
+    # the QFT at the largest size (compiled passes, indices above 2^32)
+    # against its closed form
+    st.qft()
+    qidx = np.unique(np.concatenate([[0, 1, 2, (1 << 32) - 1, 1 << 32, N // 2, N - 1], g.integers(0, N, 500)]))
+    assert np.max(np.abs(gather(st, qidx) - qft_closed(n, marked, a, b, qidx))) <= 4 * tol
     st.close()
     del st
     torch.cuda.empty_cache()
