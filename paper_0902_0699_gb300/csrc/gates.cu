@@ -120,9 +120,19 @@ __device__ __forceinline__ uint64_t pair_base(uint64_t p, int p0, int p1, uint64
 // diagonal, anti-diagonal), which declare three (85 registers) -- the
 // launcher runs three per SM for complex128 anyway, and under 64 registers
 // they spill 100+ bytes.
+// complex128 Hadamard and exchange: eight pairs per loop trip (sixteen
+// 16-byte loads in flight per thread) on two blocks per SM.  Measured on one
+// box against four pairs on three blocks: H 5.455 against 5.53 ms, CNOT
+// 2.884 against 2.899 ms at 30 qubits; the phase kinds, which read only the
+// bit-1 half, ran slower that way (1.631 against 1.602 ms) and keep four.
+template <int KIND>
+struct PairWide {
+  static constexpr bool value = KIND == MK_HAD || KIND == MK_SWAPX;
+};
 template <typename R, int KIND>
 struct PairBlocks {
   static constexpr int value =
+      (sizeof(R) == 8 && PairWide<KIND>::value) ? 2 :
       (sizeof(R) == 8 && (KIND == MK_GENERAL || KIND == MK_DIAG || KIND == MK_ANTI)) ? 3 : 4;
 };
 template <typename R, int KIND, int NINS>
@@ -130,7 +140,7 @@ __global__ void __launch_bounds__(256, PairBlocks<R, KIND>::value)
     k_pairs(typename CT<R>::V2* __restrict__ s, uint64_t npairs, int p0, int p1, uint64_t setm, int t, GateArg<R> G) {
   using IO = AmpIO<R>;
   constexpr bool B1 = touches_bit1_only(KIND);
-  constexpr int UNR = sizeof(R) == 8 ? 4 : 2;
+  constexpr int UNR = sizeof(R) == 8 ? (PairWide<KIND>::value ? 8 : 4) : 2;
   const uint64_t st = 1ull << t;
   const uint64_t GS = (uint64_t)gridDim.x * blockDim.x;
   uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -246,7 +256,7 @@ static void launch_kind(qc_state* s, int nins, int p0, int p1, uint64_t setm, in
     }
   }
   auto k = (nins == 1) ? k_pairs<R, KIND, 1> : k_pairs<R, KIND, 2>;
-  unsigned g = resident_grid(k, T, npairs, (sizeof(R) == 8 ? 4 : 2) * T);
+  unsigned g = resident_grid(k, T, npairs, (sizeof(R) == 8 ? (PairWide<KIND>::value ? 8 : 4) : 2) * T);
   // complex128: three blocks per SM (24 warps, 96 16-byte loads in flight
   // per warp) stream best on GB300; a fourth adds DRAM contention (H: 0.92-
   // 0.95 of copy bandwidth with three, 0.89-0.91 with four).
