@@ -583,29 +583,52 @@ __device__ __forceinline__ void qft_stages_c128(ffc* sm, const ffc* LAD, int kl)
   }
 }
 
+// Between the passes of one transform the state holds each amplitude's
+// double-float parts (re.hi, re.lo, im.hi, im.lo: the same 16 bytes), so
+// only the first pass converts from IEEE double and only the last converts
+// back.
+__device__ __forceinline__ ffc ffc_unpack(double2 v) {
+  return ffc_make(ff_make(__int_as_float(__double2loint(v.x)), __int_as_float(__double2hiint(v.x))),
+                  ff_make(__int_as_float(__double2loint(v.y)), __int_as_float(__double2hiint(v.y))));
+}
+__device__ __forceinline__ double2 ffc_pack(ffc z) {
+  return make_double2(__hiloint2double(__float_as_int(z.re.lo), __float_as_int(z.re.hi)),
+                      __hiloint2double(__float_as_int(z.im.lo), __float_as_int(z.im.hi)));
+}
+
 template <int K>
 __global__ void __launch_bounds__(512, 2) k_qft_c128_k(double2* __restrict__ s, uint64_t ntiles, const TileProg<double> P,
                                                        const double2* __restrict__ tlo,
-                                                       const double2* __restrict__ thi) {
+                                                       const double2* __restrict__ thi, int ld_ff, int st_ff) {
   using A = TA<double>;
   constexpr int C = 12 - K, NE = 1 << 12, PER = NE / 512;
   static_assert(C <= 9, "512-element strides stay inside the group bits");
+  static_assert(PER == 8, "eight elements per thread");
   extern __shared__ __align__(16) unsigned char smraw[];
   ffc* sm = reinterpret_cast<ffc*>(smraw);
-  const int lo = P.lo;
+  const int lo = P.lo, hi = lo + K - 1, sh = P.n - hi - 1, nl = P.nl;
   const bool tw = P.twiddle != 0;
-  ffc* V = sm + NE;
-  ffc* LAD = V + (tw ? (1 << K) : 0);
+  ffc* LAD = sm + NE;
   constexpr int kl = lad_levels<double>(K);
-  ffc* TWA = LAD + lad_entries<double>(K);
-  ffc* TWB = TWA + TS_TWA;
+  for (int a = threadIdx.x; a < (1 << kl) - 1; a += blockDim.x) {
+    const int j = 31 - __clz(a + 1);
+    LAD[a] = A::root((uint64_t)(a + 1 - (1 << j)), j + 1);
+  }
+  if (K > kl && threadIdx.x == 0) LAD[(1 << kl) - 1] = A::root(1, K);
   const typename A::S sc = A::scale_const(K);
-  tile_tables<double>(P, LAD, TWA, TWB, kl);
   const int tid = threadIdx.x;
   const int st = tsw(tid);
   const uint64_t gstep = (uint64_t)(512 >> C) << lo;
+  const uint64_t hm = (2ull << hi) - 1ull;
+  // twiddle of element e = tid + 512 u: 2^{-K/2} Omega_{hi+1}^{m f} with
+  // m = its bits below lo (the tile's bits between C and lo, then the C low
+  // bits of tid: the same for all eight elements of a thread) and
+  // f = brev_K(e >> C) = F + brev_3(u), F = brev_K(tid >> C) (a multiple of
+  // 8).  So the eight twiddles are B g^v, v = brev_3(u), with
+  // B = 2^{-K/2} Omega^{m F} and g = Omega^m: two root-table lookups and a
+  // chain of seven products per thread instead of two products per element.
+  const int F = (int)(__brev((unsigned)(tid >> C)) >> (32 - K));
   for (uint64_t T = blockIdx.x; T < ntiles; T += gridDim.x) {
-    if (tw) tile_twiddle_v<double>(P, T, V, tlo, thi, sc);
     const uint64_t g0 = tile_global((uint64_t)tid, T, lo, K, C);
     // four 16-byte loads in flight per thread, twice
 #pragma unroll
@@ -614,23 +637,28 @@ __global__ void __launch_bounds__(512, 2) k_qft_c128_k(double2* __restrict__ s, 
 #pragma unroll
       for (int u = 0; u < 4; ++u) v[u] = s[g0 + (4 * h + u) * gstep];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) sm[st ^ tsw(512 * (4 * h + u))] = A::from(v[u]);
+      for (int u = 0; u < 4; ++u) sm[st ^ tsw(512 * (4 * h + u))] = ld_ff ? ffc_unpack(v[u]) : A::from(v[u]);
     }
     __syncthreads();
     qft_stages_c128<K, K - 1>(sm, LAD, kl);
     // store: the twiddle (which carries the 2^{-K/2} scale), or the scale
+    if (tw) {
+      const uint64_t m = ((T & ((1ull << (lo - C)) - 1ull)) << C) | (uint64_t)(tid & ((1 << C) - 1));
+      ffc W = A::scale_by(omega<double>(tlo, thi, ((m * (uint64_t)F) & hm) << sh, nl), sc);
+      const ffc g = omega<double>(tlo, thi, (m & hm) << sh, nl);
 #pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const int e = tid + 512 * u;
-      ffc z = sm[st ^ tsw(512 * u)];
-      if (tw) {
-        const int f = (int)(__brev((unsigned)(e >> C)) >> (32 - K));
-        const int x = (e & ((1 << C) - 1)) * f;  // < 2^12
-        z = A::mul(A::mul(V[f], A::mul(TWA[x & 127], TWB[x >> 7])), z);
-      } else {
-        z = A::scale_by(z, sc);
+      for (int v = 0; v < PER; ++v) {
+        const int u = ((v & 1) << 2) | (v & 2) | (v >> 2);  // brev_3(v)
+        const ffc z = A::mul(W, sm[st ^ tsw(512 * u)]);
+        s[g0 + u * gstep] = st_ff ? ffc_pack(z) : A::to(z);
+        if (v + 1 < PER) W = A::mul(W, g);
       }
-      s[g0 + u * gstep] = A::to(z);
+    } else {
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const ffc z = A::scale_by(sm[st ^ tsw(512 * u)], sc);
+        s[g0 + u * gstep] = st_ff ? ffc_pack(z) : A::to(z);
+      }
     }
     __syncthreads();
   }
@@ -1113,11 +1141,19 @@ static qc_status run_tile(qc_state* s, TileProg<R>& P, const typename CT<R>::V2*
 
 // complex128 QFT pass: the compiled kernel for 2^12-amplitude tiles, else
 // the general tile program.
-static qc_status run_qft_c128(qc_state* s, TileProg<double>& P, const double2* tlo, const double2* thi) {
+static bool qft_c128_compiled(const TileProg<double>& P) {
+  return P.k + P.c == 12 && P.scale_p == P.k && P.nops == P.k && ((P.k >= 3 && P.k <= 9) || P.k == 12);
+}
+
+// ld_ff / st_ff: the pass reads / leaves the double-float form (compiled
+// passes only; the transform's first pass reads and its last leaves IEEE
+// doubles).
+static qc_status run_qft_c128(qc_state* s, TileProg<double>& P, const double2* tlo, const double2* thi, bool ld_ff,
+                              bool st_ff) {
   P.n = s->n;
-  if (P.k + P.c == 12 && P.scale_p == P.k && P.nops == P.k) {
+  if (qft_c128_compiled(P)) {
     const uint64_t ntiles = 1ull << (s->n - 12);
-    const size_t smem = tile_smem<double>(P.k, P.c, P.twiddle != 0, true);
+    const size_t smem = sizeof(ffc) * (((size_t)1 << 12) + (size_t)lad_entries<double>(P.k));
     double2* d = reinterpret_cast<double2*>(s->data);
     switch (P.k) {
 #define QC_QFT_C128(KK)                                                                             \
@@ -1128,7 +1164,7 @@ static qc_status run_qft_c128(qc_state* s, TileProg<double>& P, const double2* t
       a = true;                                                                                     \
     }                                                                                               \
     const unsigned g = resident_grid(k_qft_c128_k<KK>, 512, (int64_t)ntiles, 1, smem);             \
-    k_qft_c128_k<KK><<<g, 512, smem, s->stream>>>(d, ntiles, P, tlo, thi);                          \
+    k_qft_c128_k<KK><<<g, 512, smem, s->stream>>>(d, ntiles, P, tlo, thi, ld_ff, st_ff);            \
     return check_launch("qft pass");                                                                \
   }
       QC_QFT_C128(3) QC_QFT_C128(4) QC_QFT_C128(5) QC_QFT_C128(6) QC_QFT_C128(7) QC_QFT_C128(8)
@@ -1137,6 +1173,7 @@ static qc_status run_qft_c128(qc_state* s, TileProg<double>& P, const double2* t
       default: break;
     }
   }
+  if (ld_ff || st_ff) return QC_EINVAL;
   return run_tile<double>(s, P, tlo, thi);
 }
 
@@ -1370,9 +1407,11 @@ static qc_status qft_impl(qc_state* s) {
   qc_status st = check_launch("qft roots");
   // complex64: groups of at most 9 above the lowest 13 (64 KiB tiles)
   std::vector<Group> groups = sizeof(R) == 4 ? plan_groups_k(n, 13, 9) : plan_groups<R>(n);
-  for (int gi = (int)groups.size() - 1; gi >= 0 && !st; --gi) {
+  std::vector<TileProg<R>> progs(groups.size());
+  bool all_compiled = true;  // complex128: double-float form between the passes
+  for (int gi = (int)groups.size() - 1; gi >= 0; --gi) {
     const Group& g = groups[gi];
-    TileProg<R> P;
+    TileProg<R>& P = progs[gi];
     prog_init(P, g, n);
     P.nl = nl;
     P.qft = 1;
@@ -1384,8 +1423,12 @@ static qc_status qft_impl(qc_state* s) {
     }
     P.scale_p = g.k;
     P.twiddle = g.lo > 0;
-    if constexpr (sizeof(R) == 4) st = run_qft_db_c64(s, P, tlo, thi);
-    else st = run_qft_c128(s, P, tlo, thi);
+    if constexpr (sizeof(R) == 8) all_compiled = all_compiled && qft_c128_compiled(P);
+  }
+  for (int gi = (int)groups.size() - 1; gi >= 0 && !st; --gi) {
+    if constexpr (sizeof(R) == 4) st = run_qft_db_c64(s, progs[gi], tlo, thi);
+    else
+      st = run_qft_c128(s, progs[gi], tlo, thi, all_compiled && gi + 1 < (int)groups.size(), all_compiled && gi > 0);
   }
   if (!st) st = bitrev_impl<R>(s);
   cudaFreeAsync(tab, s->stream);
