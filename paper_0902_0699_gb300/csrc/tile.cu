@@ -585,8 +585,8 @@ __device__ __forceinline__ void qft_stages_c128(ffc* sm, const ffc* LAD, int kl)
 
 // Between the passes of one transform the state holds each amplitude's
 // double-float parts (re.hi, re.lo, im.hi, im.lo: the same 16 bytes), so
-// only the first pass converts from IEEE double and only the last converts
-// back.
+// only the first pass converts from IEEE double, and the bit reversal that
+// ends the transform converts back.
 __device__ __forceinline__ ffc ffc_unpack(double2 v) {
   return ffc_make(ff_make(__int_as_float(__double2loint(v.x)), __int_as_float(__double2hiint(v.x))),
                   ff_make(__int_as_float(__double2loint(v.y)), __int_as_float(__double2hiint(v.y))));
@@ -1146,8 +1146,8 @@ static bool qft_c128_compiled(const TileProg<double>& P) {
 }
 
 // ld_ff / st_ff: the pass reads / leaves the double-float form (compiled
-// passes only; the transform's first pass reads and its last leaves IEEE
-// doubles).
+// passes only; the transform's first pass reads IEEE doubles, and the bit
+// reversal after its last pass converts back).
 static qc_status run_qft_c128(qc_state* s, TileProg<double>& P, const double2* tlo, const double2* thi, bool ld_ff,
                               bool st_ff) {
   P.n = s->n;
@@ -1310,9 +1310,22 @@ qc_status launch_hall(qc_state* s) {
 // with 128 threads (twelve blocks per SM; 0.76 of copy bandwidth on GB300
 // at 30 qubits, against 0.63 for B = 5 with 256 threads); complex64 keeps
 // B = 5 with 256 threads (rows of 256 bytes).
-template <typename R, int B, int T>
+template <typename V2, bool FF>
+__device__ __forceinline__ V2 bitrev_out(V2 v) {
+  if constexpr (FF) {
+    const ffc z = ffc_unpack(v);
+    return make_double2(ff_to_d(z.re), ff_to_d(z.im));
+  } else {
+    return v;
+  }
+}
+
+// FF (complex128 only): the input holds double-float parts (the form the
+// compiled QFT passes leave) and is converted to IEEE double on the way.
+template <typename R, int B, int T, bool FF = false>
 __global__ void __launch_bounds__(T) k_bitrev(typename CT<R>::V2* __restrict__ s, int n) {
   using V2 = typename CT<R>::V2;
+  static_assert(!FF || sizeof(R) == 8, "double-float input is complex128");
   constexpr int W = 1 << B, WP = W + 1, PER = W * W / T;
   static_assert(PER * T == W * W, "whole tiles per block");
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -1347,10 +1360,10 @@ __global__ void __launch_bounds__(T) k_bitrev(typename CT<R>::V2* __restrict__ s
       const int rl = (int)(__brev((unsigned)l) >> (32 - B)), rh = (int)(__brev((unsigned)h) >> (32 - B));
       // element (h, m, l) of the output is the input at rev(h, m, l)
       if (mr != m) {
-        s[((uint64_t)h << (n - B)) | (m << B) | (uint64_t)l] = Bt[rl * WP + rh];
-        s[((uint64_t)h << (n - B)) | (mr << B) | (uint64_t)l] = A[rl * WP + rh];
+        s[((uint64_t)h << (n - B)) | (m << B) | (uint64_t)l] = bitrev_out<V2, FF>(Bt[rl * WP + rh]);
+        s[((uint64_t)h << (n - B)) | (mr << B) | (uint64_t)l] = bitrev_out<V2, FF>(A[rl * WP + rh]);
       } else {
-        s[((uint64_t)h << (n - B)) | (m << B) | (uint64_t)l] = A[rl * WP + rh];
+        s[((uint64_t)h << (n - B)) | (m << B) | (uint64_t)l] = bitrev_out<V2, FF>(A[rl * WP + rh]);
       }
     }
     __syncthreads();
@@ -1373,17 +1386,26 @@ __global__ void k_bitrev_small(typename CT<R>::V2* __restrict__ s, int n) {
 }
 
 template <typename R>
-static qc_status bitrev_impl(qc_state* s) {
+static qc_status bitrev_impl(qc_state* s, bool from_ff = false) {
   using V2 = typename CT<R>::V2;
   V2* d = reinterpret_cast<V2*>(s->data);
   const int n = s->n;
   constexpr int b = sizeof(R) == 8 ? 4 : 5, T = sizeof(R) == 8 ? 128 : 256;
   if (n < 2 * b) {
+    if (from_ff) return QC_EINVAL;
     k_bitrev_small<R><<<1, 256, sizeof(V2) << n, s->stream>>>(d, n);
     return check_launch("bitrev small");
   }
   const size_t smem = 2 * (size_t)(1 << b) * ((1 << b) + 1) * sizeof(V2);
   const uint64_t M = 1ull << (n - 2 * b);
+  if constexpr (sizeof(R) == 8) {
+    if (from_ff) {
+      const unsigned grid = resident_grid(k_bitrev<R, b, T, true>, T, (int64_t)M, 1, smem);
+      k_bitrev<R, b, T, true><<<grid, T, smem, s->stream>>>(d, n);
+      return check_launch("bitrev");
+    }
+  }
+  if (from_ff) return QC_EINVAL;
   const unsigned grid = resident_grid(k_bitrev<R, b, T>, T, (int64_t)M, 1, smem);
   k_bitrev<R, b, T><<<grid, T, smem, s->stream>>>(d, n);
   return check_launch("bitrev");
@@ -1428,9 +1450,10 @@ static qc_status qft_impl(qc_state* s) {
   for (int gi = (int)groups.size() - 1; gi >= 0 && !st; --gi) {
     if constexpr (sizeof(R) == 4) st = run_qft_db_c64(s, progs[gi], tlo, thi);
     else
-      st = run_qft_c128(s, progs[gi], tlo, thi, all_compiled && gi + 1 < (int)groups.size(), all_compiled && gi > 0);
+      st = run_qft_c128(s, progs[gi], tlo, thi, all_compiled && gi + 1 < (int)groups.size(), all_compiled);
   }
-  if (!st) st = bitrev_impl<R>(s);
+  // the bit reversal converts the complex128 passes' double-float form back
+  if (!st) st = bitrev_impl<R>(s, sizeof(R) == 8 && all_compiled);
   cudaFreeAsync(tab, s->stream);
   return st;
 }
