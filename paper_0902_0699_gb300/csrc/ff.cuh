@@ -117,7 +117,7 @@ FF_HD uint64_t ff_f2dbits(float x) {
 
 // double -> (hi, lo): hi = d truncated to 24 significant bits, lo = the
 // remaining (up to 29) bits rounded to a float.  |d - (hi + lo)| <= 2^-47 |d|
-// for 2^-75 < |d| < 2^128; smaller magnitudes lose only absolute 2^-98.
+// for 2^-74 <= |d| < 2^128; smaller magnitudes lose only absolute 2^-98.
 FF_HD ff ff_from_d(double d) {
   const uint64_t b = ff_dbits(d);
   const uint32_t E = (uint32_t)((b >> 52) & 0x7FFu);
@@ -156,6 +156,57 @@ FF_HD double ff_to_d(ff x) {
   // where one unit of the pattern is half as large
   if ((hb & 0x000FFFFFFFFFFFFFull) == 0 && m < 0) m *= 2;
   return ff_bitsd(hb + (uint64_t)m);
+}
+
+// Integer-lean conversions for the arithmetic-bound kernels (the general
+// one-qubit operator, the QFT passes' conversions): about half the integer
+// operations of ff_from_d / ff_to_d and no int-to-float conversion.  The
+// streaming kernels (Hadamard, real operators, the Grover pass) keep the
+// forms above, which measured faster there.
+//
+// double -> (hi, lo): hi = d truncated to 24 significant bits; lo = the
+// remaining 29 bits rounded (half up) to a multiple of 2^6 of d's last unit,
+// formed without an int-to-float conversion: the float 2^(E-1046)(1 + k/2^23)
+// minus 2^(E-1046) is exactly k 2^(E-1069) (E = d's biased exponent; k <= 2^23,
+// where the carry into the exponent gives the same difference).
+// |d - (hi + lo)| <= 2^-47 |d| and |lo| <= ulp(hi) for 2^-103 <= |d| < 2^128;
+// smaller magnitudes map to zero (an absolute error below 1e-31).
+FF_HD ff ff_from_d_fast(double d) {
+  const uint64_t b = ff_dbits(d);
+  const uint32_t bh = (uint32_t)(b >> 32), bl = (uint32_t)b;
+  ff r;
+  if ((bh & 0x7FF00000u) < (920u << 20)) {
+    r.hi = 0.f;
+    r.lo = 0.f;
+    return r;
+  }
+  // sign, exponent re-biased from 1023 to 127 (subtracting 896 from the
+  // field), mantissa bits 51..29
+  const uint32_t hb = (bh & 0x80000000u) | (((uint32_t)(b >> 29) - (896u << 23)) & 0x7FFFFFFFu);
+  const uint32_t eb = (hb & 0xFF800000u) - (23u << 23);  // sign | exponent field of 2^(E-1046)
+  const uint32_t k = ((bl & 0x1FFFFFFFu) + 32u) >> 6;
+  r.hi = ff_bitsf(hb);
+  r.lo = ff_sub_rn(ff_bitsf(eb + k), ff_bitsf(eb));
+  return r;
+}
+
+// (hi, lo) with |lo| <= ulp(hi) -> the double nearest hi + lo (within one
+// unit in the last place): hi's binary64 pattern (exponent field + 896,
+// mantissa << 29) plus lo in units of ulp_53(hi).  |hi| below 2^-75 (where
+// that unit leaves float's range), zero included: the larger part alone.
+FF_HD double ff_to_d_fast(ff x) {
+  const uint32_t hb = ff_fbits(x.hi);
+  const uint32_t ef = hb & 0x7F800000u;
+  if (ef < (52u << 23)) return ff_bitsd(ff_f2dbits(ef ? x.hi : x.lo));
+  const uint32_t dh = (hb & 0x80000000u) | (((hb & 0x7FFFFFFFu) >> 3) + (896u << 20));
+  const uint32_t dl = hb << 29;
+  const float t = ff_mul_rn(x.lo, ff_bitsf((306u << 23) - ef));  // lo / 2^(e_hi - 52), exact
+  int m = ff_rint(t);
+  if (hb >> 31) m = -m;  // magnitude units
+  // a power of two whose magnitude decreases lands in the binade below,
+  // where one unit of the pattern is half as large
+  if ((hb & 0x7FFFFFu) == 0 && m < 0) m *= 2;
+  return ff_bitsd((((uint64_t)dh << 32) | dl) + (uint64_t)(int64_t)m);
 }
 
 // Knuth two-sum: s + e == a + b exactly.

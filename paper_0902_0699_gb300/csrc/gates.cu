@@ -35,19 +35,23 @@ template <> struct GateArg<double> {
 // read+write pass takes at 0.8 of HBM), the rest in double-float on the FP32
 // pipe.  The FP64 part is one output component (general: Re b0) or the
 // real parts (real operators) or one output (diagonal, anti-diagonal).
+// The real part of the first output on the FP64 pipe, the other three as
+// four-term double-float dots, with the integer-lean conversions (the kernel
+// is bound by issue, not by memory).
 __device__ __forceinline__ void apply_general_c128(const GateArg<double>& G, Cx<double>& a0, Cx<double>& a1) {
   const Mat2<double>& U = G.U;
   double r0 = U.m[0].re * a0.re;
   r0 = fma(-U.m[0].im, a0.im, r0);
   r0 = fma(U.m[1].re, a1.re, r0);
   r0 = fma(-U.m[1].im, a1.im, r0);
-  const ff x0r = ff_from_d(a0.re), x0i = ff_from_d(a0.im), x1r = ff_from_d(a1.re), x1i = ff_from_d(a1.im);
+  const ff x0r = ff_from_d_fast(a0.re), x0i = ff_from_d_fast(a0.im);
+  const ff x1r = ff_from_d_fast(a1.re), x1i = ff_from_d_fast(a1.im);
   const Mat2ff& F = G.F;
   const ff i0 = ff_dot4(F.m[0].re, x0i, F.m[0].im, x0r, F.m[1].re, x1i, F.m[1].im, x1r);
   const ff r1 = ff_dot4(F.m[2].re, x0r, ff_neg(F.m[2].im), x0i, F.m[3].re, x1r, ff_neg(F.m[3].im), x1i);
   const ff i1 = ff_dot4(F.m[2].re, x0i, F.m[2].im, x0r, F.m[3].re, x1i, F.m[3].im, x1r);
-  a0 = cmake<double>(r0, ff_to_d(i0));
-  a1 = cmake<double>(ff_to_d(r1), ff_to_d(i1));
+  a0 = cmake<double>(r0, ff_to_d_fast(i0));
+  a1 = cmake<double>(ff_to_d_fast(r1), ff_to_d_fast(i1));
 }
 __device__ __forceinline__ void apply_real_c128(const GateArg<double>& G, Cx<double>& a0, Cx<double>& a1) {
   const double u00 = G.U.m[0].re, u01 = G.U.m[1].re, u10 = G.U.m[2].re, u11 = G.U.m[3].re;
@@ -116,10 +120,16 @@ __device__ __forceinline__ uint64_t pair_base(uint64_t p, int p0, int p1, uint64
 // streams at 0.93-0.95 of copy bandwidth on GB300, without it at 0.82-0.86
 // (same register count, different schedule).
 // Register budget: four blocks per SM (64 registers), except the complex128
-// kinds whose products are split between FP64 and double-float (general,
-// diagonal, anti-diagonal), which declare three (85 registers) -- the
-// launcher runs three per SM for complex128 anyway, and under 64 registers
-// they spill 100+ bytes.
+// diagonal and anti-diagonal kinds, whose products are split between FP64
+// and double-float and which declare three (85 registers) -- the launcher
+// runs three per SM for complex128 anyway, and under 64 registers they spill
+// 100+ bytes.
+// complex128 general operator: two pairs per loop trip on four blocks per SM
+// (issue bound: more warps, fewer registers).  With the integer-lean
+// conversions, measured on one box at 30 qubits: 5.90 ms per gate, 0.859 of
+// the measured copy bandwidth, against 7.27 ms (0.697) with four pairs on
+// three blocks and the general conversions; with four pairs on three blocks
+// and the lean conversions 7.11 ms.
 // complex128 Hadamard and exchange: eight pairs per loop trip (sixteen
 // 16-byte loads in flight per thread) on two blocks per SM.  Measured on one
 // box against four pairs on three blocks: H 5.455 against 5.53 ms, CNOT
@@ -130,17 +140,22 @@ struct PairWide {
   static constexpr bool value = KIND == MK_HAD || KIND == MK_SWAPX;
 };
 template <typename R, int KIND>
+struct PairUnroll {
+  static constexpr int value =
+      sizeof(R) == 8 ? (PairWide<KIND>::value ? 8 : (KIND == MK_GENERAL ? 2 : 4)) : 2;
+};
+template <typename R, int KIND>
 struct PairBlocks {
   static constexpr int value =
       (sizeof(R) == 8 && PairWide<KIND>::value) ? 2 :
-      (sizeof(R) == 8 && (KIND == MK_GENERAL || KIND == MK_DIAG || KIND == MK_ANTI)) ? 3 : 4;
+      (sizeof(R) == 8 && (KIND == MK_DIAG || KIND == MK_ANTI)) ? 3 : 4;
 };
 template <typename R, int KIND, int NINS>
 __global__ void __launch_bounds__(256, PairBlocks<R, KIND>::value)
     k_pairs(typename CT<R>::V2* __restrict__ s, uint64_t npairs, int p0, int p1, uint64_t setm, int t, GateArg<R> G) {
   using IO = AmpIO<R>;
   constexpr bool B1 = touches_bit1_only(KIND);
-  constexpr int UNR = sizeof(R) == 8 ? (PairWide<KIND>::value ? 8 : 4) : 2;
+  constexpr int UNR = PairUnroll<R, KIND>::value;
   const uint64_t st = 1ull << t;
   const uint64_t GS = (uint64_t)gridDim.x * blockDim.x;
   uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -256,11 +271,11 @@ static void launch_kind(qc_state* s, int nins, int p0, int p1, uint64_t setm, in
     }
   }
   auto k = (nins == 1) ? k_pairs<R, KIND, 1> : k_pairs<R, KIND, 2>;
-  unsigned g = resident_grid(k, T, npairs, (sizeof(R) == 8 ? (PairWide<KIND>::value ? 8 : 4) : 2) * T);
+  unsigned g = resident_grid(k, T, npairs, PairUnroll<R, KIND>::value * T);
   // complex128: three blocks per SM (24 warps, 96 16-byte loads in flight
   // per warp) stream best on GB300; a fourth adds DRAM contention (H: 0.92-
   // 0.95 of copy bandwidth with three, 0.89-0.91 with four).
-  if (sizeof(R) == 8) g = std::min<unsigned>(g, 3u * (unsigned)sm_count());
+  if (sizeof(R) == 8) g = std::min<unsigned>(g, (KIND == MK_GENERAL ? 4u : 3u) * (unsigned)sm_count());
   k<<<g, T, 0, s->stream>>>(d, npairs, p0, p1, setm, t, G);
 }
 

@@ -637,7 +637,9 @@ __global__ void __launch_bounds__(512, 2) k_qft_c128_k(double2* __restrict__ s, 
 #pragma unroll
       for (int u = 0; u < 4; ++u) v[u] = s[g0 + (4 * h + u) * gstep];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) sm[st ^ tsw(512 * (4 * h + u))] = ld_ff ? ffc_unpack(v[u]) : A::from(v[u]);
+      for (int u = 0; u < 4; ++u)
+        sm[st ^ tsw(512 * (4 * h + u))] =
+            ld_ff ? ffc_unpack(v[u]) : ffc_make(ff_from_d_fast(v[u].x), ff_from_d_fast(v[u].y));
     }
     __syncthreads();
     qft_stages_c128<K, K - 1>(sm, LAD, kl);
@@ -1314,7 +1316,7 @@ template <typename V2, bool FF>
 __device__ __forceinline__ V2 bitrev_out(V2 v) {
   if constexpr (FF) {
     const ffc z = ffc_unpack(v);
-    return make_double2(ff_to_d(z.re), ff_to_d(z.im));
+    return make_double2(ff_to_d_fast(z.re), ff_to_d_fast(z.im));
   } else {
     return v;
   }

@@ -1,6 +1,7 @@
 // Host-side check of the double-float layer the complex128 kernels use
 // (paper_0902_0699_gb300/csrc/ff.cuh compiled as plain C++): conversions
-// double <-> (hi, lo) and the ff arithmetic against long double references.
+// double <-> (hi, lo) (both conversion pairs) and the ff arithmetic against
+// long double references.
 // Prints "ok" and exits 0, or prints the first failure and exits 1.
 #include <cmath>
 #include <cstdio>
@@ -16,6 +17,65 @@ static long double val(ff x) { return (long double)x.hi + (long double)x.lo; }
 static int fail(const char* what, double a, double b, long double err) {
   printf("FAIL %s: a=%.17g b=%.17g err=%Lg\n", what, a, b, err);
   return 1;
+}
+
+// The conversions' stated bounds: |d - (hi + lo)| <= 2^-47 |d| and
+// |lo| <= ulp(hi) for 2^-103 <= |d| < 2^128 (2^-74 for the general form;
+// the lean form maps smaller magnitudes to zero), including low words that round up into the next
+// power of two; and the join of any (hi, lo) with |lo| <= ulp(hi) within one
+// unit of hi + lo.
+template <typename FROM, typename TO>
+static int conversion_bounds(FROM from_d, TO to_d, bool zero_below, std::mt19937_64& rng) {
+  std::uniform_int_distribution<uint64_t> M(0, (1ull << 52) - 1);
+  std::uniform_int_distribution<int> EX(-103, 127);
+  for (int i = 0; i < 3000000; ++i) {
+    uint64_t mant = M(rng);
+    if (i % 4 == 1) mant |= (1ull << 29) - 1 - (i & 31);  // low word at the top of its range
+    if (i % 4 == 2) mant &= ~((1ull << 29) - 1);          // low word zero
+    const double d = std::ldexp(1.0 + std::ldexp((double)mant, -52), EX(rng)) * ((i & 8) ? -1.0 : 1.0);
+    const ff f = from_d(d);
+    const long double err = std::fabs(val(f) - (long double)d);
+    // the general form keeps the relative bound from 2^-74 up (below it the
+    // low word is dropped: an absolute error under 2^-98)
+    const long double fb = (zero_below || std::fabs(d) >= std::ldexp(1.0, -74)) ? std::ldexp(std::fabs((long double)d), -47)
+                                                                                 : std::ldexp((long double)1, -98);
+    if (err > fb) return fail("from_d 2^-47", d, 0, err);
+    const float uh = std::ldexp(1.0f, std::ilogb(f.hi) - 23);
+    if (std::fabs(f.lo) > uh) return fail("from_d |lo| <= ulp(hi)", d, 0, f.lo);
+    if ((f.hi < 0) != (d < 0) || (f.lo != 0 && (f.lo < 0) != (d < 0))) return fail("from_d sign", d, 0, 0);
+    // the join keeps the low word for |hi| >= 2^-75 (below: hi alone, an
+    // absolute error under 2^-98; the general split keeps it from 2^-74)
+    const double back = to_d(f);
+    const double rt = std::fabs(d) >= std::ldexp(1.0, -74) ? std::ldexp(std::fabs(d), -47) : std::ldexp(1.0, -98);
+    if (std::fabs(back - d) > rt) return fail("round trip 2^-47", d, back, back - d);
+  }
+  if (zero_below)
+    for (double d : {std::ldexp(1.0, -104), -std::ldexp(1.7, -110), 1e-300}) {
+      const ff f = from_d(d);
+      if (f.hi != 0.f || f.lo != 0.f) return fail("below 2^-103", d, 0, f.hi);
+    }
+  std::uniform_real_distribution<float> UF(-1.0f, 1.0f);
+  for (int i = 0; i < 3000000; ++i) {
+    const float hi = std::ldexp(1.0f + std::fabs(UF(rng)), EX(rng) / 2) * ((i & 1) ? -1.f : 1.f);
+    const float lo = UF(rng) * std::ldexp(1.0f, std::ilogb(hi) - 23);
+    const long double want = (long double)hi + (long double)lo;
+    const double got = to_d(ff_make(hi, lo));
+    const long double ulp = std::ldexp((long double)1, std::ilogb((double)want) - 52);
+    if (std::fabs((long double)got - want) > ulp) return fail("join", (double)want, got, got - want);
+  }
+  // exact edges and the binade below a power of two
+  for (double d : {0.0, -0.0, 1.0, -1.0, 0.5, 0.7071067811865476, -0.7071067811865476, 1e-30}) {
+    const double b = to_d(from_d(d));
+    if (std::fabs(b - d) > std::fmax(std::ldexp(std::fabs(d), -46), std::ldexp(1.0, -97))) return fail("edge", d, b, b - d);
+  }
+  for (int e = -40; e <= 4; ++e)
+    for (int k = 1; k < 1000; ++k) {
+      const float hi = std::ldexp(1.0f, e), lo = -std::ldexp((float)k, e - 34);
+      const double want = (double)hi + (double)lo;
+      if (std::fabs(to_d(ff_make(hi, lo)) - want) > std::ldexp(1.0, e - 52)) return fail("binade", want, 0, 0);
+      if (std::fabs(to_d(ff_make(-hi, -lo)) + want) > std::ldexp(1.0, e - 52)) return fail("binade neg", -want, 0, 0);
+    }
+  return 0;
 }
 
 int main() {
@@ -99,6 +159,9 @@ int main() {
     if (std::fabs(R4.lo) > std::fabs(R4.hi) * std::ldexp(1.0, -23) + std::ldexp(s4, -70))
       return fail("dot4 norm", a, c, R4.lo);
   }
+  // 5. the stated conversion bounds, for both conversion pairs
+  if (conversion_bounds(ff_from_d, ff_to_d, false, rng)) return 1;
+  if (conversion_bounds(ff_from_d_fast, ff_to_d_fast, true, rng)) return 1;
   printf("ok\n");
   return 0;
 }
