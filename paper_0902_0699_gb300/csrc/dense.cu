@@ -17,7 +17,7 @@
 // two of which sum integers exactly, so no product or partial sum is
 // rounded toward zero and the result keeps FP32-level accuracy without
 // drift.  Other k and complex128 run on CUDA cores (complex128 in
-// double-float).
+// double-float; k <= 3 in the compiled one-thread-per-group kernel).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -119,6 +119,65 @@ __global__ void __launch_bounds__(DENSE_T) k_dense(typename DenseT<R>::V* __rest
       for (int lp = 0; lp < dim; ++lp) D::mac(acc, Us[lp * dim + l], xr[lp]);
       D::store(psi, group_base(g0 + gi, M) | M.offs[l], acc);
     }
+  }
+}
+
+// complex128 blocks of K <= 3 qubits, compiled per K, one thread per group:
+// the thread loads its group's 2^K amplitudes (integer-lean conversions),
+// runs all 2^{K+1} output components as running dots at once (ffacc: one
+// renormalisation per four terms instead of one per complex multiply-add;
+// 2^{K+1} independent chains), and writes the group back.  The operator, as
+// double-float, sits in shared memory, and every lane of a warp reads the
+// same entry (a broadcast).  Measured on the 24-qubit, 200-layer random
+// circuit fused into 1108 three-qubit blocks: 403.7 ms, against 559.8 ms with
+// k_dense (runtime loop, a renormalisation per term) and 472 ms with one
+// output per thread (fewer independent chains).
+template <int K>
+__global__ void __launch_bounds__(DENSE_T, K == 3 ? 2 : 3) k_dense_grp(double2* __restrict__ psi, uint64_t ngroups,
+                                                    const double* __restrict__ U, DenseMap M) {
+  constexpr int DIM = 1 << K;
+  __shared__ ffc Us[DIM * DIM];  // row-major: Us[l DIM + l'] = U[l][l']
+  for (int e = threadIdx.x; e < DIM * DIM; e += blockDim.x)
+    Us[e] = ffc_make(ff_from_d_fast(U[2 * e]), ff_from_d_fast(U[2 * e + 1]));
+  __syncthreads();
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
+       g += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t base = group_base(g, M);
+    ffc x[DIM];
+    {
+      double2 v[DIM];
+#pragma unroll
+      for (int lp = 0; lp < DIM; ++lp) v[lp] = psi[base | M.offs[lp]];
+#pragma unroll
+      for (int lp = 0; lp < DIM; ++lp) x[lp] = ffc_make(ff_from_d_fast(v[lp].x), ff_from_d_fast(v[lp].y));
+    }
+    ffacc re[DIM], im[DIM];
+#pragma unroll
+    for (int l = 0; l < DIM; ++l) {
+      const ffc u = Us[l * DIM];
+      re[l] = ffacc_first(u.re, x[0].re);
+      im[l] = ffacc_first(u.re, x[0].im);
+      ffacc_add(re[l], ff_neg(u.im), x[0].im);
+      ffacc_add(im[l], u.im, x[0].re);
+    }
+#pragma unroll
+    for (int lp = 1; lp < DIM; ++lp) {
+#pragma unroll
+      for (int l = 0; l < DIM; ++l) {
+        const ffc u = Us[l * DIM + lp];
+        ffacc_add(re[l], u.re, x[lp].re);
+        ffacc_add(re[l], ff_neg(u.im), x[lp].im);
+        ffacc_add(im[l], u.re, x[lp].im);
+        ffacc_add(im[l], u.im, x[lp].re);
+        if (lp & 1) {  // four terms per component since the last
+          ffacc_norm(re[l]);
+          ffacc_norm(im[l]);
+        }
+      }
+    }
+#pragma unroll
+    for (int l = 0; l < DIM; ++l)
+      psi[base | M.offs[l]] = make_double2(ff_to_d_fast(ffacc_result(re[l])), ff_to_d_fast(ffacc_result(im[l])));
   }
 }
 
@@ -564,6 +623,19 @@ qc_status dense_launch(qc_state* s, const DenseMap& M, const void* dev_op, int* 
     const unsigned grid = resident_grid(k_dense<float>, DENSE_T, (int64_t)((ngroups + G - 1) / G), 1, smem);
     k_dense<float><<<grid, DENSE_T, smem, s->stream>>>(reinterpret_cast<float2*>(s->data), ngroups,
                                                     reinterpret_cast<const double*>(dev_op), M);
+  } else if (k <= 3) {
+    double2* d = reinterpret_cast<double2*>(s->data);
+    const double* op = reinterpret_cast<const double*>(dev_op);
+    switch (k) {
+#define QC_DENSE_GRP(KK)                                                                    \
+  case KK: {                                                                                \
+    const unsigned grid = resident_grid(k_dense_grp<KK>, DENSE_T, (int64_t)ngroups, DENSE_T); \
+    k_dense_grp<KK><<<grid, DENSE_T, 0, s->stream>>>(d, ngroups, op, M);                      \
+    break;                                                                                  \
+  }
+      QC_DENSE_GRP(1) QC_DENSE_GRP(2) QC_DENSE_GRP(3)
+#undef QC_DENSE_GRP
+    }
   } else {
     const size_t smem = sizeof(ffc) * ((size_t)dim * dim + DENSE_AMPS);
     static bool attr = false;

@@ -159,7 +159,28 @@ int main() {
     if (std::fabs(R4.lo) > std::fabs(R4.hi) * std::ldexp(1.0, -23) + std::ldexp(s4, -70))
       return fail("dot4 norm", a, c, R4.lo);
   }
-  // 5. the stated conversion bounds, for both conversion pairs
+  // 5. running dots of up to 64 terms, renormalised after every fourth (the
+  // dense blocks' accumulation): within 2^-43 of sum |a_i b_i|
+  for (int i = 0; i < 200000; ++i) {
+    const int nt = 1 + (i % 64);
+    double a[64], b[64];
+    long double ref = 0, mag = 0;
+    ffacc A{};
+    for (int j = 0; j < nt; ++j) {
+      a[j] = std::ldexp(U(rng), X(rng) / 8);
+      b[j] = std::ldexp(U(rng), X(rng) / 8);
+      ref += (long double)a[j] * b[j];
+      mag += std::fabs((long double)a[j] * b[j]);
+      if (j == 0) A = ffacc_first(ff_from_d(a[j]), ff_from_d(b[j]));
+      else ffacc_add(A, ff_from_d(a[j]), ff_from_d(b[j]));
+      if ((j & 3) == 3) ffacc_norm(A);
+    }
+    const ff r = ffacc_result(A);
+    const long double err = std::fabs(val(r) - ref);
+    if (err > std::ldexp(mag, -43)) return fail("dot acc", a[0], (double)nt, err);
+    if (std::fabs(r.lo) > std::fabs(r.hi) * std::ldexp(1.0, -23) + std::ldexp(mag, -70)) return fail("dot acc norm", a[0], nt, r.lo);
+  }
+  // 6. the stated conversion bounds, for both conversion pairs
   if (conversion_bounds(ff_from_d, ff_to_d, false, rng)) return 1;
   if (conversion_bounds(ff_from_d_fast, ff_to_d_fast, true, rng)) return 1;
   printf("ok\n");
