@@ -277,8 +277,11 @@ inline Mat2ff mat2ff_from_host(const double* U) {
 template <int KIND>
 __device__ __forceinline__ void apply2_ff(const Mat2ff& U, ffc& a0, ffc& a1) {
   if (KIND == MK_GENERAL) {
-    const ffc b0 = ffc_mul2(U.m[0], a0, U.m[1], a1);
-    a1 = ffc_mul2(U.m[2], a0, U.m[3], a1);
+    // each output component as one four-term dot (one renormalisation)
+    const ffc b0 = ffc_make(ff_dot4(U.m[0].re, a0.re, ff_neg(U.m[0].im), a0.im, U.m[1].re, a1.re, ff_neg(U.m[1].im), a1.im),
+                            ff_dot4(U.m[0].re, a0.im, U.m[0].im, a0.re, U.m[1].re, a1.im, U.m[1].im, a1.re));
+    a1 = ffc_make(ff_dot4(U.m[2].re, a0.re, ff_neg(U.m[2].im), a0.im, U.m[3].re, a1.re, ff_neg(U.m[3].im), a1.im),
+                  ff_dot4(U.m[2].re, a0.im, U.m[2].im, a0.re, U.m[3].re, a1.im, U.m[3].im, a1.re));
     a0 = b0;
   } else if (KIND == MK_REAL) {
     const ffc b0 = ffc_make(ff_dot2p(U.m[0].re, a0.re, U.m[1].re, a1.re), ff_dot2p(U.m[0].re, a0.im, U.m[1].re, a1.im));

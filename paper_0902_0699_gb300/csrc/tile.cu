@@ -91,8 +91,9 @@ template <> struct TA<double> {
   using V2 = double2;
   using M = Mat2ff;
   static M mat(const double* U) { return mat2ff_from_host(U); }
-  __device__ static E from(V2 v) { return ffc_from_d(v.x, v.y); }
-  __device__ static V2 to(E z) { return make_double2(ff_to_d(z.re), ff_to_d(z.im)); }
+  // the tile passes are arithmetic bound: the integer-lean conversions
+  __device__ static E from(V2 v) { return ffc_make(ff_from_d_fast(v.x), ff_from_d_fast(v.y)); }
+  __device__ static V2 to(E z) { return make_double2(ff_to_d_fast(z.re), ff_to_d_fast(z.im)); }
   __device__ static E add(E a, E b) { return ffc_add(a, b); }
   __device__ static E sub(E a, E b) { return ffc_sub(a, b); }
   // first level of a radix-4 step: its sums feed the second level's adds
