@@ -175,7 +175,10 @@ qc_status qc_grover_apply_mean(qc_state* s, const uint64_t* marked, int n_marked
 /* Quantum Fourier transform (Appendix A): the Hadamard / CPHASEK ladder
  * followed by the qubit-order reversal swaps, i.e.
  *   C~_{n'} = 2^{-n/2} sum_n e^{+2 pi i n n' / 2^n} C_n.
- * Runs as fused tile passes plus one in-place bit-reversal pass. */
+ * Runs as fused tile passes plus one in-place bit-reversal pass.  For
+ * complex128 the buffer holds an internal double-float form between those
+ * passes, so a CUDA failure in the middle (QC_ECUDA) leaves the state's
+ * contents undefined. */
 qc_status qc_qft(qc_state* s);
 
 /* General two-qubit operator, TwoOpA (Eq. resmat2, Eq. twoopB): for every
