@@ -33,11 +33,26 @@ __device__ __forceinline__ ffc load_ffc(const float2* p, uint64_t i) {
   const float2 v = p[i];
   return ffc_make(ff_make(v.x, 0.f), ff_make(v.y, 0.f));
 }
-__device__ __forceinline__ void store_ffc(double2* p, uint64_t i, const ffc& z) {
-  p[i] = make_double2(ff_to_d(z.re), ff_to_d(z.im));
+template <typename V2> __device__ __forceinline__ V2 ffc_to_v2(const ffc& z);
+template <> __device__ __forceinline__ double2 ffc_to_v2<double2>(const ffc& z) {
+  return make_double2(ff_to_d(z.re), ff_to_d(z.im));
 }
-__device__ __forceinline__ void store_ffc(float2* p, uint64_t i, const ffc& z) {
-  p[i] = make_float2(z.re.hi + z.re.lo, z.im.hi + z.im.lo);
+template <> __device__ __forceinline__ float2 ffc_to_v2<float2>(const ffc& z) {
+  return make_float2(z.re.hi + z.re.lo, z.im.hi + z.im.lo);
+}
+__device__ __forceinline__ double2 conj_v(double2 v) { return make_double2(v.x, -v.y); }
+__device__ __forceinline__ float2 conj_v(float2 v) { return make_float2(v.x, -v.y); }
+
+// rho is Hermitian: only tiles on and above the diagonal are formed, and an
+// off-diagonal tile's conjugate transpose goes through shared memory (Tm) to
+// the mirrored tile in coalesced rows.
+template <typename V2>
+__device__ __forceinline__ void rho_mirror(V2 (*Tm)[33], V2* __restrict__ rho, uint64_t N, uint64_t r0, uint64_t c0) {
+  __syncthreads();
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int rr = e >> 5, cc = e & 31;
+    if (c0 + rr < N && r0 + cc < N) rho[(c0 + rr) * N + r0 + cc] = Tm[rr][cc];
+  }
 }
 
 // acc += a * conj(b)
@@ -55,7 +70,11 @@ __device__ __forceinline__ void mac_conj_b(ffc& acc, const ffc& a, const ffc& b)
 template <typename V2>
 __global__ void __launch_bounds__(256) k_rho(const V2* __restrict__ psi, uint64_t N, int B,
                                              const double* __restrict__ P, V2* __restrict__ rho) {
+  static_assert(RHO_TILE == 32, "the mirror tile is 32 x 32");
+  if (blockIdx.y > blockIdx.x) return;  // the mirror of a tile above the diagonal
+  const bool mirror = blockIdx.y != blockIdx.x;
   __shared__ ffc Ar[RHO_KC][RHO_TILE], Ac[RHO_KC][RHO_TILE];
+  __shared__ V2 Tm[RHO_TILE][RHO_TILE + 1];
   const uint64_t r0 = (uint64_t)blockIdx.y * RHO_TILE, c0 = (uint64_t)blockIdx.x * RHO_TILE;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   if constexpr (std::is_same<V2, float2>::value) {
@@ -94,7 +113,9 @@ __global__ void __launch_bounds__(256) k_rho(const V2* __restrict__ psi, uint64_
       for (int j = 0; j < 2; ++j) {
         const uint64_t r = r0 + 2 * ty + i, c = c0 + 2 * tx + j;
         if (r < N && c < N) rho[r * N + c] = f[i][j];
+        Tm[2 * tx + j][2 * ty + i] = conj_v(f[i][j]);
       }
+    if (mirror) rho_mirror<V2>(Tm, rho, N, r0, c0);
   } else {
   ffc acc[2][2];
   for (int i = 0; i < 2; ++i)
@@ -129,8 +150,11 @@ __global__ void __launch_bounds__(256) k_rho(const V2* __restrict__ psi, uint64_
   for (int i = 0; i < 2; ++i)
     for (int j = 0; j < 2; ++j) {
       const uint64_t r = r0 + 2 * ty + i, c = c0 + 2 * tx + j;
-      if (r < N && c < N) store_ffc(rho, r * N + c, acc[i][j]);
+      const V2 v = ffc_to_v2<V2>(acc[i][j]);
+      if (r < N && c < N) rho[r * N + c] = v;
+      Tm[2 * tx + j][2 * ty + i] = conj_v(v);
     }
+  if (mirror) rho_mirror<V2>(Tm, rho, N, r0, c0);
   }
 }
 

@@ -35,7 +35,7 @@ def as_dt(x, dt):
 
 
 @pytest.mark.parametrize("dt", [0, 1])
-@pytest.mark.parametrize("n,B", [(3, 1), (7, 5), (9, 19)])
+@pytest.mark.parametrize("n,B", [(3, 1), (7, 5), (9, 19), (6, 70)])
 def test_density_matrix_vs_oracle(qc, dt, n, B):
     import torch
     g = W.rng(n * 100 + B)
