@@ -1062,7 +1062,7 @@ def extra_f3(n=14, B=64):
             "rho64_GB/s_written": N * N * 8 / (t_rho64 * 1e6),
             "rho64_tensor_TFLOP/s (bf16 digit products executed)": 2.0 * 8 * (2 * B) * (2 * N * N) / (t_rho64 * 1e9),
             "rho64_mm_minus_rho128_mm": rho64_mm - p_m,
-            "spectrum_ms (Gram + Jacobi, synchronous)": t_spec * 1e3, "trace": tr, "purity": pur,
+            "spectrum_ms (Gram + Householder/bisection, synchronous)": t_spec * 1e3, "trace": tr, "purity": pur,
             "entropy": ent, "p_success_rho_mm": p_m, "largest_eigenvalue": float(ev[0])}
 
 

@@ -532,12 +532,13 @@ qc_status qc_density_matrix(const void* psi_dev, int n, qc_dtype dt, int B, cons
 
 /* Eigenvalues of the same rho without forming it: its nonzero eigenvalues
  * are those of the B x B Gram matrix G_ab = sqrt(P_a P_b) <psi_a|psi_b>
- * (one streaming pass over the batch), diagonalised by a one-CTA Jacobi
- * solver in FP64.  evals_host (B doubles) receives them in descending
+ * (one streaming pass over the batch), whose eigenvalues one CTA finds in
+ * FP64 (Householder reduction to tridiagonal form, then bisection on Sturm
+ * counts).  evals_host (B doubles) receives them in descending
  * order (the other 2^n - B eigenvalues of rho are zero); stats_host[0..2] =
  * Tr rho, Tr rho^2 and the entropy -sum l ln l over l > 1e-14 (natural
  * logarithm).  1 <= B <= QC_SPECTRUM_MAX_UNIVERSES, 1 <= n <= 34.
- * Synchronises the stream.  QC_ECUDA if the solver does not converge. */
+ * Synchronises the stream.  QC_ECUDA if G has a non-finite entry. */
 qc_status qc_mixed_spectrum(const void* psi_dev, int n, qc_dtype dt, int B, const double* P_host,
                             double* evals_host, double* stats_host, void* stream);
 

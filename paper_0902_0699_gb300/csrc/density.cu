@@ -9,12 +9,13 @@
 // * qc_mixed_spectrum: the eigenvalues of rho without forming it.  rho has
 //   rank <= B, and its nonzero eigenvalues are those of the B x B Gram
 //   matrix G_ab = sqrt(P_a P_b) <psi_a|psi_b>, which one streaming pass over
-//   the batch builds; a one-CTA Jacobi solver diagonalises G.  Trace,
+//   the batch builds; one CTA reduces G to tridiagonal form (Householder)
+//   and finds its eigenvalues by bisection.  Trace,
 //   purity Tr rho^2 and the entropy -sum l ln l follow.
 //
 // Inner products run in double-float on the FP32 pipe (GB300's FP64 rate is
-// ~1/70 of FP32); the Jacobi solver works in FP64 on a matrix of at most
-// 64 x 64.
+// ~1/70 of FP32); the eigenvalue solver works in FP64 on a matrix of at
+// most 64 x 64.
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(256) k_gram(const V2* __restrict__ psi, uint64
 // G[a][b] = sqrt(P_a P_b) * sum over blocks (in block order), one thread per
 // entry.  G is made exactly Hermitian: the entries with a > b are the
 // conjugates of their mirrors and the diagonal is real (the two triangles'
-// separately rounded sums differ by ~1e-14, which Jacobi cannot rotate away).
+// separately rounded sums differ by ~1e-14; the solver assumes a Hermitian G).
 __global__ void k_gram_final(const float4* __restrict__ part, int nblk, int B, const double* __restrict__ sqrtP,
                              double2* __restrict__ G) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -247,138 +248,162 @@ __global__ void k_gram_final(const float4* __restrict__ part, int nblk, int B, c
   G[e] = make_double2(ff_to_d(re) * w, a > b ? -gi : gi);
 }
 
-// ----------------------------------------------------------- Jacobi ------
+// ------------------------------------------------------- eigenvalues ----
 // Eigenvalues of the Hermitian B x B matrix G (one CTA, FP64, B <= 64):
-// cyclic Jacobi with a round-robin ordering, so the B'/2 rotations of one
-// round touch disjoint rows and columns.  Rotation (p, q): with
-// c = A_pq = |c| e^{i phi}, the phase e^{-i phi} on q makes the pair real
-// and the classical rotation tan(2 theta) = 2|c| / (A_qq - A_pp) zeroes it.
+//  1. Householder reduction to a real symmetric tridiagonal matrix.  Step k
+//     reflects x = A[k+1.., k] onto alpha e_1 with alpha = -(x_0/|x_0|) |x|
+//     (no cancellation in v = x - alpha e_1), through u = v / |v|:
+//     p = A22 u, K = u^H p, q = p - K u, A22 -= 2 (u q^H + q u^H).  The
+//     off-diagonal entries' phases are removed by a diagonal unitary
+//     similarity, so T has diagonal Re A_kk and off-diagonal |x|.
+//  2. Each eigenvalue by bisection on Sturm counts of T (one thread each;
+//     the number of negative pivots of T - x I is the number of
+//     eigenvalues below x), from the Gershgorin interval down to a width
+//     of 2^-52 of its magnitude.
+// About n^3 complex multiply-adds once, where the cyclic Jacobi method it
+// replaces took that per sweep on one SM's FP64 pipe (64 x 64: 15 ms with
+// Jacobi's ~10 sweeps).
 // Out: ev[0..B) descending; stats = trace, sum l^2, -sum l ln l (l > 1e-14);
-// status[0] = sweeps used (a capped, bounded loop).
-#define JAC_MAX_SWEEPS 40
-// The matrix lives in dynamic shared memory, B' x (B'+1) entries (B' = B
-// rounded up to even, the extra row and column zero).
-#define JAC_SMEM(Bp) ((size_t)(Bp) * ((Bp) + 1) * sizeof(double2))
-__global__ void __launch_bounds__(256) k_jacobi(const double2* __restrict__ G, int B, double* __restrict__ ev,
-                                                double* __restrict__ stats, int* __restrict__ status) {
-  extern __shared__ double2 Ash[];
-  __shared__ double prm[QC_SPECTRUM_MAX_UNIVERSES / 2][4];  // cs, sn, e re, e im
-  __shared__ int pq[QC_SPECTRUM_MAX_UNIVERSES / 2][2];
-  __shared__ double red[256];
-  __shared__ int done;
-  const int Bp = B + (B & 1);
-  const int tid = threadIdx.x, T = blockDim.x;
-  for (int e = tid; e < Bp * Bp; e += T) {
-    const int r = e / Bp, c = e % Bp;
-    Ash[(r) * (Bp + 1) + (c)] = (r < B && c < B) ? G[r * B + c] : make_double2(0.0, 0.0);
-  }
+// status[0] = 0, or 1 if T has a non-finite entry.
+#define EIG_SMEM(B) ((size_t)(B) * ((B) + 1) * sizeof(double2))
+
+__device__ __forceinline__ double eig_block_sum(double x, double* red) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  __syncthreads();  // red is free
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
   __syncthreads();
-  int sweep = 0;
-  for (; sweep < JAC_MAX_SWEEPS; ++sweep) {
-    // off-diagonal and total Frobenius mass
-    double off = 0.0, tot = 0.0;
-    for (int e = tid; e < Bp * Bp; e += T) {
-      const double2 v = Ash[(e / Bp) * (Bp + 1) + (e % Bp)];
-      const double m2 = v.x * v.x + v.y * v.y;
-      tot += m2;
-      if (e / Bp != e % Bp) off += m2;
-    }
-    red[tid] = off;
-    __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;
+}
+
+// number of eigenvalues of T (diagonal d, squared off-diagonal e2) below x
+__device__ __forceinline__ int sturm_count(const double* d, const double* e2, int B, double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += q < 0.0;
+  for (int i = 1; i < B; ++i) {
+    q = d[i] - x - e2[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0;
+  }
+  return cnt;
+}
+
+__global__ void __launch_bounds__(256) k_eigh(const double2* __restrict__ G, int B, double* __restrict__ ev,
+                                              double* __restrict__ stats, int* __restrict__ status) {
+  extern __shared__ double2 A[];  // B x (B + 1), padded rows
+  __shared__ double2 u[QC_SPECTRUM_MAX_UNIVERSES], pq[QC_SPECTRUM_MAX_UNIVERSES];
+  __shared__ double d[QC_SPECTRUM_MAX_UNIVERSES], e2[QC_SPECTRUM_MAX_UNIVERSES];
+  __shared__ double red[8];
+  __shared__ double lam[QC_SPECTRUM_MAX_UNIVERSES];
+  const int tid = threadIdx.x, T = blockDim.x, W = B + 1;
+  for (int e = tid; e < B * B; e += T) A[(e / B) * W + e % B] = G[e];
+  __syncthreads();
+  for (int k = 0; k + 2 < B; ++k) {
+    const int m = B - 1 - k, o = k + 1;  // x = A[o + i][k], i < m
+    double2 x = make_double2(0.0, 0.0);
+    if (tid < m) x = A[(o + tid) * W + k];
+    const double sigma = eig_block_sum(x.x * x.x + x.y * x.y, red);
+    const double2 x0 = A[o * W + k];
+    const double nx = sqrt(sigma), a0 = sqrt(x0.x * x0.x + x0.y * x0.y);
     if (tid == 0) {
-      double o = 0.0;
-      for (int i = 0; i < T; ++i) o += red[i];
-      red[0] = o;
+      d[k] = A[k * W + k].x;
+      e2[k] = sigma;
+    }
+    if (!(nx > 0.0)) {  // nothing below the diagonal (or non-finite: caught at the end)
+      __syncthreads();
+      continue;
+    }
+    // phase of x0 (1 for x0 = 0); v = x - alpha e_1, |v|^2 = 2 |x| (|x| + |x0|)
+    const double2 ph = a0 > 0.0 ? make_double2(x0.x / a0, x0.y / a0) : make_double2(1.0, 0.0);
+    const double inv = 1.0 / sqrt(2.0 * nx * (nx + a0));
+    if (tid < m) {
+      const double2 xv = tid == 0 ? make_double2(x0.x + ph.x * nx, x0.y + ph.y * nx) : x;
+      u[tid] = make_double2(xv.x * inv, xv.y * inv);
     }
     __syncthreads();
-    const double offs = red[0];
-    __syncthreads();
-    red[tid] = tot;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int i = 0; i < T; ++i) t += red[i];
-      done = !(offs > 1e-28 * t);  // off-diagonal mass at the FP64 floor; also ends on a zero or NaN matrix
-    }
-    __syncthreads();
-    if (done) break;
-    for (int r = 0; r < Bp - 1; ++r) {
-      if (tid < Bp / 2) {
-        const int i = tid;
-        int p = (i == 0) ? 0 : 1 + (r + i - 1) % (Bp - 1);
-        int q = 1 + (r + Bp - 2 - i) % (Bp - 1);
-        if (p > q) {
-          const int t = p;
-          p = q;
-          q = t;
+    // p = A22 u: four threads per row
+    {
+      const int r = tid >> 2, part = tid & 3;
+      double pr = 0.0, pi = 0.0;
+      if (r < m)
+        for (int c = part; c < m; c += 4) {
+          const double2 a = A[(o + r) * W + o + c], uv = u[c];
+          pr = fma(a.x, uv.x, fma(-a.y, uv.y, pr));
+          pi = fma(a.x, uv.y, fma(a.y, uv.x, pi));
         }
-        pq[i][0] = p;
-        pq[i][1] = q;
-        const double2 c = Ash[(p) * (Bp + 1) + (q)];
-        const double d = sqrt(c.x * c.x + c.y * c.y);
-        if (d == 0.0) {
-          prm[i][0] = 1.0;
-          prm[i][1] = 0.0;
-          prm[i][2] = 1.0;
-          prm[i][3] = 0.0;
-        } else {
-          const double th = (Ash[(q) * (Bp + 1) + (q)].x - Ash[(p) * (Bp + 1) + (p)].x) / (2.0 * d);
-          const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-          const double cs = 1.0 / sqrt(1.0 + t * t);
-          prm[i][0] = cs;
-          prm[i][1] = t * cs;
-          prm[i][2] = c.x / d;
-          prm[i][3] = c.y / d;
-        }
-      }
-      __syncthreads();
-      // columns: A[:,p] = cs A[:,p] - sn e* A[:,q];  A[:,q] = sn A[:,p] + cs e* A[:,q]
-      for (int w = tid; w < (Bp / 2) * Bp; w += T) {
-        const int i = w / Bp, k = w % Bp;
-        const int p = pq[i][0], q = pq[i][1];
-        const double cs = prm[i][0], sn = prm[i][1], er = prm[i][2], ei = -prm[i][3];
-        const double2 ap = Ash[(k) * (Bp + 1) + (p)], aq = Ash[(k) * (Bp + 1) + (q)];
-        const double eqr = er * aq.x - ei * aq.y, eqi = er * aq.y + ei * aq.x;  // e* A[k][q]
-        Ash[(k) * (Bp + 1) + (p)] = make_double2(cs * ap.x - sn * eqr, cs * ap.y - sn * eqi);
-        Ash[(k) * (Bp + 1) + (q)] = make_double2(sn * ap.x + cs * eqr, sn * ap.y + cs * eqi);
-      }
-      __syncthreads();
-      // rows: A[p,:] = cs A[p,:] - sn e A[q,:];  A[q,:] = sn A[p,:] + cs e A[q,:]
-      for (int w = tid; w < (Bp / 2) * Bp; w += T) {
-        const int i = w / Bp, k = w % Bp;
-        const int p = pq[i][0], q = pq[i][1];
-        const double cs = prm[i][0], sn = prm[i][1], er = prm[i][2], ei = prm[i][3];
-        const double2 ap = Ash[(p) * (Bp + 1) + (k)], aq = Ash[(q) * (Bp + 1) + (k)];
-        const double eqr = er * aq.x - ei * aq.y, eqi = er * aq.y + ei * aq.x;  // e A[q][k]
-        Ash[(p) * (Bp + 1) + (k)] = make_double2(cs * ap.x - sn * eqr, cs * ap.y - sn * eqi);
-        Ash[(q) * (Bp + 1) + (k)] = make_double2(sn * ap.x + cs * eqr, sn * ap.y + cs * eqi);
-      }
-      __syncthreads();
+      pr += __shfl_xor_sync(0xffffffffu, pr, 1);
+      pi += __shfl_xor_sync(0xffffffffu, pi, 1);
+      pr += __shfl_xor_sync(0xffffffffu, pr, 2);
+      pi += __shfl_xor_sync(0xffffffffu, pi, 2);
+      if (r < m && part == 0) pq[r] = make_double2(pr, pi);
     }
+    __syncthreads();
+    // K = u^H p (real for Hermitian A22), then q = p - K u
+    double kk = 0.0;
+    if (tid < m) kk = u[tid].x * pq[tid].x + u[tid].y * pq[tid].y;
+    const double K = eig_block_sum(kk, red);
+    if (tid < m) pq[tid] = make_double2(pq[tid].x - K * u[tid].x, pq[tid].y - K * u[tid].y);
+    __syncthreads();
+    // A22 -= 2 (u q^H + q u^H)
+    for (int e = tid; e < m * m; e += T) {
+      const int r = e / m, c = e % m;
+      const double2 ur = u[r], uc = u[c], qr = pq[r], qc = pq[c];
+      double2 a = A[(o + r) * W + o + c];
+      a.x -= 2.0 * (ur.x * qc.x + ur.y * qc.y + qr.x * uc.x + qr.y * uc.y);
+      a.y -= 2.0 * (ur.y * qc.x - ur.x * qc.y + qr.y * uc.x - qr.x * uc.y);
+      A[(o + r) * W + o + c] = a;
+    }
+    __syncthreads();
   }
   if (tid == 0) {
-    double l[QC_SPECTRUM_MAX_UNIVERSES + 1];
-    for (int i = 0; i < Bp; ++i) l[i] = Ash[(i) * (Bp + 1) + (i)].x;
-    for (int i = 1; i < Bp; ++i) {  // insertion sort, descending
-      const double v = l[i];
-      int j = i - 1;
-      while (j >= 0 && l[j] < v) {
-        l[j + 1] = l[j];
-        --j;
-      }
-      l[j + 1] = v;
+    const int k0 = B >= 2 ? B - 2 : 0;
+    for (int k = k0; k < B; ++k) d[k] = A[k * W + k].x;
+    if (B >= 2) {
+      const double2 c = A[(B - 1) * W + B - 2];
+      e2[B - 2] = c.x * c.x + c.y * c.y;
     }
-    double tr = 0.0, p2 = 0.0, s = 0.0;
+  }
+  __syncthreads();
+  // Gershgorin interval and the pivot floor
+  double lo = 0.0, hi = 0.0, emax = 0.0;
+  bool finite = true;
+  for (int i = 0; i < B; ++i) {
+    const double el = i > 0 ? sqrt(e2[i - 1]) : 0.0, er = i + 1 < B ? sqrt(e2[i]) : 0.0;
+    lo = i ? fmin(lo, d[i] - el - er) : d[i] - el - er;
+    hi = i ? fmax(hi, d[i] + el + er) : d[i] + el + er;
+    if (i + 1 < B) emax = fmax(emax, e2[i]);
+    finite = finite && isfinite(d[i]) && (i + 1 >= B || isfinite(e2[i]));
+  }
+  const double span = fmax(fabs(lo), fabs(hi));
+  lo -= 2.2e-16 * span + 1e-300;
+  hi += 2.2e-16 * span + 1e-300;
+  const double pivmin = fmax(2.2e-308, 2.2e-308 * emax);
+  if (finite && tid < B) {  // the tid-th smallest eigenvalue
+    double a = lo, b = hi;
+    for (int it = 0; it < 200 && b - a > 2.2e-16 * fmax(fabs(a), fabs(b)) + 1e-19 * span + 1e-300; ++it) {
+      const double mid = 0.5 * (a + b);
+      if (sturm_count(d, e2, B, mid, pivmin) > tid) b = mid;
+      else a = mid;
+    }
+    lam[tid] = 0.5 * (a + b);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double tr = 0.0, p2 = 0.0, sl = 0.0;
     for (int i = 0; i < B; ++i) {
-      ev[i] = l[i];
-      tr += l[i];
-      p2 += l[i] * l[i];
-      if (l[i] > 1e-14) s -= l[i] * log(l[i]);
+      const double l = finite ? lam[B - 1 - i] : NAN;
+      ev[i] = l;
+      tr += l;
+      p2 += l * l;
+      if (l > 1e-14) sl -= l * log(l);
     }
     stats[0] = tr;
     stats[1] = p2;
-    stats[2] = s;
-    status[0] = sweep;
+    stats[2] = sl;
+    status[0] = finite ? 0 : 1;
   }
 }
 
@@ -504,24 +529,23 @@ QC_API qc_status qc_mixed_spectrum(const void* psi_dev, int n, qc_dtype dt, int 
   else
     k_gram<float2><<<nblk, 256, 0, s>>>(reinterpret_cast<const float2*>(psi_dev), N, B, per, part);
   k_gram_final<<<(B * B + 255) / 256, 256, 0, s>>>(part, nblk, B, sqrtP, G);
-  const int Bp = B + (B & 1);
-  static bool jac_attr = false;  // the opt-in above 48 KiB, once per process
-  if (!jac_attr) {
-    cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)JAC_SMEM(QC_SPECTRUM_MAX_UNIVERSES));
-    jac_attr = true;
+  static bool eig_attr = false;  // the opt-in above 48 KiB, once per process
+  if (!eig_attr) {
+    cudaFuncSetAttribute(k_eigh, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)EIG_SMEM(QC_SPECTRUM_MAX_UNIVERSES));
+    eig_attr = true;
   }
-  k_jacobi<<<1, 256, JAC_SMEM(Bp), s>>>(G, B, ev, stats, status);
+  k_eigh<<<1, 256, EIG_SMEM(B), s>>>(G, B, ev, stats, status);
   st = check_launch("mixed spectrum", 3);
   if (!st) {
     e = cudaMemcpyAsync(evals_host, ev, sizeof(double) * B, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(stats_host, stats, sizeof(double) * 3, cudaMemcpyDeviceToHost, s);
-    int sweeps = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&sweeps, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    int bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, status, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) st = cuda_fail(e, "spectrum readback");
-    else if (sweeps >= JAC_MAX_SWEEPS) {
-      set_error("Jacobi did not converge in %d sweeps", JAC_MAX_SWEEPS);
+    else if (bad) {
+      set_error("mixed spectrum: the Gram matrix has a non-finite entry");
       st = QC_ECUDA;
     }
   }
