@@ -26,8 +26,11 @@
 namespace qc {
 
 // ------------------------------------------------ amplitudes as ff pairs --
+// A non-finite amplitude becomes a NaN pair (the double-float split would
+// turn it into a finite value), so that it reaches the Gram matrix.
 __device__ __forceinline__ ffc load_ffc(const double2* p, uint64_t i) {
   const double2 v = p[i];
+  if (!isfinite(v.x) || !isfinite(v.y)) return ffc_make(ff_make(NAN, 0.f), ff_make(NAN, 0.f));
   return ffc_make(ff_from_d(v.x), ff_from_d(v.y));
 }
 __device__ __forceinline__ ffc load_ffc(const float2* p, uint64_t i) {
@@ -242,6 +245,10 @@ __global__ void k_gram_final(const float4* __restrict__ part, int nblk, int B, c
     const float4 v = part[(uint64_t)k * B * B + u];
     re = ff_add(re, ff_make(v.x, v.y));
     im = ff_add(im, ff_make(v.z, v.w));
+  }
+  if (!isfinite(re.hi) || !isfinite(im.hi)) {  // kept non-finite (the join would not)
+    G[e] = make_double2(NAN, NAN);
+    return;
   }
   const double w = sqrtP[a] * sqrtP[b];
   const double gi = (a == b) ? 0.0 : ff_to_d(im) * w;

@@ -177,3 +177,21 @@ def test_density_invalid(qc):
         qc.qc_density_matrix(t.data_ptr(), 16, 0, 4, np.full(4, 0.25), t.data_ptr())
     with pytest.raises(qc.QCError):
         qc.qc_wigner_d(2, 0.1, 0.2, 0.3)
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_mixed_spectrum_non_finite_gram(qc, dt):
+    # a NaN amplitude makes the Gram matrix non-finite: the solver reports it
+    # (QC_ECUDA) instead of returning eigenvalues
+    n, B = 5, 3
+    g = W.rng(77)
+    states = np.stack([W.random_state(g, n) for _ in range(B)])
+    states[1, 7] = np.nan
+    t = batch(qc, states, dt)
+    with pytest.raises(qc.QCError, match="non-finite"):
+        qc.qc_mixed_spectrum(t.data_ptr(), n, dt, B, np.full(B, 1.0 / B))
+    # the next call on finite data is unaffected
+    states[1, 7] = 0.5
+    t = batch(qc, states, dt)
+    ev, (tr, pur, ent) = qc.qc_mixed_spectrum(t.data_ptr(), n, dt, B, np.full(B, 1.0 / B))
+    assert np.all(np.isfinite(ev)) and np.isfinite(tr)
